@@ -1,0 +1,306 @@
+"""Benchmark of the online nested polarized-traces solve.
+
+One step = one hz_solve of the whole batch (Newton potentials, FGMRES on the
+polarized traces with the Gauss-Seidel sweeps, volume reconstruction, FP64
+residual refinement to 1e-8), i.e. every row of the hot path.
+
+Default workload: smooth random medium (c in [1.5, 4.5], correlation length
+20h), 1024 x 1024 interior + 20-point PML, 10 points per wavelength at
+c_min, L = 16 layers x C = 16 cells, 64 point sources on the first interior
+row, mixed precision (complex FP32 operators, FP64 Arnoldi and residual).
+
+Metric: RHS*Mdof/s = B * n_x * n_z / 1e6 / (seconds per step), whole job.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import hz_inputs as I  # noqa: E402
+
+WORKLOADS = {
+    # name: (n, n_pml, L, C, B, ppw, seed)
+    "smooth1024": dict(n=1024, n_pml=20, L=16, C=16, B=64, ppw=10.0, seed=2),
+    "smooth512": dict(n=512, n_pml=20, L=8, C=8, B=32, ppw=10.0, seed=5),
+    "smooth256": dict(n=256, n_pml=16, L=8, C=4, B=16, ppw=10.0, seed=2),
+}
+METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
+UNIT = "RHS*Mdof/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,utilization.gpu")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        util = [num(s[7]) for s in self.samples]
+        load = [s for s, u in zip(self.samples, util) if u >= 50] or self.samples
+        sm = sorted(num(s[0]) for s in load)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in load for i in range(4) if s[3 + i].lower().startswith("active")})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": num(load[0][1]), "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def make_problem(wl):
+    pb = I.smooth_random(wl["n"], n_pml=wl["n_pml"], L=wl["L"], C=wl["C"], seed=wl["seed"], ppw=wl["ppw"])
+    f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, wl["B"])
+    return pb, f
+
+
+# ------------------------------------------------------------ GPU arm ---
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_1510_01831_gb300 import hz
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    wl = dict(WORKLOADS[args.workload])
+    if args.B:
+        wl["B"] = args.B
+    pb, f = make_problem(wl)
+    B = f.shape[0]
+    prec = hz.HZ_MIXED if args.precision == "mixed" else hz.HZ_FP64
+    stream = torch.cuda.Stream()
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec, device_ptrs=True,
+                     stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8)
+    t0 = time.time()
+    ctx.hz_factor()
+    t_factor = time.time() - t0
+    f_dev = torch.from_numpy(f).to("cuda")
+    u_dev = torch.empty_like(f_dev)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        _, st = ctx.hz_solve(f_dev, u_dev)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats = []
+    with Clocks(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, st = ctx.hz_solve(f_dev, u_dev)
+            stats.append(st.as_dict())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+    mdof = pb.n_x * pb.n_z / 1e6
+    value = world * B * mdof / (ms / 1e3)
+    # end-to-end through the same entry point with pinned host buffers
+    f_host = torch.from_numpy(f).pin_memory()
+    u_host = torch.empty_like(f_host).pin_memory()
+    ctx.hz_set_device_ptrs(False)
+    fh, uh = f_host.numpy(), u_host.numpy()
+    ctx.hz_solve(fh, uh)
+    torch.cuda.synchronize()
+    e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        ctx.hz_solve(fh, uh)
+    torch.cuda.synchronize()
+    e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
+    ctx.hz_set_device_ptrs(True)
+    # kernel-class timings over the timed region
+    kt_ms = np.sum([s["kt_ms"] for s in stats], axis=0)
+    kt_n = np.sum([s["kt_launches"] for s in stats], axis=0)
+    kt_b = np.sum([s["kt_bytes"] for s in stats], axis=0)
+    kt_f = np.sum([s["kt_flops"] for s in stats], axis=0)
+    names = ["cell_chain", "inner_chain", "batched_fes_gemm"]
+    top = int(np.argmax(kt_ms))
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32 SIMT peak from unit counts and the maximum SM clock: 152 SMs x 128 FMA lanes x 2 flops
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if prec == hz.HZ_MIXED else 1.25
+    gbs = kt_b[top] / (kt_ms[top] / 1e3) / 1e9 if kt_ms[top] > 0 else 0.0
+    tfl = kt_f[top] / (kt_ms[top] / 1e3) / 1e12 if kt_ms[top] > 0 else 0.0
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    # the kernel is bound by whichever roof it is closer to
+    if gbs / hbm >= tfl / alu_peak:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(gbs / hbm, 4)}
+    else:
+        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                "frac": round(tfl / alu_peak, 4)}
+    roof.update({"kernel": names[top], "traffic": None, "peak_source": src + " (" +
+                 ("FP32 SIMT from 152 SMs x 128 lanes x max clock" if roof["bound"] == "alu" else "copy GB/s") + ")",
+                 "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
+                 "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
+                 "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)}})
+    last = stats[-1]
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if prec == hz.HZ_MIXED else "c128", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: smooth random c in [1.5,4.5] corr 20h, "
+                               f"{pb.n_x}x{pb.n_z}+{pb.n_pml} PML, {wl['ppw']:g} ppw, L={pb.L} x C={pb.C}, "
+                               f"{B} point sources row 1, {args.precision}",
+                   "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
+                   "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
+        "gpu_launches": int(sum(s["gpu_launches"] for s in stats)),
+        "solve": {"iterations": last["iterations"], "refinements": last["refinements"],
+                  "resid": last["resid"], "gmres_resid": last["gmres_resid"], "t_factor_s": round(t_factor, 2),
+                  "phase_ms": {k: round(last[k], 2) for k in ("t_local_ms", "t_gmres_ms", "t_recon_ms",
+                                                             "t_resid_ms", "t_total_ms")}},
+        "roofline": roof,
+        "e2e": {"value": round(world * B * mdof / (e_ms / 1e3), 3), "unit": UNIT,
+                "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(f.nbytes)},
+        "clocks": clk.summary(),
+    }
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------- oracle (CPU) timing ---
+def oracle_sample(wl, rows=24, nthreads=None):
+    """Time the CPU oracle (banded LU) on a full-width strip of the workload's
+    medium and scale to the full grid: with x-fastest ordering the band width
+    is the full extended width, so the cost per grid row is the same as for
+    the full problem."""
+    import oracle as O
+    pb, f = make_problem(wl)
+    p = pb.n_pml
+    NZs = rows + 2 * p
+    m = np.ascontiguousarray(pb.m[:NZs, :])
+    fs = np.ascontiguousarray(f[:, :NZs, :])
+    box = O.Box(m, pb.n_x, rows, p, pb.omega, pb.h, O.default_pml_C(pb.m))
+    t0 = time.perf_counter()
+    fac = box.factor(order=1)
+    t1 = time.perf_counter()
+    fac.solve(fs)
+    t2 = time.perf_counter()
+    scale = (pb.n_z + 2 * p) / NZs
+    t_full = (t2 - t0) * scale
+    value = f.shape[0] * pb.n_x * pb.n_z / 1e6 / t_full
+    return value, {"factor_s": round(t1 - t0, 2), "solve_s": round(t2 - t1, 2), "rows": rows, "scale": scale}
+
+
+def run_reference(args, rank, world):
+    wl = dict(WORKLOADS[args.workload])
+    if args.B:
+        wl["B"] = args.B
+    cores = os.cpu_count()
+    steps = []
+    det = None
+    for _ in range(args.warmup + args.steps):
+        v, det = oracle_sample(wl)
+        steps.append(v)
+    v = float(np.mean(steps[args.warmup:]))
+    ms = wl["B"] * wl["n"] * wl["n"] / 1e6 / v * 1e3
+    sample = (f"banded LU (x-fastest, band = full extended width) of a {det['rows']}-row full-width strip of the "
+              f"workload, factor + {wl['B']} solves, time scaled by {det['scale']:.1f} to the full grid")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": args.workload, "B": wl["B"]},
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="smooth1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--B", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            wl = dict(WORKLOADS[args.workload])
+            if args.B:
+                wl["B"] = args.B
+            v, det = oracle_sample(wl)
+            out["cpu_baseline"] = {"value": round(v, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": f"{det['rows']}-row full-width strip, band LU factor + solves, "
+                                             f"scaled x{det['scale']:.1f} to the full grid"}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

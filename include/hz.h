@@ -1,0 +1,187 @@
+/*
+ * hz.h -- C ABI of the GB300 nested polarized-traces Helmholtz solver.
+ *
+ * Problem (Section 2, Appendix A of Zepeda-Nunez & Demanet, "Nested domain
+ * decomposition with polarized traces for the 2D Helmholtz equation"):
+ *     (-Laplacian - omega^2 m(x)) u = f   on the PML-extended rectangle,
+ * discretised by the 5-point stencil with PML (d/dx -> alpha_x d/dx,
+ * alpha = 1/(1 + i sigma/omega), sigma(d) = (C/delta)(d/delta)^2) and
+ * homogeneous Dirichlet data beyond the extended grid.  The interior has
+ * n_x x n_z nodes x_p = p h (p = 1..n_x), with n_pml PML nodes on every side.
+ *
+ * Method: the online stage of the nested polarized-traces solver
+ * (Sections 3-4): L layers of C cells; GMRES on the polarized interface
+ * traces (eq. integral_polarized) preconditioned by the Gauss-Seidel
+ * sweeps (eq. preconditioner_GS); layer Green's integrals applied through
+ * the factorization of eq. (factorization) with the inner compressed-block
+ * LU of Section 4.2.2 kept dense.
+ *
+ * Conventions for every entry point:
+ *   - Complex arrays are interleaved (re, im) doubles.
+ *   - Grid arrays are row-major [n_z + 2 n_pml][n_x + 2 n_pml], x fastest;
+ *     batched arrays put the batch index outermost: [B][rows][cols].
+ *   - Pointers are host pointers unless opts.device_ptrs = 1 at setup, in
+ *     which case every array argument (m excepted) is a device pointer.
+ *   - The caller owns every array it passes.  The context owns its factors
+ *     and workspaces and frees them in hz_destroy.
+ *   - No entry point aborts.  Each returns a status; hz_last_error() returns
+ *     a message for the last failure on that context.
+ *   - Calls on one context must not overlap; distinct contexts are
+ *     independent (they may share a stream).
+ */
+#ifndef HZ_H
+#define HZ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hz_ctx hz_ctx;
+
+typedef enum {
+    HZ_OK = 0,
+    HZ_EINVAL = 1,      /* bad argument (sizes, partition, NULL pointer, NaN/Inf input) */
+    HZ_ENOMEM = 2,      /* host or device allocation failed */
+    HZ_ECUDA = 3,       /* a CUDA call failed (message in hz_last_error) */
+    HZ_ESTATE = 4,      /* call out of order (solve before factor) */
+    HZ_ENOTCONV = 5,    /* GMRES or refinement did not reach the tolerance; best iterate written */
+    HZ_ETIMEOUT = 6,    /* a bounded device wait gave up */
+    HZ_ESINGULAR = 7    /* a zero pivot in a cell or inner factorization */
+} hz_status;
+
+enum { HZ_FP64 = 0, HZ_MIXED = 1 };            /* hz_opts.precision */
+enum { HZ_PGS = 0, HZ_PJAC = 1, HZ_PNONE = 2 }; /* hz_opts.precond */
+
+typedef struct {
+    int precision;      /* HZ_FP64: every online operator in FP64.
+                           HZ_MIXED: operators and sweeps in complex FP32, GMRES
+                           Arnoldi and the volume residual in FP64, accuracy
+                           recovered by residual refinement. */
+    int precond;        /* HZ_PGS (eq. preconditioner_GS), HZ_PJAC (eq.
+                           preconditioner_Jac) or HZ_PNONE */
+    int restart;        /* GMRES restart length (default 30) */
+    int max_it;         /* GMRES iteration cap per solve (default 200) */
+    double tol;         /* GMRES relative residual on the polarized system
+                           (default 1e-10 FP64, 1e-6 mixed) */
+    double refine_tol;  /* target ||H u - f|| / ||f|| on the volume; refinement
+                           passes repeat the solve on the residual until it is
+                           met (0: no refinement; default 1e-8) */
+    int max_refine;     /* refinement pass cap (default 6) */
+    double pml_C;       /* sigma amplitude C; <= 0 selects
+                           1.5 * c_max * ln(1e6) (1e-6 normal-incidence
+                           continuum reflection at the fastest speed) */
+    const int *layer_rows; /* L interior rows per layer, sum n_z; NULL = even split */
+    const int *cell_cols;  /* C interior columns per cell, sum n_x; NULL = even split */
+    int device_ptrs;    /* 1: array arguments of solve/gradient/component calls are device pointers */
+    void *stream;       /* cudaStream_t used by every call on the context (NULL = legacy default) */
+    int time_kernels;   /* 1: time the hot kernels with CUDA events (hz_stats.kt_*) */
+} hz_opts;
+
+typedef struct {
+    int iterations;        /* GMRES iterations, summed over refinement passes (max over RHS per pass) */
+    int refinements;       /* solves performed (1 = no refinement pass needed) */
+    double gmres_resid;    /* max over RHS of the last pass's GMRES relative residual */
+    double resid;          /* max over RHS of ||H u - f||_2 / ||f||_2 (FP64, Appendix A operator) */
+    double t_total_ms;     /* wall time of the call (device-synchronised) */
+    double t_local_ms;     /* Newton potentials: cell solves + inner sweeps (all passes) */
+    double t_gmres_ms;     /* GMRES on the traces (all passes) */
+    double t_recon_ms;     /* volume reconstruction (all passes) */
+    double t_resid_ms;     /* FP64 residual evaluations */
+    int gpu_launches;      /* kernels launched by the call */
+    /* with opts.time_kernels: launches and summed device time of the hot
+       kernel classes 0 = cell chain solves (a1), 1 = inner block-LU sweeps
+       (a3), 2 = batched F/E/S products (a2, a4) */
+    int kt_launches[3];
+    double kt_ms[3];
+    double kt_bytes[3];    /* algorithmic bytes moved by those launches */
+    double kt_flops[3];    /* algorithmic real flops of those launches */
+} hz_stats;
+
+/* Fill opts with the defaults documented above (precision HZ_FP64). */
+void hz_default_opts(hz_opts *opts);
+
+/* Create a context for one medium and frequency (Section 2: H u = f on the
+ * extended grid, m given on the extended grid, Appendix A footnote).
+ *   m      : host array (n_z+2n_pml) x (n_x+2n_pml) of squared slowness, copied.
+ *   L, C   : layers and cells per layer (Section 4; every layer and cell needs
+ *            at least 1 interior row/column; L >= 2).
+ *   opts   : may be NULL for defaults; copied (the partition arrays too).
+ * Errors: HZ_EINVAL (sizes, partition, non-finite m/omega/h), HZ_ENOMEM, HZ_ECUDA. */
+hz_status hz_setup(hz_ctx **ctx, const double *m, int n_x, int n_z, double omega,
+                   double h, int n_pml, int L, int C, const hz_opts *opts);
+
+/* Offline stage (Section 4.3.1, Table chap:nested:table:complexity): per cell
+ * assembly and block-tridiagonal factorization in FP64 with pivoted inverses of
+ * the diagonal Schur blocks, the cell Green's blocks of eq. (factorization)
+ * (M_f, M_u split into F, E, S), and the block-LU factors of each layer's inner
+ * SIE (Section 4.2.2) with inverted diagonal blocks.  Idempotent.
+ * Errors: HZ_ESINGULAR (zero pivot), HZ_ENOMEM, HZ_ECUDA. */
+hz_status hz_factor(hz_ctx *ctx);
+
+/* Online solve (Alg. matrix_free_solver with the nested inner solver):
+ *   f : [B][n_z+2p][n_x+2p] complex source, u : same shape, written.
+ *   st: may be NULL.
+ * u satisfies H u = f for the Appendix A operator.  Returns HZ_ENOTCONV (u still
+ * written with the best iterate) when the GMRES or refinement target is missed.
+ * Errors: HZ_ESTATE (not factored), HZ_EINVAL (B < 1, NULL, non-finite f). */
+hz_status hz_solve(hz_ctx *ctx, const double *f, int B, double *u, hz_stats *st);
+
+/* Receiver misfit J = 1/2 sum_s ||R u_s - d_s||^2 and its gradient with respect
+ * to m on the extended grid (not in the paper; adjoint state).  One forward
+ * solve per source, one adjoint solve reusing the factors (the row-scaled
+ * operator is complex symmetric), then
+ *   dJ/dm_i = omega^2 sum_s Re(lambda_{s,i} u_{s,i}),  H^T lambda_s = R^T conj(r_s).
+ *   f      : [B][grid] sources; d : [B][n_rec] data; rec_idx: [n_rec] flat
+ *            grid indices (host or device per device_ptrs);
+ *   J      : scalar out (host pointer always); grad_m : [grid] real out;
+ *   u_out  : optional [B][grid] forward fields (may be NULL).
+ * Errors as hz_solve. */
+hz_status hz_gradient(hz_ctx *ctx, const double *f, int B, const double *d,
+                      const int *rec_idx, int n_rec, double *J, double *grad_m,
+                      double *u_out, hz_stats *st);
+
+/* ---- component entry points (each runs one step of the online path on the
+ * device, used to test that step alone; inputs/outputs follow the conventions
+ * above, batch outermost) ---- */
+
+/* a1: solve one cell's local problem H^{l,c} x = g (0-based l, c) on the cell's
+ * extended grid [B][n_l+2p][w_c+2p]; the cell operator is the row-scaled
+ * (symmetric) form of Appendix A on a box with its own PML (Section 4). */
+hz_status hz_cell_solve(hz_ctx *ctx, int l, int c, const double *g, int B, double *x);
+
+/* a5: layer Green's integrals of layer l (Def. incomplete_green in the form of
+ * Appendix C, eq. pde_GRF_real) applied through eq. (factorization):
+ *   tr  : [B][4][T] traces at local rows (0, 1, n_l, n_l+1), T = n_x + 2p
+ *   out : [B][4][T] field sampled at the same rows.
+ * in_mask bit 0: use rows (0,1); bit 1: use rows (n,n+1). */
+hz_status hz_layer_green(hz_ctx *ctx, int l, const double *tr, int in_mask, int B, double *out);
+
+/* a6: y = M x for the polarized system (eqs. jump_1..jump_4, moved to the
+ * left); x, y : [B][L-1][4][T] with components (d_a, d_b, u_a, u_b) of each
+ * interface k (a = last row of layer k, b = first row of layer k+1). */
+hz_status hz_apply_M(hz_ctx *ctx, const double *x, int B, double *y);
+
+/* a7-a9: which = 0: P^GS x (eq. preconditioner_GS); 1: P^Jac x;
+ * 2: D_down^{-1} (Alg. downwardsSweep) on the d-part, u-part copied;
+ * 3: D_up^{-1} (Alg. upwardsSweep) on the u-part, d-part copied;
+ * 4: L applied to the d-part (Alg. upwardsReflections), written to the u-part,
+ *    d-part zeroed.  Layout as hz_apply_M. */
+hz_status hz_precond(hz_ctx *ctx, int which, const double *x, int B, double *y);
+
+/* a12: relative residual ||H u - f|| / ||f|| per RHS in FP64 (res: [B], host
+ * or device per device_ptrs). */
+hz_status hz_residual(hz_ctx *ctx, const double *u, const double *f, int B, double *res);
+
+/* Switch the pointer mode of later calls (same meaning as opts.device_ptrs). */
+hz_status hz_set_device_ptrs(hz_ctx *ctx, int device_ptrs);
+
+/* Bytes of device memory held by the context (factors + workspaces). */
+long long hz_device_bytes(const hz_ctx *ctx);
+
+void hz_destroy(hz_ctx *ctx);
+const char *hz_last_error(const hz_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HZ_H */

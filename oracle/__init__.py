@@ -77,6 +77,8 @@ def _load():
             P = ctypes.POINTER(_Box)
             lib.hzo_factor.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
             lib.hzo_factor.restype = ctypes.c_void_p
+            lib.hzo_factor_ordered.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+            lib.hzo_factor_ordered.restype = ctypes.c_void_p
             lib.hzo_solve.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
             lib.hzo_solve.restype = ctypes.c_int
             lib.hzo_free.argtypes = [ctypes.c_void_p]
@@ -151,18 +153,19 @@ class Box:
             A[:, j] = self.apply(eye).reshape(-1)
         return A
 
-    def factor(self) -> "Factor":
-        return Factor(self)
+    def factor(self, order: int = 0) -> "Factor":
+        """order 0: smaller band width; 1: x fastest; 2: z fastest."""
+        return Factor(self, order)
 
 
 class Factor:
     """Banded LU (partial pivoting) of a Box's operator."""
 
-    def __init__(self, box: Box):
+    def __init__(self, box: Box, order: int = 0):
         lib = _load()
         self.box = box
         info = ctypes.c_int(0)
-        self._h = lib.hzo_factor(ctypes.byref(box._c), ctypes.byref(info))
+        self._h = lib.hzo_factor_ordered(ctypes.byref(box._c), order, ctypes.byref(info))
         if not self._h:
             raise MemoryError("oracle factor: allocation failed")
         if info.value != 0:

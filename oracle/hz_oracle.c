@@ -164,7 +164,7 @@ void hzo_free(void *handle)
 /* Factor H; transposed solves reuse the factors (hzo_solve trans = 1).
  * Returns NULL on allocation failure; *info = 0 on success, j+1 if the j-th
  * pivot column is exactly zero. */
-void *hzo_factor(const hzo_box *b, int *info)
+void *hzo_factor_ordered(const hzo_box *b, int order, int *info)
 {
     const int NX = b->nxi + 2 * b->p, NZ = b->nzi + 2 * b->p;
     hzo_lu *F = (hzo_lu *)calloc(1, sizeof(hzo_lu));
@@ -172,7 +172,8 @@ void *hzo_factor(const hzo_box *b, int *info)
     F->NX = NX;
     F->NZ = NZ;
     F->n = (long)NX * NZ;
-    F->xfast = NX <= NZ;
+    /* order 0: the smaller band width; 1: x fastest (band NX); 2: z fastest (band NZ) */
+    F->xfast = order == 1 ? 1 : (order == 2 ? 0 : NX <= NZ);
     int bw = F->xfast ? NX : NZ;
     F->kl = F->ku = bw;
     F->ldab = 2 * F->kl + F->ku + 1;
@@ -228,6 +229,11 @@ void *hzo_factor(const hzo_box *b, int *info)
         }
     }
     return F;
+}
+
+void *hzo_factor(const hzo_box *b, int *info)
+{
+    return hzo_factor_ordered(b, 0, info);
 }
 
 /* In-place solve for nrhs right-hand sides in grid order (length NX*NZ each).

@@ -1,0 +1,451 @@
+// C ABI entry points (include/hz.h): argument checks, host/device staging,
+// error capture.  The numerical work is in hz_factor.cu and hz_solve.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "hz_ctx.cuh"
+
+using hz::CudaError;
+using hz::HzError;
+
+namespace {
+
+thread_local std::string g_err;  // errors without a context (hz_setup failures)
+
+__global__ void k_finite(const double *a, long long n, int *flag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(a[i])) atomicExch(flag, 1);
+}
+
+// d [B][n_rec], u [B][N]: r = R u - d; adjoint source g[b][rec] = conj(r)
+__global__ void k_misfit(const double2 *__restrict__ u, const double2 *__restrict__ d, const int *__restrict__ rec,
+                         int n_rec, long long N, int B, double2 *r, double2 *g) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n_rec * B;
+         e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e / n_rec), i = (int)(e % n_rec);
+        long long gi = (long long)b * N + rec[i];
+        double2 v = make_double2(u[gi].x - d[e].x, u[gi].y - d[e].y);
+        r[e] = v;
+        g[gi] = make_double2(v.x, -v.y);
+    }
+}
+
+// grad_i = omega^2 sum_b Re(lambda_{b,i} u_{b,i}) / (alpha_x alpha_z)_i  with lambda the
+// row-scaled-form adjoint field (so lambda / (alpha_x alpha_z) solves the transposed
+// Appendix A system)
+__global__ void k_grad(const double2 *__restrict__ lam, const double2 *__restrict__ u, const double2 *__restrict__ ax,
+                       const double2 *__restrict__ az, int NX, long long N, int B, double om2, double *grad) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+        double2 D = hz::operator*(ax[g % NX], az[g / NX]);
+        double s = 0.0;
+        for (int b = 0; b < B; b++) {
+            double2 p = hz::operator*(lam[(long long)b * N + g], u[(long long)b * N + g]);
+            double2 q = hz::cdiv(p, D);
+            s += q.x;
+        }
+        grad[g] = om2 * s;
+    }
+}
+
+hz_status fail(hz_ctx *c, int code, const std::string &msg) {
+    if (c)
+        c->err = msg;
+    else
+        g_err = msg;
+    return (hz_status)code;
+}
+
+template <class F> hz_status guarded(hz_ctx *c, F &&f) {
+    try {
+        return f();
+    } catch (const HzError &e) {
+        return fail(c, e.code, e.what);
+    } catch (const CudaError &e) {
+        return fail(c, HZ_ECUDA, e.what);
+    } catch (const std::bad_alloc &) {
+        return fail(c, HZ_ENOMEM, "host allocation failed");
+    } catch (const std::exception &e) {
+        return fail(c, HZ_ECUDA, e.what());
+    }
+}
+
+double2 *stage(hz_ctx *c, long long n) {
+    if (c->stage_n < n) {
+        c->dfree(c->stage);
+        c->stage = (double2 *)c->dalloc(sizeof(double2) * n);
+        c->stage_n = n;
+    }
+    return c->stage;
+}
+
+void check_finite(hz_ctx *c, const double *a, long long n, const char *what) {
+    if (!c->d_flag) c->d_flag = (int *)c->dalloc(sizeof(int));
+    HZ_CU(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
+    k_finite<<<256, 256, 0, c->st>>>(a, n, c->d_flag);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    int f = 0;
+    HZ_CU(cudaMemcpyAsync(&f, c->d_flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+    if (f) throw HzError(HZ_EINVAL, std::string(what) + " contains NaN or Inf");
+}
+
+// copy a user array (host or device, n complex) to a device buffer
+const double2 *to_dev(hz_ctx *c, const double *a, long long n, double2 *buf) {
+    if (c->opts.device_ptrs) return (const double2 *)a;
+    HZ_CU(cudaMemcpyAsync(buf, a, sizeof(double2) * n, cudaMemcpyHostToDevice, c->st));
+    return buf;
+}
+void from_dev(hz_ctx *c, double *a, const double2 *buf, long long n) {
+    if (c->opts.device_ptrs) return;  // written in place
+    HZ_CU(cudaMemcpyAsync(a, buf, sizeof(double2) * n, cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+
+}  // namespace
+
+extern "C" {
+
+void hz_default_opts(hz_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof *o);
+    o->precision = HZ_FP64;
+    o->precond = HZ_PGS;
+    o->restart = 30;
+    o->max_it = 200;
+    o->tol = 0.0;  // 0: precision default (1e-10 FP64, 1e-6 mixed)
+    o->refine_tol = 1e-8;
+    o->max_refine = 6;
+    o->pml_C = 0.0;
+}
+
+hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega, double h, int n_pml, int L, int C,
+                   const hz_opts *opts) {
+    if (!out) return fail(nullptr, HZ_EINVAL, "ctx pointer is NULL");
+    *out = nullptr;
+    if (!m) return fail(nullptr, HZ_EINVAL, "m is NULL");
+    if (n_x < 1 || n_z < 1 || n_pml < 1 || L < 2 || C < 1 || L > n_z || C > n_x)
+        return fail(nullptr, HZ_EINVAL, "need n_x, n_z >= 1, n_pml >= 1, 2 <= L <= n_z, 1 <= C <= n_x");
+    if (!(std::isfinite(omega) && omega > 0 && std::isfinite(h) && h > 0))
+        return fail(nullptr, HZ_EINVAL, "omega and h must be finite and positive");
+    hz_ctx *c = new (std::nothrow) hz_ctx();
+    if (!c) return fail(nullptr, HZ_ENOMEM, "host allocation failed");
+    hz_default_opts(&c->opts);
+    if (opts) c->opts = *opts;
+    if (c->opts.restart < 1) c->opts.restart = 30;
+    if (c->opts.max_it < 1) c->opts.max_it = 200;
+    if (c->opts.tol <= 0) c->opts.tol = c->opts.precision == HZ_MIXED ? 1e-6 : 1e-10;
+    if (c->opts.precision != HZ_FP64 && c->opts.precision != HZ_MIXED) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "precision must be HZ_FP64 or HZ_MIXED");
+    }
+    if (c->opts.precond < HZ_PGS || c->opts.precond > HZ_PNONE) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "precond must be HZ_PGS, HZ_PJAC or HZ_PNONE");
+    }
+    c->n_x = n_x;
+    c->n_z = n_z;
+    c->p = n_pml;
+    c->L = L;
+    c->C = C;
+    c->omega = omega;
+    c->h = h;
+    c->NX = n_x + 2 * n_pml;
+    c->NZ = n_z + 2 * n_pml;
+    c->st = (cudaStream_t)c->opts.stream;
+    const long long N = (long long)c->NX * c->NZ;
+    double cmax = 0;
+    for (long long i = 0; i < N; i++) {
+        if (!std::isfinite(m[i]) || m[i] <= 0) {
+            delete c;
+            return fail(nullptr, HZ_EINVAL, "m must be finite and positive");
+        }
+        cmax = std::max(cmax, 1.0 / std::sqrt(m[i]));
+    }
+    c->pml_C = c->opts.pml_C > 0 ? c->opts.pml_C : 1.5 * cmax * std::log(1e6);
+    auto part = [](const int *a, int parts, int n, std::vector<int> &v) {
+        v.resize(parts);
+        if (!a) {
+            for (int i = 0; i < parts; i++) v[i] = n / parts + (i < n % parts ? 1 : 0);
+            return true;
+        }
+        long long s = 0;
+        for (int i = 0; i < parts; i++) {
+            if (a[i] < 1) return false;
+            v[i] = a[i];
+            s += a[i];
+        }
+        return s == n;
+    };
+    if (!part(c->opts.layer_rows, L, n_z, c->rows) || !part(c->opts.cell_cols, C, n_x, c->cols)) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "layer_rows must be L positive counts summing to n_z, cell_cols C summing to n_x");
+    }
+    c->opts.layer_rows = nullptr;  // copied
+    c->opts.cell_cols = nullptr;
+    hz_status s = guarded(c, [&]() -> hz_status {
+        c->d_m = (double *)c->dalloc(sizeof(double) * N);
+        HZ_CU(cudaMemcpy(c->d_m, m, sizeof(double) * N, cudaMemcpyHostToDevice));
+        hz::build_decomposition(c);
+        hz::init_global_alpha(c);
+        return HZ_OK;
+    });
+    if (s != HZ_OK) {
+        g_err = c->err;
+        hz_destroy(c);
+        return s;
+    }
+    *out = c;
+    return HZ_OK;
+}
+
+hz_status hz_factor(hz_ctx *c) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (c->factored) return HZ_OK;
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        hz::factor_all(c);
+        c->factored = true;
+        return HZ_OK;
+    });
+}
+
+hz_status hz_solve(hz_ctx *c, const double *f, int B, double *u, hz_stats *st) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_solve before hz_factor");
+    if (!f || !u || B < 1) return fail(c, HZ_EINVAL, "f, u must be non-NULL and B >= 1");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        double2 *buf = stage(c, 2 * N * B);
+        const double2 *fd = to_dev(c, f, N * B, buf);
+        check_finite(c, (const double *)fd, 2 * N * B, "f");
+        double2 *ud = c->opts.device_ptrs ? (double2 *)u : buf + N * B;
+        c->kt_reset();
+        int s = c->mixed() ? hz::solve_impl<float2>(c, fd, B, ud, st, true)
+                           : hz::solve_impl<double2>(c, fd, B, ud, st, true);
+        from_dev(c, u, ud, N * B);
+        c->kt_collect();
+        if (st) {
+            st->gpu_launches = c->nl;
+            for (int i = 0; i < 3; i++) {
+                st->kt_launches[i] = c->kt_launches[i];
+                st->kt_ms[i] = c->kt_ms[i];
+                st->kt_bytes[i] = c->kt_bytes[i];
+                st->kt_flops[i] = c->kt_flops[i];
+            }
+        }
+        if (s == HZ_ENOTCONV) c->err = "tolerance not reached; best iterate written";
+        return (hz_status)s;
+    });
+}
+
+hz_status hz_gradient(hz_ctx *c, const double *f, int B, const double *d, const int *rec_idx, int n_rec, double *J,
+                      double *grad_m, double *u_out, hz_stats *st) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_gradient before hz_factor");
+    if (!f || !d || !rec_idx || n_rec < 1 || !J || !grad_m || B < 1)
+        return fail(c, HZ_EINVAL, "NULL argument or n_rec < 1 or B < 1");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        cudaStream_t s_ = c->st;
+        // device buffers: f/u (2NB) staging + lambda, g, r, d, rec, grad
+        double2 *buf = stage(c, 2 * N * B);
+        const double2 *fd = to_dev(c, f, N * B, buf);
+        check_finite(c, (const double *)fd, 2 * N * B, "f");
+        double2 *ud = buf + N * B;
+        double2 *g = (double2 *)c->dalloc(sizeof(double2) * N * B);
+        double2 *lam = (double2 *)c->dalloc(sizeof(double2) * N * B);
+        double2 *r = (double2 *)c->dalloc(sizeof(double2) * (long long)n_rec * B);
+        double2 *dd = (double2 *)c->dalloc(sizeof(double2) * (long long)n_rec * B);
+        int *rd = (int *)c->dalloc(sizeof(int) * n_rec);
+        double *gd = (double *)c->dalloc(sizeof(double) * N);
+        struct Free {
+            hz_ctx *c;
+            std::vector<void *> v;
+            ~Free() {
+                for (void *p : v) c->dfree(p);
+            }
+        } fr{c, {g, lam, r, dd, rd, gd}};
+        if (c->opts.device_ptrs) {
+            HZ_CU(cudaMemcpyAsync(dd, d, sizeof(double2) * (long long)n_rec * B, cudaMemcpyDeviceToDevice, s_));
+            HZ_CU(cudaMemcpyAsync(rd, rec_idx, sizeof(int) * n_rec, cudaMemcpyDeviceToDevice, s_));
+        } else {
+            for (int i = 0; i < n_rec; i++)
+                if (rec_idx[i] < 0 || rec_idx[i] >= N) throw HzError(HZ_EINVAL, "receiver index out of range");
+            HZ_CU(cudaMemcpyAsync(dd, d, sizeof(double2) * (long long)n_rec * B, cudaMemcpyHostToDevice, s_));
+            HZ_CU(cudaMemcpyAsync(rd, rec_idx, sizeof(int) * n_rec, cudaMemcpyHostToDevice, s_));
+        }
+        hz_stats s1{}, s2{};
+        c->kt_reset();
+        int sf = c->mixed() ? hz::solve_impl<float2>(c, fd, B, ud, &s1, true)
+                            : hz::solve_impl<double2>(c, fd, B, ud, &s1, true);
+        HZ_CU(cudaMemsetAsync(g, 0, sizeof(double2) * N * B, s_));
+        k_misfit<<<256, 256, 0, s_>>>(ud, dd, rd, n_rec, N, B, r, g);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        std::vector<double2> rh((size_t)n_rec * B);
+        HZ_CU(cudaMemcpyAsync(rh.data(), r, sizeof(double2) * rh.size(), cudaMemcpyDeviceToHost, s_));
+        HZ_CU(cudaStreamSynchronize(s_));
+        double Jv = 0;
+        for (auto &v : rh) Jv += v.x * v.x + v.y * v.y;
+        *J = 0.5 * Jv;
+        // adjoint: the row-scaled operator is symmetric, so the same factors solve it
+        int sa = c->mixed() ? hz::solve_impl<float2>(c, g, B, lam, &s2, false)
+                            : hz::solve_impl<double2>(c, g, B, lam, &s2, false);
+        k_grad<<<256, 256, 0, s_>>>(lam, ud, c->d_ax, c->d_az, c->NX, N, B, c->omega * c->omega, gd);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        if (c->opts.device_ptrs) {
+            HZ_CU(cudaMemcpyAsync(grad_m, gd, sizeof(double) * N, cudaMemcpyDeviceToDevice, s_));
+            if (u_out) HZ_CU(cudaMemcpyAsync(u_out, ud, sizeof(double2) * N * B, cudaMemcpyDeviceToDevice, s_));
+        } else {
+            HZ_CU(cudaMemcpyAsync(grad_m, gd, sizeof(double) * N, cudaMemcpyDeviceToHost, s_));
+            if (u_out) HZ_CU(cudaMemcpyAsync(u_out, ud, sizeof(double2) * N * B, cudaMemcpyDeviceToHost, s_));
+        }
+        HZ_CU(cudaStreamSynchronize(s_));
+        if (st) {
+            *st = s1;
+            st->iterations += s2.iterations;
+            st->refinements += s2.refinements;
+            st->resid = std::max(s1.resid, s2.resid);
+            st->t_total_ms += s2.t_total_ms;
+            st->t_local_ms += s2.t_local_ms;
+            st->t_gmres_ms += s2.t_gmres_ms;
+            st->t_recon_ms += s2.t_recon_ms;
+            st->t_resid_ms += s2.t_resid_ms;
+            st->gpu_launches = c->nl;
+            c->kt_collect();
+            for (int i = 0; i < 3; i++) {
+                st->kt_launches[i] = c->kt_launches[i];
+                st->kt_ms[i] = c->kt_ms[i];
+                st->kt_bytes[i] = c->kt_bytes[i];
+                st->kt_flops[i] = c->kt_flops[i];
+            }
+        }
+        return (hz_status)(sf != HZ_OK ? sf : sa);
+    });
+}
+
+hz_status hz_cell_solve(hz_ctx *c, int l, int cc, const double *g, int B, double *x) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_cell_solve before hz_factor");
+    if (l < 0 || l >= c->L || cc < 0 || cc >= c->C || !g || !x || B < 1) return fail(c, HZ_EINVAL, "bad argument");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const int ci = l * c->C + cc;
+        const long long n = (long long)c->cells[ci].nx * c->cells[ci].nz;
+        double2 *buf = stage(c, 2 * n * B);
+        const double2 *gd = to_dev(c, g, n * B, buf);
+        double2 *xd = c->opts.device_ptrs ? (double2 *)x : buf + n * B;
+        if (c->mixed())
+            hz::comp_cell_solve<float2>(c, ci, gd, B, xd);
+        else
+            hz::comp_cell_solve<double2>(c, ci, gd, B, xd);
+        from_dev(c, x, xd, n * B);
+        return HZ_OK;
+    });
+}
+
+hz_status hz_layer_green(hz_ctx *c, int l, const double *tr, int in_mask, int B, double *out) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_layer_green before hz_factor");
+    if (l < 0 || l >= c->L || !tr || !out || B < 1 || in_mask < 0 || in_mask > 3)
+        return fail(c, HZ_EINVAL, "bad argument");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long n = 4LL * c->NX;
+        double2 *buf = stage(c, 2 * n * B);
+        const double2 *td = to_dev(c, tr, n * B, buf);
+        double2 *od = c->opts.device_ptrs ? (double2 *)out : buf + n * B;
+        if (c->mixed())
+            hz::comp_layer_green<float2>(c, l, td, in_mask, B, od);
+        else
+            hz::comp_layer_green<double2>(c, l, td, in_mask, B, od);
+        from_dev(c, out, od, n * B);
+        return HZ_OK;
+    });
+}
+
+static hz_status polar(hz_ctx *c, int which, const double *x, int B, double *y) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "called before hz_factor");
+    if (!x || !y || B < 1 || which < -1 || which > 4) return fail(c, HZ_EINVAL, "bad argument");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long n = c->n_tr();
+        double2 *buf = stage(c, 2 * n * B);
+        const double2 *xd = to_dev(c, x, n * B, buf);
+        double2 *yd = c->opts.device_ptrs ? (double2 *)y : buf + n * B;
+        if (c->mixed())
+            hz::comp_polar<float2>(c, which, xd, B, yd);
+        else
+            hz::comp_polar<double2>(c, which, xd, B, yd);
+        from_dev(c, y, yd, n * B);
+        return HZ_OK;
+    });
+}
+
+hz_status hz_apply_M(hz_ctx *c, const double *x, int B, double *y) { return polar(c, -1, x, B, y); }
+hz_status hz_precond(hz_ctx *c, int which, const double *x, int B, double *y) {
+    if (which < 0) return fail(c, HZ_EINVAL, "which must be 0..4");
+    return polar(c, which, x, B, y);
+}
+
+hz_status hz_residual(hz_ctx *c, const double *u, const double *f, int B, double *res) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!u || !f || !res || B < 1) return fail(c, HZ_EINVAL, "bad argument");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        double2 *buf = stage(c, 2 * N * B);
+        const double2 *ud = c->opts.device_ptrs ? (const double2 *)u : buf;
+        const double2 *fd = c->opts.device_ptrs ? (const double2 *)f : buf + N * B;
+        if (!c->opts.device_ptrs) {
+            HZ_CU(cudaMemcpyAsync(buf, u, sizeof(double2) * N * B, cudaMemcpyHostToDevice, c->st));
+            HZ_CU(cudaMemcpyAsync(buf + N * B, f, sizeof(double2) * N * B, cudaMemcpyHostToDevice, c->st));
+        }
+        std::vector<double> r(B);
+        if (c->mixed())
+            hz::comp_residual<float2>(c, ud, fd, B, r.data());
+        else
+            hz::comp_residual<double2>(c, ud, fd, B, r.data());
+        if (c->opts.device_ptrs)
+            HZ_CU(cudaMemcpy(res, r.data(), sizeof(double) * B, cudaMemcpyHostToDevice));
+        else
+            std::memcpy(res, r.data(), sizeof(double) * B);
+        return HZ_OK;
+    });
+}
+
+hz_status hz_set_device_ptrs(hz_ctx *c, int device_ptrs) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    c->opts.device_ptrs = device_ptrs ? 1 : 0;
+    return HZ_OK;
+}
+
+long long hz_device_bytes(const hz_ctx *c) { return c ? c->dev_bytes : 0; }
+
+void hz_destroy(hz_ctx *c) {
+    if (!c) return;
+    for (auto &kv : c->allocs) cudaFree(kv.first);
+    c->kt_open.clear();
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
+    c->allocs.clear();
+    if (c->w64) {
+        if (c->w64->hhost) cudaFreeHost(c->w64->hhost);
+        if (c->w64->rhost) cudaFreeHost(c->w64->rhost);
+    }
+    if (c->w32) {
+        if (c->w32->hhost) cudaFreeHost(c->w32->hhost);
+        if (c->w32->rhost) cudaFreeHost(c->w32->rhost);
+    }
+    delete c;
+}
+
+const char *hz_last_error(const hz_ctx *c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

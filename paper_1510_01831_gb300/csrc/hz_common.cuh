@@ -1,0 +1,170 @@
+// Shared types and device helpers of the CUDA path (complex arithmetic,
+// problem descriptors, kernel declarations).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace hz {
+
+// ------------------------------------------------------------ complex ---
+template <class T> struct cx;
+template <> struct cx<double> { using t = double2; };
+template <> struct cx<float> { using t = float2; };
+
+__host__ __device__ inline double2 mk(double a, double b) { return make_double2(a, b); }
+__host__ __device__ inline float2 mk(float a, float b) { return make_float2(a, b); }
+
+__host__ __device__ inline double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 operator*(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__host__ __device__ inline float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline float2 operator*(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+
+// acc += a * b with fused multiply-adds
+__device__ __forceinline__ void cmac(double2 &acc, double2 a, double2 b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
+    // Smith's algorithm for a / b
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+__host__ __device__ inline double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+template <class T2> __device__ __forceinline__ T2 czero();
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ double2 to2(double2 a, double2) { return a; }
+__device__ __forceinline__ float2 to2(double2 a, float2) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to2(float2 a, double2) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ float2 to2(float2 a, float2) { return a; }
+
+// ------------------------------------------------------- descriptors ---
+// One cell (l, c) of the nested decomposition.  Local arrays are row-major
+// [nz][nx] with nz = n + 2p rows and nx = w + 2p columns; local array column
+// jx maps to global array column t + jx, local row jz to global row s + jz.
+struct CellDesc {
+    int l, c;
+    int top, bot, left, right;  // neighbour flags: layer above/below, cell left/right
+    int nx, nz;          // extended cell size
+    int w, n;            // interior columns / rows
+    int t, s;            // global interior column / row offsets (t_c, s_l)
+    int own_lo, no;      // owned local columns [own_lo, own_lo + no)
+    int row_lo, row_hi;  // owned local rows [row_lo, row_hi) of the layer
+    long long vol_off;   // cell volume buffer offset (in grid points; x B for RHS-major)
+    long long w_off;     // block-tridiagonal inverse blocks: nz blocks of nx*nx
+    long long cz_off;    // z-couplings between consecutive rows: (nz-1) x nx
+    long long F_off;     // F: (2 nz) x (4 no)
+    long long E_off;     // E: (4 no) x (4 nz)
+    long long S_off;     // S: (4 no) x (4 no)
+    long long K_off;     // K (offline only): (2 nz) x (4 nz)
+};
+
+// One layer: its inner SIE over the C-1 cell interfaces.
+struct LayerDesc {
+    int n, nz, s, C;
+    int row_lo, row_hi;
+    int cell0;           // index of its first cell
+    long long inner_off; // inner vector offset: (C+1) slots of 2 nz (slot 0 and C are zero pads)
+    long long W_off;     // C-1 blocks (2nz)^2
+    long long Z_off;     // C-1 blocks nz x 2nz (slot 0 unused)
+    long long V_off;     // C-1 blocks (2nz)^2 (last unused)
+};
+
+// Batched, segmented complex GEMM problem:  Y (+)= alpha (A X + A2 X2)
+//   A : M x K row-major (lda); A2 : M x K2 (lda2), optional (K2 = 0)
+//   X row k lives at X[k / xseg] + (k % xseg) * ldx (N contiguous entries)
+//   Y row m lives at Y[m / yseg] + (m % yseg) * ldy
+template <class T2> struct GemmProb {
+    const T2 *A;
+    long long lda;
+    int M, K, N;
+    int xseg, yseg;
+    long long ldx, ldy;
+    const T2 *X[4];
+    T2 *Y[4];
+    int beta;     // 0 overwrite, 1 accumulate
+    float alpha;  // real scale
+    const T2 *A2;
+    long long lda2;
+    int K2, xseg2;
+    long long ldx2;
+    const T2 *X2[4];
+};
+
+// ------------------------------------------------------------ errors ---
+struct Err {
+    int code = 0;
+    std::string msg;
+};
+
+#define HZ_CU(call)                                                                  \
+    do {                                                                             \
+        cudaError_t e_ = (call);                                                     \
+        if (e_ != cudaSuccess) {                                                     \
+            throw hz::CudaError(e_, #call, __FILE__, __LINE__);                      \
+        }                                                                            \
+    } while (0)
+
+struct CudaError {
+    cudaError_t e;
+    std::string what;
+    CudaError(cudaError_t e_, const char *call, const char *file, int line) : e(e_) {
+        char b[512];
+        snprintf(b, sizeof b, "%s failed: %s (%s:%d)", call, cudaGetErrorString(e_), file, line);
+        what = b;
+    }
+};
+struct HzError {
+    int code;
+    std::string what;
+    HzError(int c, const std::string &w) : code(c), what(w) {}
+};
+
+// ------------------------------------------------- kernel launchers ---
+// (defined in hz_kernels.cu; all launch on `st` and count launches in *nl)
+template <class T2>
+void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, cudaStream_t st, int *nl);
+
+template <class T2>
+void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B,
+                       int max_nx, cudaStream_t st, int *nl);
+
+template <class T2>
+void launch_inner_chain(const LayerDesc *d_layers, const int *d_layer_ids, int nlayer, const T2 *W,
+                        const T2 *Z, const T2 *V, T2 *inner, int B, int max_nz2, cudaStream_t st, int *nl);
+
+// offline (FP64)
+void launch_cell_coeffs(const CellDesc *d_cells, int ncell, const double *m, int NX, double omega, double h,
+                        double C, int p, double2 *diag, double2 *cx, double2 *cz, cudaStream_t st, int *nl);
+void launch_cell_factor(const CellDesc *d_cells, int ncell, const double2 *diag, const double2 *cx,
+                        const double2 *cz, double2 *W, int max_nx, int *d_info, cudaStream_t st, int *nl);
+void launch_gj_inverse(double2 *const *d_mats, const int *d_n, int nmat, int max_n, int *d_info,
+                       cudaStream_t st, int *nl);
+
+}  // namespace hz

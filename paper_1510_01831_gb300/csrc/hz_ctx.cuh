@@ -1,0 +1,132 @@
+// Solver context: problem description, decomposition descriptors, device
+// operators and workspaces.  Internal to the library.
+#pragma once
+#include <map>
+#include <memory>
+
+#include "../../include/hz.h"
+#include "hz_common.cuh"
+
+namespace hz {
+
+// Online operators in one precision (T2 = double2 or float2).
+template <class T2> struct Ops {
+    T2 *cellW = nullptr;  // per cell: nz blocks of nx*nx (inverted Schur complements)
+    T2 *cz = nullptr;     // per cell: z couplings (nz x nx, last row unused)
+    T2 *F = nullptr, *E = nullptr, *S = nullptr;
+    T2 *W = nullptr, *Z = nullptr, *V = nullptr;  // inner block LU
+};
+
+// Problem lists of batched GEMMs, kept on the device (built once per workspace).
+template <class T2> struct ProbList {
+    GemmProb<T2> *d = nullptr;
+    int n = 0, max_tiles = 0;
+    double bytes = 0, flops = 0;  // algorithmic traffic and real flops of one launch
+};
+
+// Workspace for one batch width B, in the working precision T2.
+template <class T2> struct Work {
+    int B = 0;
+    T2 *vol = nullptr;     // cell volumes [tot_vol][B]: Newton potentials
+    T2 *vol2 = nullptr;    // cell volumes for the reconstruction solve
+    T2 *inner = nullptr;   // inner vectors [tot_inner][B]
+    T2 *inner2 = nullptr;  // inner vectors [tot_inner][2B] (polarized operator, two input sets)
+    T2 *inner_f = nullptr; // inner right-hand side of the Newton potentials (saved)
+    T2 *lin = nullptr;     // layer-application inputs  [L][4][T][2B]
+    T2 *lout = nullptr;    // layer-application outputs [L][4][T][2B]
+    T2 *pa = nullptr, *pb = nullptr, *pc = nullptr;  // polarized vectors [K][4][T][B]
+    T2 *Z = nullptr;       // FGMRES preconditioned basis [m][n_tr][B]
+    // FP64 buffers
+    double2 *V = nullptr;      // Arnoldi basis [m+1][n_tr][B]
+    double2 *w64 = nullptr;    // [n_tr][B]
+    double2 *rhs64 = nullptr;  // [n_tr][B]
+    double2 *x64 = nullptr;    // [n_tr][B]
+    double *dots = nullptr;    // reduction scratch
+    double *hbuf = nullptr;    // [m+2][B] complex as 2 doubles
+    double *hhost = nullptr;   // pinned mirror
+    double2 *gsrc = nullptr;   // symmetric-form source / residual [NZ*NX][B]
+    double2 *u = nullptr;      // FP64 solution [NZ*NX][B]
+    double2 *io = nullptr;     // batch-outer staging [B][NZ*NX]
+    double *rnorm = nullptr;   // [B] norms
+    double *rhost = nullptr;   // pinned [4B]
+    int restart = 0;
+    // precomputed problem lists
+    ProbList<T2> f_full, es_bot_A, es_top_B;  // apply_M (all layers)
+    std::vector<ProbList<T2>> f_down, es_down; // per sweep step
+    std::vector<ProbList<T2>> f_up, es_up;
+    ProbList<T2> f_refl, es_refl;               // reflections (all layers)
+    ProbList<T2> f_rec, e_newton;              // reconstruction F-step, Newton E-step
+    std::vector<ProbList<T2>> f_layer, es_layer; // single-layer (component API)
+};
+
+}  // namespace hz
+
+struct hz_ctx {
+    // problem
+    int n_x = 0, n_z = 0, p = 0, L = 0, C = 0;
+    double omega = 0, h = 0, pml_C = 0;
+    int NX = 0, NZ = 0;
+    hz_opts opts{};
+    std::vector<int> rows, cols;
+    cudaStream_t st = nullptr;
+    std::string err;
+    bool factored = false;
+    int nl = 0;  // kernel launches counter for the current call
+    // decomposition
+    std::vector<hz::CellDesc> cells;
+    std::vector<hz::LayerDesc> layers;
+    hz::CellDesc *d_cells = nullptr;
+    hz::LayerDesc *d_layers = nullptr;
+    int *d_layer_ids = nullptr;  // 0..L-1
+    long long tot_vol = 0, tot_W = 0, tot_F = 0, tot_E = 0, tot_S = 0, tot_K = 0;
+    long long tot_inner = 0, tot_Wi = 0, tot_Z = 0, tot_V = 0;
+    int max_nx = 0, max_nz = 0, max_no = 0;
+    // global medium and PML profiles (FP64)
+    double *d_m = nullptr;
+    double2 *d_ax = nullptr, *d_axh = nullptr, *d_az = nullptr, *d_azh = nullptr;
+    // operators
+    hz::Ops<double2> o64;
+    hz::Ops<float2> o32;
+    std::unique_ptr<hz::Work<double2>> w64;
+    std::unique_ptr<hz::Work<float2>> w32;
+    // kernel timing (opts.time_kernels): event pairs per hot-kernel class
+    struct KT {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes, flops;
+    };
+    std::vector<KT> kt_open;
+    std::vector<cudaEvent_t> ev_pool;
+    int kt_launches[3] = {0, 0, 0};
+    double kt_ms[3] = {0, 0, 0}, kt_bytes[3] = {0, 0, 0}, kt_flops[3] = {0, 0, 0};
+    cudaEvent_t ev_get();
+    void kt_begin(int cls, double bytes, double flops);
+    void kt_end();
+    void kt_collect();  // synchronises; folds open event pairs into kt_*
+    void kt_reset();
+    // host<->device staging of user arrays
+    double2 *stage = nullptr;
+    long long stage_n = 0;
+    int *d_flag = nullptr;
+    // allocations
+    std::map<void *, size_t> allocs;
+    long long dev_bytes = 0;
+
+    void *dalloc(size_t bytes);
+    void dfree(void *p);
+    bool mixed() const { return opts.precision == HZ_MIXED; }
+    long long n_tr() const { return 4LL * (L - 1) * NX; }
+};
+
+namespace hz {
+void build_decomposition(hz_ctx *c);
+void factor_all(hz_ctx *c);
+void init_global_alpha(hz_ctx *c);
+template <class T2> int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st, bool scale_src);
+template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev, int B, double2 *x_dev);
+template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_dev, int mask, int B, double2 *out_dev);
+template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, int B, double2 *y_dev);
+template <class T2> void comp_residual(hz_ctx *c, const double2 *u_dev, const double2 *f_dev, int B, double *res_host);
+template <class T2> Ops<T2> &ops(hz_ctx *c);
+template <class T2> Work<T2> &work(hz_ctx *c, int B);
+}  // namespace hz

@@ -1,0 +1,1361 @@
+// Online stage: Alg. matrix_free_solver with the nested inner solver.
+//   1. Newton potentials: cell solves (local solves), inner sweeps, samples.
+//   2. FGMRES on the polarized traces (eq. integral_polarized) with P^GS
+//      (eq. preconditioner_GS): matrix-free M (Alg. applyM generalised to the
+//      polarized system), downward / upward sweeps and upward reflections.
+//   3. Reconstruction of the volume from the traces.
+//   4. FP64 residual of the global system; refinement passes repeat 1-3 on it.
+// Every layer Green's integral is applied through eq. (factorization):
+//   F (M_f) -> inner block-LU sweeps ((M^l)^{-1}) -> E and S (M_u).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "hz_ctx.cuh"
+
+namespace hz {
+
+template <> Ops<double2> &ops<double2>(hz_ctx *c) { return c->o64; }
+template <> Ops<float2> &ops<float2>(hz_ctx *c) { return c->o32; }
+
+static inline int grid1(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 65535LL * 8); }
+
+// ----------------------------------------------------------- kernels ---
+__device__ inline double2 pml_alpha_s(double k, int nint, int p, double h, double C, double omega) {
+    double x = k * h, Lx = (nint + 1) * h, delta = p * h, d = 0.0;
+    if (x < 0.0)
+        d = -x;
+    else if (x > Lx)
+        d = x - Lx;
+    double sig = 0.0;
+    if (d > 0.0 && p > 0) {
+        double r = d / delta;
+        sig = (C / delta) * r * r;
+    }
+    double s = sig / omega, den = 1.0 + s * s;
+    return make_double2(1.0 / den, -s / den);
+}
+
+// global alpha at nodes (n entries) and half nodes (n+1 entries, index i = position i - 1/2)
+__global__ void k_global_alpha(int NX, int NZ, int nxi, int nzi, int p, double h, double C, double omega, double2 *ax,
+                               double2 *axh, double2 *az, double2 *azh) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= NX) {
+        if (i < NX) ax[i] = pml_alpha_s(i - p + 1.0, nxi, p, h, C, omega);
+        axh[i] = pml_alpha_s(i - p + 0.5, nxi, p, h, C, omega);
+    }
+    if (i <= NZ) {
+        if (i < NZ) az[i] = pml_alpha_s(i - p + 1.0, nzi, p, h, C, omega);
+        azh[i] = pml_alpha_s(i - p + 0.5, nzi, p, h, C, omega);
+    }
+}
+
+// f [B][N] (batch outer) -> fs [N][B] = f / (alpha_x alpha_z): the row-scaled source
+__global__ void k_src_in(const double2 *__restrict__ f, double2 *fs, const double2 *__restrict__ ax,
+                         const double2 *__restrict__ az, int NX, long long N, int B, int scale) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * B; e += (long long)gridDim.x * blockDim.x) {
+        long long g = e / B;
+        int b = (int)(e % B);
+        double2 v = f[(long long)b * N + g];
+        if (scale) v = cdiv(v, ax[g % NX] * az[g / NX]);
+        fs[e] = v;
+    }
+}
+
+// u [N][B] -> out [B][N]
+__global__ void k_out(const double2 *__restrict__ u, double2 *out, long long N, int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * B; e += (long long)gridDim.x * blockDim.x) {
+        long long g = e % N;
+        int b = (int)(e / N);
+        out[e] = u[g * B + b];
+    }
+}
+
+// r = fs - H_s u  (row-scaled operator on the global box) and per-RHS partial
+// sums of |alpha_x alpha_z r|^2 = |(H u - f)_{Appendix A}|^2 (and |alpha f_s|^2 when fnorm)
+__global__ void k_residual(const double2 *__restrict__ u, const double2 *__restrict__ fs, double2 *r,
+                           const double *__restrict__ m, const double2 *__restrict__ ax, const double2 *__restrict__ axh,
+                           const double2 *__restrict__ az, const double2 *__restrict__ azh, int NX, int NZ, double h,
+                           double omega, int B, double *part, int nchunk, int mode) {
+    // mode 0: residual + norm; mode 1: norm of fs only (no r written)
+    const int b = blockIdx.y * 32 + threadIdx.x;
+    const long long N = (long long)NX * NZ;
+    const long long chunk = (N + nchunk - 1) / nchunk;
+    const long long g0 = blockIdx.x * chunk, g1 = min(N, g0 + chunk);
+    double acc = 0.0;
+    const double ih2 = 1.0 / (h * h);
+    if (b < B) {
+        for (long long g = g0 + threadIdx.y; g < g1; g += blockDim.y) {
+            int iz = (int)(g / NX), ix = (int)(g % NX);
+            double2 a_x = ax[ix], a_z = az[iz];
+            double2 D = a_x * a_z;
+            double2 v;
+            if (mode == 0) {
+                double2 axp = axh[ix + 1], axm = axh[ix], azp = azh[iz + 1], azm = azh[iz];
+                double2 cxp = cdiv(axp, a_z), cxm = cdiv(axm, a_z), czp = cdiv(azp, a_x), czm = cdiv(azm, a_x);
+                double2 uc = u[g * B + b];
+                double2 Hu = (cxp + cxm + czp + czm) * uc;
+                if (ix > 0) Hu = Hu - cxm * u[(g - 1) * B + b];
+                if (ix < NX - 1) Hu = Hu - cxp * u[(g + 1) * B + b];
+                if (iz > 0) Hu = Hu - czm * u[(g - NX) * B + b];
+                if (iz < NZ - 1) Hu = Hu - czp * u[(g + NX) * B + b];
+                Hu = ih2 * Hu - cdiv(make_double2(omega * omega * m[g], 0.0), D) * uc;
+                v = fs[g * B + b] - Hu;
+                r[g * B + b] = v;
+            } else {
+                v = fs[g * B + b];
+            }
+            acc += cabs2(D * v);
+        }
+    }
+    __shared__ double red[8][33];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && b < B) {
+        double s = 0;
+        for (int y = 0; y < blockDim.y; y++) s += red[y][threadIdx.x];
+        part[(long long)blockIdx.x * B + b] = s;
+    }
+}
+
+__global__ void k_reduce_parts(const double *__restrict__ part, int nchunk, int width, double *out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= width) return;
+    double s = 0;
+    for (int c = 0; c < nchunk; c++) s += part[(long long)c * width + i];
+    out[i] = s;
+}
+
+// symmetric-form global source [N][B] -> cell volumes (owned region only)
+template <class T2>
+__global__ void k_scatter(const CellDesc *__restrict__ cells, const double2 *__restrict__ g, T2 *vol, int NX, int B) {
+    const CellDesc &cd = cells[blockIdx.y];
+    const long long n = (long long)cd.nx * cd.nz * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long pt = e / B;
+        int b = (int)(e % B);
+        int jz = (int)(pt / cd.nx), jx = (int)(pt % cd.nx);
+        T2 v = czero<T2>();
+        if (jz >= cd.row_lo && jz < cd.row_hi && jx >= cd.own_lo && jx < cd.own_lo + cd.no)
+            v = to2(g[((long long)(cd.s + jz) * NX + cd.t + jx) * B + b], T2{});
+        vol[cd.vol_off * B + e] = v;
+    }
+}
+
+// inner right-hand side from the cell Newton potentials: interface j gets the
+// potential of cell j at its column node w (a-half) and of cell j+1 at column
+// node 1 (b-half)
+template <class T2>
+__global__ void k_gather_inner(const LayerDesc *__restrict__ layers, const CellDesc *__restrict__ cells,
+                               const T2 *__restrict__ vol, T2 *inner, int B, int p) {
+    const LayerDesc &ld = layers[blockIdx.y];
+    const int nz = ld.nz, J = ld.C - 1;
+    const long long n = (long long)J * 2 * nz * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        long long q = e / B;
+        int m = (int)(q % (2 * nz)), j = (int)(q / (2 * nz));
+        T2 v;
+        if (m < nz) {
+            const CellDesc &ca = cells[ld.cell0 + j];
+            v = vol[(ca.vol_off + (long long)m * ca.nx + p + ca.w - 1) * B + b];
+        } else {
+            const CellDesc &cb = cells[ld.cell0 + j + 1];
+            v = vol[(cb.vol_off + (long long)(m - nz) * cb.nx + p) * B + b];
+        }
+        inner[(ld.inner_off + (long long)(j + 1) * 2 * nz + m) * B + b] = v;
+    }
+}
+
+// Newton potential samples at local rows (0, 1, n, n+1) of every layer, owned columns:
+// out [L][4][NX][B]
+template <class T2>
+__global__ void k_samples(const CellDesc *__restrict__ cells, const T2 *__restrict__ vol, T2 *out, int NX, int B,
+                          int p) {
+    const CellDesc &cd = cells[blockIdx.y];
+    const long long n = 4LL * cd.no * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        long long q = e / B;
+        int o = (int)(q % cd.no), rho = (int)(q / cd.no);
+        int jz = rho == 0 ? p - 1 : (rho == 1 ? p : (rho == 2 ? p + cd.n - 1 : p + cd.n));
+        int jx = cd.own_lo + o;
+        out[(((long long)cd.l * 4 + rho) * NX + cd.t + jx) * B + b] = vol[(cd.vol_off + (long long)jz * cd.nx + jx) * B + b];
+    }
+}
+
+// polarized right-hand side: interface k gets rows n, n+1 of layer k (d-part)
+// and rows 0, 1 of layer k+1 (u-part)
+template <class T2>
+__global__ void k_pol_rhs(const T2 *__restrict__ s, double2 *rhs, int K, int NX, int B) {
+    const long long n = (long long)K * 4 * NX * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long xb = e % ((long long)NX * B);
+        long long q = e / ((long long)NX * B);
+        int comp = (int)(q % 4), k = (int)(q / 4);
+        int l = comp < 2 ? k : k + 1;
+        int rho = comp == 0 ? 2 : (comp == 1 ? 3 : (comp == 2 ? 0 : 1));
+        rhs[e] = to2(s[((long long)l * 4 + rho) * NX * B + xb], double2{});
+    }
+}
+
+// Stage the two input sets of M for every layer (columns [0,B): set A, [B,2B): set B):
+//   set A (rows n, n+1 out): top = d+u of interface l-1, bottom = u of interface l
+//   set B (rows 0, 1 out)  : top = d of interface l-1,   bottom = u+d of interface l
+template <class T2>
+__global__ void k_stage_M(const T2 *__restrict__ x, T2 *lin, int L, int NX, int B) {
+    const long long n = (long long)L * 4 * NX * 2 * B;
+    const long long rowsz = (long long)NX * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int col = (int)(e % (2 * B));
+        long long q = e / (2 * B);
+        int xi = (int)(q % NX);
+        q /= NX;
+        int rho = (int)(q % 4), l = (int)(q / 4);
+        int set = col >= B, b = col - set * B;
+        T2 v = czero<T2>();
+        if (rho < 2 && l > 0) {
+            const T2 *I = x + (long long)(l - 1) * 4 * rowsz + (long long)xi * B + b;
+            v = I[rho * rowsz];                           // d_a or d_b
+            if (!set) v = v + I[(2 + rho) * rowsz];       // + u
+        } else if (rho >= 2 && l < L - 1) {
+            const T2 *I = x + (long long)l * 4 * rowsz + (long long)xi * B + b;
+            v = I[rho * rowsz];                           // u_a or u_b
+            if (set) v = v + I[(rho - 2) * rowsz];        // + d
+        }
+        lin[e] = v;
+    }
+}
+
+// y = M x from the sampled layer fields (jump_2, jump_4 for the d-rows,
+// jump_3, jump_1 for the u-rows), written in FP64
+template <class T2>
+__global__ void k_combine_M(const T2 *__restrict__ x, const T2 *__restrict__ lout, double2 *y, int L, int NX, int B) {
+    const int K = L - 1;
+    const long long rowsz = (long long)NX * B;
+    const long long n = (long long)K * 4 * rowsz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long xb = e % rowsz;
+        int xi = (int)(xb / B), b = (int)(xb % B);
+        long long q = e / rowsz;
+        int comp = (int)(q % 4), k = (int)(q / 4);
+        const T2 *I = x + (long long)k * 4 * rowsz + xb;
+        double2 da = to2(I[0], double2{}), db = to2(I[rowsz], double2{});
+        double2 ua = to2(I[2 * rowsz], double2{}), ub = to2(I[3 * rowsz], double2{});
+        double2 v;
+        if (comp < 2) {  // layer k, set A (columns 0..B), rows n (2), n+1 (3)
+            double2 s = to2(lout[(((long long)k * 4 + 2 + comp) * NX + xi) * 2 * B + b], double2{});
+            v = comp == 0 ? (da + ua) - s : db - s;
+        } else {         // layer k+1, set B (columns B..2B), rows 0, 1
+            double2 t = to2(lout[(((long long)(k + 1) * 4 + comp - 2) * NX + xi) * 2 * B + B + b], double2{});
+            v = comp == 2 ? ua - t : (ub + db) - t;
+        }
+        y[e] = v;
+    }
+}
+
+// w = v_u - L d with L d = [-t0, d_b - t1]: here only the -d_b part (t added by the E/S step)
+template <class T2>
+__global__ void k_gs_fix(T2 *x, int K, int NX, int B) {
+    const long long rowsz = (long long)NX * B;
+    const long long n = (long long)K * rowsz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long xb = e % rowsz;
+        int k = (int)(e / rowsz);
+        T2 *I = x + (long long)k * 4 * rowsz + xb;
+        I[3 * rowsz] = I[3 * rowsz] - I[rowsz];
+    }
+}
+
+// -L d -> L d in the u-part, d-part cleared
+template <class T2>
+__global__ void k_refl_finish(T2 *x, int K, int NX, int B) {
+    const long long rowsz = (long long)NX * B;
+    const long long n = (long long)K * rowsz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long xb = e % rowsz;
+        int k = (int)(e / rowsz);
+        T2 *I = x + (long long)k * 4 * rowsz + xb;
+        I[2 * rowsz] = czero<T2>() - I[2 * rowsz];
+        I[3 * rowsz] = czero<T2>() - I[3 * rowsz];
+        I[0] = czero<T2>();
+        I[rowsz] = czero<T2>();
+    }
+}
+
+// traces of the interfaces: tr[k][a|b] = d + u  ([K][2][NX][B])
+template <class T2>
+__global__ void k_traces(const double2 *__restrict__ x, T2 *tr, int K, int NX, int B) {
+    const long long rowsz = (long long)NX * B;
+    const long long n = (long long)K * 2 * rowsz;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        long long xb = e % rowsz;
+        long long q = e / rowsz;
+        int ab = (int)(q % 2), k = (int)(q / 2);
+        const double2 *I = x + (long long)k * 4 * rowsz + xb;
+        tr[e] = to2(I[ab * rowsz] + I[(2 + ab) * rowsz], T2{});
+    }
+}
+
+// reconstruction source of every cell: outer interface forcing on rows
+// (0,1,n,n+1) x owned columns from the traces, inner interface forcing on
+// columns (0,1,w,w+1) from the inner traces (Appendix C forcing, both levels)
+template <class T2>
+__global__ void k_recon_src(const CellDesc *__restrict__ cells, const LayerDesc *__restrict__ layers,
+                            const T2 *__restrict__ tr, const T2 *__restrict__ inner, T2 *vol2, int L, int NX, int B,
+                            int p, double h, double Cp, double omega) {
+    const CellDesc &cd = cells[blockIdx.y];
+    const LayerDesc &ld = layers[cd.l];
+    const int nx = cd.nx, nz = cd.nz;
+    const long long rowsz = (long long)NX * B;
+    const double h2 = h * h;
+    const long long n = (long long)nx * nz * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        long long pt = e / B;
+        int jz = (int)(pt / nx), jx = (int)(pt % nx);
+        double2 v = make_double2(0.0, 0.0);
+        // outer rows: source row node 0 <- +gamma t(row 1), node 1 <- -gamma t(row 0),
+        // node n <- -gamma t(row n+1), node n+1 <- +gamma t(row n)
+        if (jx >= cd.own_lo && jx < cd.own_lo + cd.no) {
+            const int r0 = p - 1, r1 = p, rn = p + cd.n - 1, rn1 = p + cd.n;
+            if (jz == r0 || jz == r1 || jz == rn || jz == rn1) {
+                double2 ax = pml_alpha_s(jx - p + 1.0, cd.w, p, h, Cp, omega);
+                double2 gam = cdiv(make_double2(-1.0, 0.0), h2 * ax);
+                const long long gx = (long long)(cd.t + jx) * B + b;
+                double2 s = make_double2(0.0, 0.0);
+                if (cd.l > 0) {  // top pair: interface l-1
+                    const T2 *I = tr + (long long)(cd.l - 1) * 2 * rowsz + gx;
+                    if (jz == r0) s = s + to2(I[rowsz], double2{});
+                    if (jz == r1) s = s - to2(I[0], double2{});
+                }
+                if (cd.l < L - 1) {  // bottom pair: interface l
+                    const T2 *I = tr + (long long)cd.l * 2 * rowsz + gx;
+                    if (jz == rn) s = s - to2(I[rowsz], double2{});
+                    if (jz == rn1) s = s + to2(I[0], double2{});
+                }
+                v = v + gam * s;
+            }
+        }
+        const int c0 = p - 1, c1 = p, cw = p + cd.w - 1, cw1 = p + cd.w;
+        if (jx == c0 || jx == c1 || jx == cw || jx == cw1) {
+            double2 az = pml_alpha_s(jz - p + 1.0, cd.n, p, h, Cp, omega);
+            double2 beta = cdiv(make_double2(-1.0, 0.0), h2 * az);
+            const long long n2 = 2LL * nz;
+            const T2 *Il = inner + (ld.inner_off + (long long)cd.c * n2) * B;        // interface c-1 (slot c)
+            const T2 *Ir = inner + (ld.inner_off + (long long)(cd.c + 1) * n2) * B;  // interface c (slot c+1)
+            double2 s = make_double2(0.0, 0.0);
+            if (jx == c0) s = s + to2(Il[((long long)nz + jz) * B + b], double2{});   // + x_{c-1,b}
+            if (jx == c1) s = s - to2(Il[(long long)jz * B + b], double2{});          // - x_{c-1,a}
+            if (jx == cw) s = s - to2(Ir[((long long)nz + jz) * B + b], double2{});   // - x_{c,b}
+            if (jx == cw1) s = s + to2(Ir[(long long)jz * B + b], double2{});         // + x_{c,a}
+            v = v + beta * s;
+        }
+        vol2[cd.vol_off * B + e] = to2(v, T2{});
+    }
+}
+
+// u += Newton potential + interface response on the owned region of every cell
+template <class T2>
+__global__ void k_accum_u(const CellDesc *__restrict__ cells, const T2 *__restrict__ vol, const T2 *__restrict__ vol2,
+                          double2 *u, int NX, int B) {
+    const CellDesc &cd = cells[blockIdx.y];
+    const int rows = cd.row_hi - cd.row_lo;
+    const long long n = (long long)rows * cd.no * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        long long q = e / B;
+        int jx = cd.own_lo + (int)(q % cd.no), jz = cd.row_lo + (int)(q / cd.no);
+        long long o = (cd.vol_off + (long long)jz * cd.nx + jx) * B + b;
+        long long g = ((long long)(cd.s + jz) * NX + cd.t + jx) * B + b;
+        u[g] = u[g] + to2(vol[o] + vol2[o], double2{});
+    }
+}
+
+template <class TA, class TB>
+__global__ void k_cast(const TA *__restrict__ a, TB *b, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = to2(a[i], TB{});
+}
+
+// ---- FGMRES helpers (FP64) ----
+// partial[i][chunk][b] = sum over the chunk of conj(V_i) w
+__global__ void k_dots(const double2 *__restrict__ V, long long vstride, const double2 *__restrict__ w, long long n,
+                       int B, int nchunk, double2 *part) {
+    const int i = blockIdx.z;
+    const int b = blockIdx.y * 32 + threadIdx.x;
+    const long long chunk = (n + nchunk - 1) / nchunk;
+    const long long x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
+    double2 acc = make_double2(0.0, 0.0);
+    if (b < B) {
+        const double2 *Vi = V + i * vstride;
+        for (long long x = x0 + threadIdx.y; x < x1; x += blockDim.y) {
+            double2 a = Vi[x * B + b], c = w[x * B + b];
+            acc.x += a.x * c.x + a.y * c.y;
+            acc.y += a.x * c.y - a.y * c.x;
+        }
+    }
+    __shared__ double2 red[8][33];
+    red[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && b < B) {
+        double2 s = make_double2(0.0, 0.0);
+        for (int y = 0; y < blockDim.y; y++) s = s + red[y][threadIdx.x];
+        part[((long long)i * nchunk + blockIdx.x) * B + b] = s;
+    }
+}
+
+// h[i][b] (+)= sum over chunks
+__global__ void k_dots_final(const double2 *__restrict__ part, int nchunk, int B, int nvec, double2 *h, int accum) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nvec * B) return;
+    int i = e / B, b = e % B;
+    double2 s = make_double2(0.0, 0.0);
+    for (int c = 0; c < nchunk; c++) s = s + part[((long long)i * nchunk + c) * B + b];
+    h[e] = accum ? h[e] + s : s;
+}
+
+// w -= sum_i V_i h[i]   (coefficients hc[i][b])
+__global__ void k_axpy_multi(const double2 *__restrict__ V, long long vstride, const double2 *__restrict__ hc, int nvec,
+                             double2 *w, long long n, int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        double2 s = w[e];
+        for (int i = 0; i < nvec; i++) s = s - V[i * vstride + e] * hc[i * B + b];
+        w[e] = s;
+    }
+}
+
+// out = w * scale[b]
+__global__ void k_scale(const double2 *__restrict__ w, const double *__restrict__ scale, double2 *out, long long n,
+                        int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x)
+        out[e] = scale[e % B] * w[e];
+}
+
+// x += sum_j Z_j y[j][b]
+template <class T2>
+__global__ void k_update_x(const T2 *__restrict__ Z, long long zstride, const double2 *__restrict__ y, int nvec,
+                           double2 *x, long long n, int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
+        int b = (int)(e % B);
+        double2 s = x[e];
+        for (int j = 0; j < nvec; j++) s = s + to2(Z[j * zstride + e], double2{}) * y[j * B + b];
+        x[e] = s;
+    }
+}
+
+// r = b - w
+__global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__ w, double2 *r, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        r[e] = a[e] - w[e];
+}
+
+// ------------------------------------------------- problem-list build ---
+template <class T2> struct ListBuilder {
+    hz_ctx *c;
+    Ops<T2> &o;
+    std::vector<GemmProb<T2>> v;
+    int max_tiles = 0;
+    ListBuilder(hz_ctx *c_, Ops<T2> &o_) : c(c_), o(o_) {}
+
+    double bytes = 0, flops = 0;
+    void push(const GemmProb<T2> &g) {
+        v.push_back(g);
+        max_tiles = std::max(max_tiles, ((g.M + 63) / 64) * ((g.N + 31) / 32));
+        const double es = sizeof(T2);
+        const double K = (double)g.K + g.K2;
+        bytes += es * ((double)g.M * K + K * g.N + (double)g.M * g.N * (g.beta ? 2 : 1));
+        flops += 8.0 * g.M * K * g.N;
+    }
+    // F-step of layer l: inputs (row q of the layer's 4 trace rows at in[q], global
+    // column 0, ld) -> inner right-hand sides (inner buffer with ld ldi, column offset coff)
+    void add_F(int l, int mask, const T2 *const in[4], long long ld, int N, T2 *inner, long long ldi, int beta) {
+        const LayerDesc &ld_ = c->layers[l];
+        const int nz = ld_.nz;
+        for (int cc = 0; cc < c->C; cc++) {
+            const CellDesc &cd = c->cells[ld_.cell0 + cc];
+            const int no = cd.no;
+            const long long ocol = (long long)(cd.t + cd.own_lo) * ld;
+            for (int t = 0; t < 2; t++) {
+                int slot;
+                long long roff;
+                if (t == 0) {
+                    if (cc == 0) continue;
+                    slot = cc;        // interface c-1, b-half
+                    roff = nz;
+                } else {
+                    if (cc == c->C - 1) continue;
+                    slot = cc + 1;    // interface c, a-half
+                    roff = 0;
+                }
+                GemmProb<T2> g{};
+                int q0 = (mask & 1) ? 0 : 2, nq = ((mask & 1) ? 2 : 0) + ((mask & 2) ? 2 : 0);
+                g.A = o.F + cd.F_off + (long long)t * nz * 4 * no + (long long)q0 * no;
+                g.lda = 4LL * no;
+                g.M = nz;
+                g.K = nq * no;
+                g.N = N;
+                g.xseg = no;
+                g.ldx = ld;
+                for (int q = 0; q < nq; q++) g.X[q] = in[q0 + q] + ocol;
+                g.yseg = 1 << 30;
+                g.ldy = ldi;
+                g.Y[0] = inner + (ld_.inner_off + (long long)slot * 2 * nz + roff) * ldi;
+                g.beta = beta;
+                g.alpha = 1.f;
+                push(g);
+            }
+        }
+    }
+    // E (+ S) step of layer l: out rows selected by outmask into out[q] (global col 0, ldo);
+    // E reads the inner traces (ld ldi), S the outer inputs (if inmask != 0)
+    void add_ES(int l, int inmask, const T2 *const in[4], long long ld, int outmask, T2 *const out[4], long long ldo,
+                const T2 *inner, long long ldi, int N, int beta) {
+        const LayerDesc &ld_ = c->layers[l];
+        const int nz = ld_.nz;
+        for (int cc = 0; cc < c->C; cc++) {
+            const CellDesc &cd = c->cells[ld_.cell0 + cc];
+            const int no = cd.no;
+            int r0 = (outmask & 1) ? 0 : 2, nr = ((outmask & 1) ? 2 : 0) + ((outmask & 2) ? 2 : 0);
+            GemmProb<T2> g{};
+            g.A = o.E + cd.E_off + (long long)r0 * no * 4 * nz;
+            g.lda = 4LL * nz;
+            g.M = nr * no;
+            g.K = 4 * nz;
+            g.N = N;
+            g.xseg = 1 << 30;
+            g.ldx = ldi;
+            g.X[0] = inner + (ld_.inner_off + (long long)cd.c * 2 * nz) * ldi;
+            g.yseg = no;
+            g.ldy = ldo;
+            const long long ocol_o = (long long)(cd.t + cd.own_lo) * ldo;
+            for (int q = 0; q < nr; q++) g.Y[q] = out[r0 + q] + ocol_o;
+            g.beta = beta;
+            g.alpha = 1.f;
+            if (inmask) {
+                int q0 = (inmask & 1) ? 0 : 2, nq = ((inmask & 1) ? 2 : 0) + ((inmask & 2) ? 2 : 0);
+                g.A2 = o.S + cd.S_off + (long long)r0 * no * 4 * no + (long long)q0 * no;
+                g.lda2 = 4LL * no;
+                g.K2 = nq * no;
+                g.xseg2 = no;
+                g.ldx2 = ld;
+                const long long ocol = (long long)(cd.t + cd.own_lo) * ld;
+                for (int q = 0; q < nq; q++) g.X2[q] = in[q0 + q] + ocol;
+            }
+            push(g);
+        }
+    }
+    ProbList<T2> finish() {
+        ProbList<T2> pl;
+        pl.n = (int)v.size();
+        pl.max_tiles = max_tiles;
+        pl.bytes = bytes;
+        pl.flops = flops;
+        bytes = flops = 0;
+        if (pl.n) {
+            pl.d = (GemmProb<T2> *)c->dalloc(sizeof(GemmProb<T2>) * v.size());
+            HZ_CU(cudaMemcpy(pl.d, v.data(), sizeof(GemmProb<T2>) * v.size(), cudaMemcpyHostToDevice));
+        }
+        v.clear();
+        max_tiles = 0;
+        return pl;
+    }
+};
+
+template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
+    if (!pl.n) return;
+    c->kt_begin(2, pl.bytes, pl.flops);
+    launch_gemm<T2>(pl.d, pl.n, pl.max_tiles, c->st, &c->nl);
+    c->kt_end();
+}
+
+// algorithmic traffic / flops of the chain solves
+template <class T2> static void cell_chain_cost(hz_ctx *c, int N, double &bytes, double &flops) {
+    const double es = sizeof(T2);
+    bytes = flops = 0;
+    for (const CellDesc &cd : c->cells) {
+        const double nx = cd.nx, nz = cd.nz;
+        bytes += es * (2 * nz * nx * nx + 2 * (nz - 1) * nx + 4 * nz * nx * N);
+        flops += 8.0 * (2 * nz - 1) * nx * nx * N;
+    }
+}
+template <class T2> static void inner_chain_cost(hz_ctx *c, int l0, int nl, int N, double &bytes, double &flops) {
+    const double es = sizeof(T2);
+    bytes = flops = 0;
+    for (int l = l0; l < l0 + nl; l++) {
+        const double J = c->C - 1, nz = c->layers[l].nz, n2 = 2 * nz;
+        if (J <= 0) continue;
+        const double ent = J * n2 * n2 + (J - 1) * nz * n2 + (J - 1) * n2 * n2;
+        bytes += es * (ent + 4 * J * n2 * N);
+        flops += 8.0 * ent * N;
+    }
+}
+
+template <class T2> static void cell_chain(hz_ctx *c, T2 *vol, int N) {
+    Ops<T2> &o = ops<T2>(c);
+    double by = 0, fl = 0;
+    if (c->opts.time_kernels) cell_chain_cost<T2>(c, N, by, fl);
+    c->kt_begin(0, by, fl);
+    launch_cell_chain<T2>(c->d_cells, (int)c->cells.size(), o.cellW, o.cz, vol, N, c->max_nx, c->st, &c->nl);
+    c->kt_end();
+}
+
+// ---------------------------------------------------------- workspace ---
+template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
+    Ops<T2> &o = ops<T2>(c);
+    const int L = c->L, K = L - 1, NX = c->NX, B = W.B;
+    const long long rowsz = (long long)NX * B;      // one trace row, B columns
+    const long long rowsz2 = (long long)NX * 2 * B; // one trace row, 2B columns
+    ListBuilder<T2> lb(c, o);
+    auto vec_rows = [&](T2 *base, int k, int comp0) {
+        return base + ((long long)k * 4 + comp0) * rowsz;
+    };
+    // apply M: F from the staged inputs (2B wide), E/S of both sets
+    for (int l = 0; l < L; l++) {
+        const T2 *in[4];
+        for (int q = 0; q < 4; q++) in[q] = W.lin + ((long long)l * 4 + q) * rowsz2;
+        lb.add_F(l, 3, in, 2 * B, 2 * B, W.inner2, 2 * B, 0);
+    }
+    W.f_full = lb.finish();
+    for (int l = 0; l < L; l++) {
+        const T2 *in[4];
+        T2 *out[4];
+        for (int q = 0; q < 4; q++) {
+            in[q] = W.lin + ((long long)l * 4 + q) * rowsz2;
+            out[q] = W.lout + ((long long)l * 4 + q) * rowsz2;
+        }
+        if (l < L - 1) lb.add_ES(l, 3, in, 2 * B, 2, out, 2 * B, W.inner2, 2 * B, B, 0);  // set A -> rows n, n+1
+        if (l > 0) {
+            const T2 *inB[4];
+            T2 *outB[4];
+            for (int q = 0; q < 4; q++) {
+                inB[q] = in[q] + B;
+                outB[q] = out[q] + B;
+            }
+            // set B -> rows 0, 1 (E reads the inner traces of columns B..2B)
+            lb.add_ES(l, 3, inB, 2 * B, 1, outB, 2 * B, W.inner2 + B, 2 * B, B, 0);
+        }
+    }
+    W.es_bot_A = lb.finish();
+    // downward sweep on pb: layer k from the d-part of interface k-1 into the d-part of interface k
+    W.f_down.assign(L, ProbList<T2>());
+    W.es_down.assign(L, ProbList<T2>());
+    for (int k = 1; k <= L - 2; k++) {
+        const T2 *in[4] = {vec_rows(W.pb, k - 1, 0), vec_rows(W.pb, k - 1, 1), nullptr, nullptr};
+        lb.add_F(k, 1, in, B, B, W.inner, B, 0);
+        W.f_down[k] = lb.finish();
+        T2 *out[4] = {nullptr, nullptr, vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1)};
+        lb.add_ES(k, 1, in, B, 2, out, B, W.inner, B, B, 1);
+        W.es_down[k] = lb.finish();
+    }
+    // upward sweep on pb: layer k+1 from the u-part of interface k+1 into the u-part of interface k
+    W.f_up.assign(L, ProbList<T2>());
+    W.es_up.assign(L, ProbList<T2>());
+    for (int k = L - 3; k >= 0; k--) {
+        const T2 *in[4] = {nullptr, nullptr, vec_rows(W.pb, k + 1, 2), vec_rows(W.pb, k + 1, 3)};
+        lb.add_F(k + 1, 2, in, B, B, W.inner, B, 0);
+        W.f_up[k] = lb.finish();
+        T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
+        lb.add_ES(k + 1, 2, in, B, 1, out, B, W.inner, B, B, 1);
+        W.es_up[k] = lb.finish();
+    }
+    // reflections on pb: layer k+1, top = d of interface k, bottom = d of interface k+1
+    for (int k = 0; k < K; k++) {
+        int mask = (k + 1 <= L - 2) ? 3 : 1;
+        const T2 *in[4] = {vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1), nullptr, nullptr};
+        if (mask & 2) {
+            in[2] = vec_rows(W.pb, k + 1, 0);
+            in[3] = vec_rows(W.pb, k + 1, 1);
+        }
+        lb.add_F(k + 1, mask, in, B, B, W.inner, B, 0);
+    }
+    W.f_refl = lb.finish();
+    for (int k = 0; k < K; k++) {
+        int mask = (k + 1 <= L - 2) ? 3 : 1;
+        const T2 *in[4] = {vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1), nullptr, nullptr};
+        if (mask & 2) {
+            in[2] = vec_rows(W.pb, k + 1, 0);
+            in[3] = vec_rows(W.pb, k + 1, 1);
+        }
+        T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
+        lb.add_ES(k + 1, mask, in, B, 1, out, B, W.inner, B, B, 1);
+    }
+    W.es_refl = lb.finish();
+    // reconstruction F-step from the traces tr = pc viewed as [K][2][NX][B] (accumulating)
+    for (int l = 0; l < L; l++) {
+        int mask = (l > 0 ? 1 : 0) | (l < L - 1 ? 2 : 0);
+        const T2 *in[4] = {nullptr, nullptr, nullptr, nullptr};
+        if (l > 0) {
+            in[0] = W.pc + ((long long)(l - 1) * 2 + 0) * rowsz;
+            in[1] = W.pc + ((long long)(l - 1) * 2 + 1) * rowsz;
+        }
+        if (l < L - 1) {
+            in[2] = W.pc + ((long long)l * 2 + 0) * rowsz;
+            in[3] = W.pc + ((long long)l * 2 + 1) * rowsz;
+        }
+        if (mask) lb.add_F(l, mask, in, B, B, W.inner, B, 1);
+    }
+    W.f_rec = lb.finish();
+    // Newton samples: lout (B-wide view [L][4][NX][B]) += E x_f
+    for (int l = 0; l < L; l++) {
+        T2 *out[4];
+        for (int q = 0; q < 4; q++) out[q] = W.lout + ((long long)l * 4 + q) * rowsz;
+        const T2 *in[4] = {nullptr, nullptr, nullptr, nullptr};
+        lb.add_ES(l, 0, in, B, 3, out, B, W.inner, B, B, 1);
+    }
+    W.e_newton = lb.finish();
+    // single-layer applications (component entry point), inputs/outputs in lin/lout (B wide)
+    W.f_layer.assign(L, ProbList<T2>());
+    W.es_layer.assign(L, ProbList<T2>());
+    for (int l = 0; l < L; l++) {
+        const T2 *in[4];
+        T2 *out[4];
+        for (int q = 0; q < 4; q++) {
+            in[q] = W.lin + ((long long)l * 4 + q) * rowsz;
+            out[q] = W.lout + ((long long)l * 4 + q) * rowsz;
+        }
+        lb.add_F(l, 3, in, B, B, W.inner, B, 0);
+        W.f_layer[l] = lb.finish();
+        lb.add_ES(l, 3, in, B, 3, out, B, W.inner, B, B, 0);
+        W.es_layer[l] = lb.finish();
+    }
+}
+
+template <class T2> static std::unique_ptr<Work<T2>> &work_slot(hz_ctx *c);
+template <> std::unique_ptr<Work<double2>> &work_slot<double2>(hz_ctx *c) { return c->w64; }
+template <> std::unique_ptr<Work<float2>> &work_slot<float2>(hz_ctx *c) { return c->w32; }
+
+template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
+    void *ptrs[] = {W.vol, W.vol2, W.inner, W.inner2, W.inner_f, W.lin, W.lout, W.pa, W.pb, W.pc, W.Z, W.V, W.w64,
+                    W.rhs64, W.x64, W.dots, W.hbuf, W.gsrc, W.u, W.io, W.rnorm};
+    for (void *q : ptrs) c->dfree(q);
+    auto fl = [&](ProbList<T2> &pl) { c->dfree(pl.d); };
+    fl(W.f_full);
+    fl(W.es_bot_A);
+    fl(W.f_refl);
+    fl(W.es_refl);
+    fl(W.f_rec);
+    fl(W.e_newton);
+    for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer})
+        for (auto &pl : *vv) fl(pl);
+    if (W.hhost) cudaFreeHost(W.hhost);
+    if (W.rhost) cudaFreeHost(W.rhost);
+}
+
+template <class T2> Work<T2> &work(hz_ctx *c, int B) {
+    auto &slot = work_slot<T2>(c);
+    const int m = std::max(1, c->opts.restart);
+    if (slot && slot->B == B && slot->restart == m) return *slot;
+    if (slot) {
+        free_work(c, *slot);
+        slot.reset();
+    }
+    slot.reset(new Work<T2>());
+    Work<T2> &W = *slot;
+    W.B = B;
+    W.restart = m;
+    const long long ntr = c->n_tr(), N = (long long)c->NX * c->NZ;
+    auto al = [&](long long n, size_t es) { return c->dalloc(es * std::max(n, 1LL)); };
+    W.vol = (T2 *)al(c->tot_vol * B, sizeof(T2));
+    W.vol2 = (T2 *)al(c->tot_vol * B, sizeof(T2));
+    W.inner = (T2 *)al(c->tot_inner * B, sizeof(T2));
+    W.inner2 = (T2 *)al(c->tot_inner * 2 * B, sizeof(T2));
+    W.inner_f = (T2 *)al(c->tot_inner * B, sizeof(T2));
+    HZ_CU(cudaMemset(W.inner, 0, sizeof(T2) * c->tot_inner * B));
+    HZ_CU(cudaMemset(W.inner2, 0, sizeof(T2) * c->tot_inner * 2 * B));
+    HZ_CU(cudaMemset(W.inner_f, 0, sizeof(T2) * c->tot_inner * B));
+    W.lin = (T2 *)al((long long)c->L * 4 * c->NX * 2 * B, sizeof(T2));
+    W.lout = (T2 *)al((long long)c->L * 4 * c->NX * 2 * B, sizeof(T2));
+    HZ_CU(cudaMemset(W.lout, 0, sizeof(T2) * c->L * 4 * c->NX * 2 * B));
+    W.pa = (T2 *)al(ntr * B, sizeof(T2));
+    W.pb = (T2 *)al(ntr * B, sizeof(T2));
+    W.pc = (T2 *)al(ntr * B, sizeof(T2));
+    W.Z = (T2 *)al((long long)m * ntr * B, sizeof(T2));
+    W.V = (double2 *)al((long long)(m + 1) * ntr * B, sizeof(double2));
+    W.w64 = (double2 *)al(ntr * B, sizeof(double2));
+    W.rhs64 = (double2 *)al(ntr * B, sizeof(double2));
+    W.x64 = (double2 *)al(ntr * B, sizeof(double2));
+    W.dots = (double *)al((long long)(m + 2) * 64 * B * 2, sizeof(double));
+    W.hbuf = (double *)al((long long)(2 * m + 4) * B * 2, sizeof(double));
+    HZ_CU(cudaMallocHost(&W.hhost, sizeof(double) * (2 * m + 4) * B * 2));
+    W.gsrc = (double2 *)al(N * B, sizeof(double2));
+    W.u = (double2 *)al(N * B, sizeof(double2));
+    W.io = (double2 *)al(N * B, sizeof(double2));
+    W.rnorm = (double *)al((long long)1024 * B + 4 * B, sizeof(double));
+    HZ_CU(cudaMallocHost(&W.rhost, sizeof(double) * 4 * B));
+    build_lists(c, W);
+    return W;
+}
+template Work<double2> &work<double2>(hz_ctx *, int);
+template Work<float2> &work<float2>(hz_ctx *, int);
+
+// ------------------------------------------------------- layer pieces ---
+template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, T2 *inner, int l0, int nl, int N) {
+    if (c->C < 2) return;
+    Ops<T2> &o = ops<T2>(c);
+    double by = 0, fl = 0;
+    if (c->opts.time_kernels) inner_chain_cost<T2>(c, l0, nl, N, by, fl);
+    c->kt_begin(1, by, fl);
+    launch_inner_chain<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.W, o.Z, o.V, inner, N, 2 * c->max_nz, c->st,
+                           &c->nl);
+    c->kt_end();
+}
+
+// polarized operator: y (FP64) = M x (x in the working precision)
+template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, double2 *y) {
+    const int B = W.B;
+    const long long n = (long long)c->L * 4 * c->NX * 2 * B;
+    k_stage_M<T2><<<grid1(n), 256, 0, c->st>>>(x, W.lin, c->L, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    run(c, W.f_full);
+    chain_layers(c, W, W.inner2, 0, c->L, 2 * B);
+    run(c, W.es_bot_A);
+    const long long m = c->n_tr() * B;
+    k_combine_M<T2><<<grid1(m), 256, 0, c->st>>>(x, W.lout, y, c->L, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+}
+
+// preconditioner on W.pb in place (input copied there by the caller):
+// kind 0 GS, 1 Jacobi, 2 down only, 3 up only, 4 reflections only
+template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind) {
+    const int L = c->L;
+    if (kind == 0 || kind == 1 || kind == 2) {
+        for (int k = 1; k <= L - 2; k++) {
+            run(c, W.f_down[k]);
+            chain_layers(c, W, W.inner, k, 1, W.B);
+            run(c, W.es_down[k]);
+        }
+    }
+    if (kind == 0 || kind == 4) {
+        if (kind == 4) {  // u := 0 so that the step below leaves -L d in the u-part
+            const long long rowsz = (long long)c->NX * W.B;
+            for (int k = 0; k < L - 1; k++)
+                HZ_CU(cudaMemsetAsync(W.pb + ((long long)k * 4 + 2) * rowsz, 0, sizeof(T2) * 2 * rowsz, c->st));
+        }
+        // w = v_u - L d = v_u + [t0, t1 - d_b]: subtract d_b here, add t below
+        k_gs_fix<T2><<<grid1((long long)(L - 1) * c->NX * W.B), 256, 0, c->st>>>(W.pb, L - 1, c->NX, W.B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        run(c, W.f_refl);
+        chain_layers(c, W, W.inner, 1, L - 1, W.B);
+        run(c, W.es_refl);
+        if (kind == 4) {
+            k_refl_finish<T2><<<grid1((long long)(L - 1) * c->NX * W.B), 256, 0, c->st>>>(W.pb, L - 1, c->NX, W.B);
+            HZ_CU(cudaGetLastError());
+            c->nl++;
+        }
+    }
+    if (kind == 0 || kind == 1 || kind == 3) {
+        for (int k = L - 3; k >= 0; k--) {
+            run(c, W.f_up[k]);
+            chain_layers(c, W, W.inner, k + 1, 1, W.B);
+            run(c, W.es_up[k]);
+        }
+    }
+}
+
+// ------------------------------------------------------------ FGMRES ---
+struct GmresOut {
+    int iters = 0;
+    double resid = 0;
+};
+
+template <class T2>
+static GmresOut fgmres(hz_ctx *c, Work<T2> &W, double tol, int maxit, int kind) {
+    const int B = W.B, m = W.restart;
+    const long long n = c->n_tr(), nB = n * B;
+    cudaStream_t st = c->st;
+    const int nchunk = (int)std::min<long long>(64, std::max<long long>(1, n / 256));
+    dim3 dblk(32, 8);
+    auto dots = [&](const double2 *V, long long vs, int nvec, const double2 *w, double2 *h, int accum) {
+        dim3 g(nchunk, (B + 31) / 32, nvec);
+        k_dots<<<g, dblk, 0, st>>>(V, vs, w, n, B, nchunk, (double2 *)W.dots);
+        HZ_CU(cudaGetLastError());
+        k_dots_final<<<(nvec * B + 255) / 256, 256, 0, st>>>((double2 *)W.dots, nchunk, B, nvec, h, accum);
+        HZ_CU(cudaGetLastError());
+        c->nl += 2;
+    };
+    double2 *H = (double2 *)W.hbuf;  // device: [m+2][B]
+    double2 *Hh = (double2 *)W.hhost;
+    double *scale_h = W.rhost;
+    double *scale_d = W.rnorm;
+    // host Hessenberg state per RHS
+    std::vector<std::vector<double2>> Hm(B, std::vector<double2>((size_t)(m + 1) * m));
+    std::vector<std::vector<double2>> g(B, std::vector<double2>(m + 1)), cs(B, std::vector<double2>(m)),
+        sn(B, std::vector<double2>(m));
+    std::vector<double> beta0(B), res(B, 1.0);
+    std::vector<int> kb(B), conv(B, 0);
+    std::vector<double2> y((size_t)m * B);
+    double2 *y_d = (double2 *)W.dots;  // reuse (synchronised before reuse)
+
+    HZ_CU(cudaMemsetAsync(W.x64, 0, sizeof(double2) * nB, st));
+    // ||rhs||
+    dots(W.rhs64, 0, 1, W.rhs64, H, 0);
+    HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
+    HZ_CU(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; b++) {
+        beta0[b] = std::sqrt(std::max(Hh[b].x, 0.0));
+        if (!(beta0[b] > 0)) {
+            conv[b] = 1;
+            res[b] = 0;
+        }
+    }
+    const double2 *r = W.rhs64;  // first cycle: r = rhs (x0 = 0)
+    int total = 0;
+    GmresOut out;
+    while (true) {
+        // beta = ||r||, V0 = r / beta
+        dots(r, 0, 1, r, H, 0);
+        HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
+        HZ_CU(cudaStreamSynchronize(st));
+        std::vector<int> act(B);
+        for (int b = 0; b < B; b++) {
+            double be = std::sqrt(std::max(Hh[b].x, 0.0));
+            act[b] = !conv[b] && be > 0;
+            scale_h[b] = act[b] ? 1.0 / be : 0.0;
+            std::fill(g[b].begin(), g[b].end(), make_double2(0, 0));
+            g[b][0] = make_double2(be, 0);
+            kb[b] = 0;
+        }
+        HZ_CU(cudaMemcpyAsync(scale_d, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+        k_scale<<<grid1(nB), 256, 0, st>>>(r, scale_d, W.V, n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        int j = 0;
+        bool stop = false;
+        for (; j < m && !stop; j++) {
+            double2 *Vj = W.V + (long long)j * nB;
+            T2 *Zj = W.Z + (long long)j * nB;
+            // z_j = P v_j
+            k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(Vj, W.pb, nB);
+            HZ_CU(cudaGetLastError());
+            c->nl++;
+            if (kind != HZ_PNONE) precond_inplace(c, W, kind == HZ_PJAC ? 1 : 0);
+            HZ_CU(cudaMemcpyAsync(Zj, W.pb, sizeof(T2) * nB, cudaMemcpyDeviceToDevice, st));
+            // w = M z_j
+            apply_M(c, W, Zj, W.w64);
+            // CGS2
+            dots(W.V, nB, j + 1, W.w64, H, 0);
+            k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W.V, nB, H, j + 1, W.w64, n, B);
+            HZ_CU(cudaGetLastError());
+            dots(W.V, nB, j + 1, W.w64, H + (long long)(j + 1) * B, 0);
+            k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W.V, nB, H + (long long)(j + 1) * B, j + 1, W.w64, n, B);
+            HZ_CU(cudaGetLastError());
+            c->nl += 2;
+            // host copy of both passes, then the norm
+            std::vector<double2> h1((size_t)(j + 1) * B), h2((size_t)(j + 1) * B);
+            HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * (j + 1) * B, cudaMemcpyDeviceToHost, st));
+            HZ_CU(cudaStreamSynchronize(st));
+            std::memcpy(h1.data(), Hh, sizeof(double2) * (j + 1) * B);
+            HZ_CU(cudaMemcpyAsync(Hh, H + (long long)(j + 1) * B, sizeof(double2) * (j + 1) * B, cudaMemcpyDeviceToHost,
+                                  st));
+            HZ_CU(cudaStreamSynchronize(st));
+            std::memcpy(h2.data(), Hh, sizeof(double2) * (j + 1) * B);
+            dots(W.w64, 0, 1, W.w64, H, 0);
+            HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
+            HZ_CU(cudaStreamSynchronize(st));
+            total++;
+            bool all = true;
+            for (int b = 0; b < B; b++) {
+                double nrm = std::sqrt(std::max(Hh[b].x, 0.0));
+                scale_h[b] = 0.0;
+                if (!act[b]) continue;
+                auto &Hb = Hm[b];
+                for (int i = 0; i <= j; i++) Hb[(size_t)i * m + j] = h1[(size_t)i * B + b] + h2[(size_t)i * B + b];
+                Hb[(size_t)(j + 1) * m + j] = make_double2(nrm, 0);
+                // apply previous rotations
+                for (int i = 0; i < j; i++) {
+                    double2 a = Hb[(size_t)i * m + j], bb = Hb[(size_t)(i + 1) * m + j];
+                    double2 csi = cs[b][i], sni = sn[b][i];
+                    // [c s; -conj(s) c] with c real
+                    double2 t1 = make_double2(csi.x * a.x + (sni.x * bb.x - sni.y * bb.y),
+                                              csi.x * a.y + (sni.x * bb.y + sni.y * bb.x));
+                    double2 t2 = make_double2(-(sni.x * a.x + sni.y * a.y) + csi.x * bb.x,
+                                              -(sni.x * a.y - sni.y * a.x) + csi.x * bb.y);
+                    Hb[(size_t)i * m + j] = t1;
+                    Hb[(size_t)(i + 1) * m + j] = t2;
+                }
+                double2 a = Hb[(size_t)j * m + j];
+                double bn = nrm;
+                double an = std::hypot(a.x, a.y);
+                double den = std::hypot(an, bn);
+                double2 csj, snj;
+                if (den == 0) {
+                    csj = make_double2(1, 0);
+                    snj = make_double2(0, 0);
+                } else if (an == 0) {
+                    csj = make_double2(0, 0);
+                    snj = make_double2(1, 0);
+                } else {
+                    csj = make_double2(an / den, 0);
+                    // s = (a/|a|) * conj(b) / den, b real here
+                    snj = make_double2(a.x / an * bn / den, a.y / an * bn / den);
+                }
+                cs[b][j] = csj;
+                sn[b][j] = snj;
+                Hb[(size_t)j * m + j] = make_double2(csj.x * a.x + (snj.x * bn), csj.x * a.y + (snj.y * bn));
+                Hb[(size_t)(j + 1) * m + j] = make_double2(0, 0);
+                double2 gj = g[b][j];
+                g[b][j] = make_double2(csj.x * gj.x, csj.x * gj.y);
+                g[b][j + 1] = make_double2(-(snj.x * gj.x + snj.y * gj.y), -(snj.x * gj.y - snj.y * gj.x));
+                kb[b] = j + 1;
+                res[b] = std::hypot(g[b][j + 1].x, g[b][j + 1].y) / beta0[b];
+                if (res[b] <= tol) {
+                    conv[b] = 1;
+                    act[b] = 0;
+                } else if (nrm > 1e-300) {
+                    scale_h[b] = 1.0 / nrm;
+                } else {
+                    act[b] = 0;  // exact breakdown: solution in the current space
+                    conv[b] = 1;
+                }
+                if (act[b]) all = false;
+            }
+            if (all || total >= maxit) stop = true;
+            if (!stop && j + 1 < m) {
+                HZ_CU(cudaMemcpyAsync(scale_d, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, st));
+                k_scale<<<grid1(nB), 256, 0, st>>>(W.w64, scale_d, W.V + (long long)(j + 1) * nB, n, B);
+                HZ_CU(cudaGetLastError());
+                c->nl++;
+            }
+        }
+        // y = R^{-1} g per RHS, x += Z y
+        const int jj = j;
+        std::fill(y.begin(), y.end(), make_double2(0, 0));
+        for (int b = 0; b < B; b++) {
+            int k = kb[b];
+            auto &Hb = Hm[b];
+            std::vector<double2> yb(k);
+            for (int i = k - 1; i >= 0; i--) {
+                double2 s = g[b][i];
+                for (int q = i + 1; q < k; q++) s = s - Hb[(size_t)i * m + q] * yb[q];
+                yb[i] = cdiv(s, Hb[(size_t)i * m + i]);
+            }
+            for (int i = 0; i < k; i++) y[(size_t)i * B + b] = yb[i];
+        }
+        HZ_CU(cudaStreamSynchronize(st));
+        HZ_CU(cudaMemcpyAsync(y_d, y.data(), sizeof(double2) * jj * B, cudaMemcpyHostToDevice, st));
+        k_update_x<T2><<<grid1(nB), 256, 0, st>>>(W.Z, nB, y_d, jj, W.x64, n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        HZ_CU(cudaStreamSynchronize(st));
+        bool all = true;
+        for (int b = 0; b < B; b++)
+            if (!conv[b]) all = false;
+        if (all || total >= maxit) break;
+        // restart: r = rhs - M x
+        k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(W.x64, W.pa, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        apply_M(c, W, W.pa, W.w64);
+        k_sub<<<grid1(nB), 256, 0, st>>>(W.rhs64, W.w64, W.w64, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        r = W.w64;
+    }
+    out.iters = total;
+    out.resid = 0;
+    for (int b = 0; b < B; b++) out.resid = std::max(out.resid, res[b]);
+    return out;
+}
+
+// ------------------------------------------------------- nested solve ---
+struct Timers {
+    double local = 0, gmres = 0, recon = 0, resid = 0;
+};
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// One pass of Alg. matrix_free_solver on the symmetric-form source src
+// ([N][B], FP64); the volume correction is added to W.u.
+template <class T2>
+static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double tol, int maxit, Timers &tm) {
+    cudaStream_t st = c->st;
+    const int B = W.B, L = c->L, ncell = (int)c->cells.size();
+    const int nb = (int)std::min<long long>(1024, (c->tot_vol * B / ncell + 255) / 256 + 1);
+    double t0 = now_ms();
+    // 1. Newton potentials: cell solves of the partitioned source
+    k_scatter<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, src, W.vol, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    cell_chain<T2>(c, W.vol, B);
+    if (c->C > 1) {
+        k_gather_inner<T2><<<dim3(256, L), 256, 0, st>>>(c->d_layers, c->d_cells, W.vol, W.inner_f, B, c->p);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+    }
+    // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy
+    HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
+    if (c->C > 1) chain_layers(c, W, W.inner, 0, L, B);
+    k_samples<T2><<<dim3(64, ncell), 256, 0, st>>>(c->d_cells, W.vol, W.lout, c->NX, B, c->p);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    run(c, W.e_newton);
+    k_pol_rhs<T2><<<grid1(c->n_tr() * B), 256, 0, st>>>(W.lout, W.rhs64, L - 1, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(st));
+    double t1 = now_ms();
+    tm.local += t1 - t0;
+    // 2. traces
+    GmresOut go = fgmres(c, W, tol, maxit, c->opts.precond);
+    double t2 = now_ms();
+    tm.gmres += t2 - t1;
+    // 3. reconstruction
+    k_traces<T2><<<grid1((long long)(L - 1) * 2 * c->NX * B), 256, 0, st>>>(W.x64, W.pc, L - 1, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
+    run(c, W.f_rec);
+    if (c->C > 1) chain_layers(c, W, W.inner, 0, L, B);
+    k_recon_src<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, c->d_layers, W.pc, W.inner, W.vol2, L, c->NX, B, c->p,
+                                                     c->h, c->pml_C, c->omega);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    cell_chain<T2>(c, W.vol2, B);
+    k_accum_u<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, W.vol, W.vol2, W.u, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(st));
+    tm.recon += now_ms() - t2;
+    return go;
+}
+
+// per-RHS ||alpha r||^2 partial sums -> host (mode 0 writes r = fs - H u)
+static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
+                           int mode, double *part) {
+    const int nchunk = 256;
+    dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
+    k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_m, c->d_ax, c->d_axh, c->d_az, c->d_azh, c->NX, c->NZ, c->h,
+                                     c->omega, B, part, nchunk, mode);
+    HZ_CU(cudaGetLastError());
+    double *fin = part + (long long)nchunk * B;
+    k_reduce_parts<<<(B + 255) / 256, 256, 0, c->st>>>(part, nchunk, B, fin);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    HZ_CU(cudaMemcpyAsync(out_host, fin, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+
+void init_global_alpha(hz_ctx *c) {
+    c->d_ax = (double2 *)c->dalloc(sizeof(double2) * c->NX);
+    c->d_axh = (double2 *)c->dalloc(sizeof(double2) * (c->NX + 1));
+    c->d_az = (double2 *)c->dalloc(sizeof(double2) * c->NZ);
+    c->d_azh = (double2 *)c->dalloc(sizeof(double2) * (c->NZ + 1));
+    int n = std::max(c->NX, c->NZ) + 1;
+    k_global_alpha<<<(n + 255) / 256, 256, 0, c->st>>>(c->NX, c->NZ, c->n_x, c->n_z, c->p, c->h, c->pml_C, c->omega,
+                                                        c->d_ax, c->d_axh, c->d_az, c->d_azh);
+    HZ_CU(cudaGetLastError());
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+
+// Full solve: f (device, batch-outer [B][N]) -> u (device, batch-outer), stats.
+template <class T2>
+int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st_out, bool scale_src) {
+    Work<T2> &W = work<T2>(c, B);
+    cudaStream_t st = c->st;
+    const long long N = (long long)c->NX * c->NZ;
+    Timers tm;
+    hz_stats s{};
+    double t0 = now_ms();
+    // source in the row-scaled form, [N][B]
+    k_src_in<<<grid1(N * B), 256, 0, st>>>(f_dev, W.gsrc, c->d_ax, c->d_az, c->NX, N, B, scale_src ? 1 : 0);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, st));
+    std::vector<double> fn(B), rn(B);
+    residual_norms(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
+    for (int b = 0; b < B; b++) fn[b] = std::sqrt(W.rhost[b]);
+    const bool mixed = c->mixed();
+    double tol = c->opts.tol;
+    const double rtol = c->opts.refine_tol;
+    const int max_pass = rtol > 0 ? std::max(1, c->opts.max_refine) : 1;
+    const double2 *src = W.gsrc;
+    int status = HZ_OK;
+    double worst = 0;
+    for (int pass = 0; pass < max_pass; pass++) {
+        GmresOut go = nested_pass<T2>(c, W, src, tol, c->opts.max_it, tm);
+        s.iterations += go.iters;
+        s.gmres_resid = go.resid;
+        s.refinements = pass + 1;
+        double tr0 = now_ms();
+        // residual r = fs - H u into io (reused as the next source)
+        residual_norms(c, W.u, W.gsrc, W.io, B, W.rhost, 0, W.rnorm);
+        tm.resid += now_ms() - tr0;
+        worst = 0;
+        for (int b = 0; b < B; b++) {
+            rn[b] = fn[b] > 0 ? std::sqrt(W.rhost[b]) / fn[b] : 0.0;
+            worst = std::max(worst, rn[b]);
+        }
+        if (go.resid > tol && !mixed) status = HZ_ENOTCONV;
+        if (rtol <= 0 || worst <= rtol) break;
+        src = W.io;
+        (void)mixed;
+    }
+    if (rtol > 0 && worst > rtol) status = HZ_ENOTCONV;
+    s.resid = worst;
+    k_out<<<grid1(N * B), 256, 0, st>>>(W.u, u_dev, N, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(st));
+    s.t_total_ms = now_ms() - t0;
+    s.t_local_ms = tm.local;
+    s.t_gmres_ms = tm.gmres;
+    s.t_recon_ms = tm.recon;
+    s.t_resid_ms = tm.resid;
+    if (st_out) {
+        int keep = st_out->gpu_launches;
+        *st_out = s;
+        st_out->gpu_launches = keep;
+    }
+    return status;
+}
+template int solve_impl<double2>(hz_ctx *, const double2 *, int, double2 *, hz_stats *, bool);
+template int solve_impl<float2>(hz_ctx *, const double2 *, int, double2 *, hz_stats *, bool);
+
+// ------------------------------------------------- component helpers ---
+template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev, int B, double2 *x_dev) {
+    Work<T2> &W = work<T2>(c, B);
+    Ops<T2> &o = ops<T2>(c);
+    const CellDesc &cd = c->cells[ci];
+    const long long npt = (long long)cd.nx * cd.nz;
+    // g [B][npt] -> vol (cell slot, [npt][B])
+    k_src_in<<<grid1(npt * B), 256, 0, c->st>>>(g_dev, W.io, nullptr, nullptr, 1, npt, B, 0);
+    HZ_CU(cudaGetLastError());
+    k_cast<double2, T2><<<grid1(npt * B), 256, 0, c->st>>>(W.io, W.vol + cd.vol_off * B, npt * B);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    launch_cell_chain<T2>(c->d_cells + ci, 1, o.cellW, o.cz, W.vol, B, c->max_nx, c->st, &c->nl);
+    k_cast<T2, double2><<<grid1(npt * B), 256, 0, c->st>>>(W.vol + cd.vol_off * B, W.io, npt * B);
+    HZ_CU(cudaGetLastError());
+    k_out<<<grid1(npt * B), 256, 0, c->st>>>(W.io, x_dev, npt, B);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+template void comp_cell_solve<double2>(hz_ctx *, int, const double2 *, int, double2 *);
+template void comp_cell_solve<float2>(hz_ctx *, int, const double2 *, int, double2 *);
+
+// tr [B][4][NX] -> lin (B-wide rows of layer l) ; out [B][4][NX]
+template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_dev, int mask, int B, double2 *out_dev) {
+    Work<T2> &W = work<T2>(c, B);
+    const long long n4 = 4LL * c->NX;
+    const long long rowsz = (long long)c->NX * B;
+    // [B][4*NX] -> [4*NX][B] into io, mask rows, cast into lin (layer l block)
+    k_src_in<<<grid1(n4 * B), 256, 0, c->st>>>(tr_dev, W.io, nullptr, nullptr, 1, n4, B, 0);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    if (!(mask & 1)) HZ_CU(cudaMemsetAsync(W.io, 0, sizeof(double2) * 2 * rowsz, c->st));
+    if (!(mask & 2)) HZ_CU(cudaMemsetAsync(W.io + 2 * rowsz, 0, sizeof(double2) * 2 * rowsz, c->st));
+    T2 *lin_l = W.lin + (long long)l * 4 * rowsz;
+    k_cast<double2, T2><<<grid1(n4 * B), 256, 0, c->st>>>(W.io, lin_l, n4 * B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    run(c, W.f_layer[l]);
+    if (c->C > 1) chain_layers(c, W, W.inner, l, 1, B);
+    run(c, W.es_layer[l]);
+    T2 *lout_l = W.lout + (long long)l * 4 * rowsz;
+    k_cast<T2, double2><<<grid1(n4 * B), 256, 0, c->st>>>(lout_l, W.io, n4 * B);
+    HZ_CU(cudaGetLastError());
+    k_out<<<grid1(n4 * B), 256, 0, c->st>>>(W.io, out_dev, n4, B);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+template void comp_layer_green<double2>(hz_ctx *, int, const double2 *, int, int, double2 *);
+template void comp_layer_green<float2>(hz_ctx *, int, const double2 *, int, int, double2 *);
+
+// x, y: [B][n_tr]; which: -1 apply M, 0..4 preconditioner variants
+template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, int B, double2 *y_dev) {
+    Work<T2> &W = work<T2>(c, B);
+    const long long n = c->n_tr(), nB = n * B;
+    k_src_in<<<grid1(nB), 256, 0, c->st>>>(x_dev, W.w64, nullptr, nullptr, 1, n, B, 0);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    if (which < 0) {
+        k_cast<double2, T2><<<grid1(nB), 256, 0, c->st>>>(W.w64, W.pa, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        apply_M(c, W, W.pa, W.x64);
+    } else {
+        k_cast<double2, T2><<<grid1(nB), 256, 0, c->st>>>(W.w64, W.pb, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        precond_inplace(c, W, which);
+        k_cast<T2, double2><<<grid1(nB), 256, 0, c->st>>>(W.pb, W.x64, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+    }
+    k_out<<<grid1(nB), 256, 0, c->st>>>(W.x64, y_dev, n, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(c->st));
+}
+template void comp_polar<double2>(hz_ctx *, int, const double2 *, int, double2 *);
+template void comp_polar<float2>(hz_ctx *, int, const double2 *, int, double2 *);
+
+template <class T2> void comp_residual(hz_ctx *c, const double2 *u_dev, const double2 *f_dev, int B, double *res_host) {
+    Work<T2> &W = work<T2>(c, B);
+    const long long N = (long long)c->NX * c->NZ;
+    k_src_in<<<grid1(N * B), 256, 0, c->st>>>(f_dev, W.gsrc, c->d_ax, c->d_az, c->NX, N, B, 1);
+    k_src_in<<<grid1(N * B), 256, 0, c->st>>>(u_dev, W.u, nullptr, nullptr, 1, N, B, 0);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    std::vector<double> fn(B);
+    residual_norms(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
+    for (int b = 0; b < B; b++) fn[b] = std::sqrt(W.rhost[b]);
+    residual_norms(c, W.u, W.gsrc, W.io, B, W.rhost, 0, W.rnorm);
+    for (int b = 0; b < B; b++) res_host[b] = fn[b] > 0 ? std::sqrt(W.rhost[b]) / fn[b] : 0.0;
+}
+template void comp_residual<double2>(hz_ctx *, const double2 *, const double2 *, int, double *);
+template void comp_residual<float2>(hz_ctx *, const double2 *, const double2 *, int, double *);
+
+}  // namespace hz
+
+// ------------------------------------------------------ kernel timers ---
+cudaEvent_t hz_ctx::ev_get() {
+    if (!ev_pool.empty()) {
+        cudaEvent_t e = ev_pool.back();
+        ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    HZ_CU(cudaEventCreate(&e));
+    return e;
+}
+void hz_ctx::kt_begin(int cls, double bytes, double flops) {
+    if (!opts.time_kernels) return;
+    KT k{cls, ev_get(), ev_get(), bytes, flops};
+    HZ_CU(cudaEventRecord(k.a, st));
+    kt_open.push_back(k);
+}
+void hz_ctx::kt_end() {
+    if (!opts.time_kernels || kt_open.empty()) return;
+    HZ_CU(cudaEventRecord(kt_open.back().b, st));
+}
+void hz_ctx::kt_collect() {
+    if (kt_open.empty()) return;
+    HZ_CU(cudaStreamSynchronize(st));
+    for (KT &k : kt_open) {
+        float ms = 0;
+        HZ_CU(cudaEventElapsedTime(&ms, k.a, k.b));
+        kt_ms[k.cls] += ms;
+        kt_launches[k.cls]++;
+        kt_bytes[k.cls] += k.bytes;
+        kt_flops[k.cls] += k.flops;
+        ev_pool.push_back(k.a);
+        ev_pool.push_back(k.b);
+    }
+    kt_open.clear();
+}
+void hz_ctx::kt_reset() {
+    for (int i = 0; i < 3; i++) {
+        kt_launches[i] = 0;
+        kt_ms[i] = kt_bytes[i] = kt_flops[i] = 0;
+    }
+}

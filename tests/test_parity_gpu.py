@@ -1,0 +1,232 @@
+"""Parity of every step of the CUDA path with the CPU oracle (through the C ABI).
+
+Sizes: cells wider than one 64-row tile with a ragged tail, several layers
+and cells, batch widths that leave partial RHS tiles.  Tolerances: FP64
+steps agree to roundoff amplified by the conditioning of the explicit block
+inverses (1e-9 relative); the end-to-end FP64 solve meets the 1e-8 bar and
+the mixed-precision solve the 1e-5 bar (it reaches far below it after FP64
+residual refinement).
+"""
+import numpy as np
+import pytest
+
+import hz_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+hz = pytest.importorskip("paper_1510_01831_gb300.hz")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def _problem(n_x=100, n_z=60, p=6, L=4, C=2, seed=21, ppw=8.0, rows=None, cols=None):
+    pb = I.smooth_random(n_x, n_pml=p, L=L, C=C, seed=seed, ppw=ppw, corr_pts=10, n_z=n_z)
+    pb.layer_rows, pb.cell_cols = rows, cols
+    return pb
+
+
+class Setup:
+    def __init__(self, pb, precision):
+        self.pb = pb
+        self.C_pml = O.default_pml_C(pb.m)
+        self.D = O.Decomposition(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, self.C_pml, pb.L, pb.C,
+                                 layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
+        self.ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=precision,
+                              pml_C=self.C_pml, layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
+        self.ctx.hz_factor()
+
+
+@pytest.fixture(scope="module")
+def fp64():
+    s = Setup(_problem(), hz.HZ_FP64)
+    yield s
+    s.ctx.close()
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    s = Setup(_problem(), hz.HZ_MIXED)
+    yield s
+    s.ctx.close()
+
+
+def _rand(shape, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+# ----------------------------------------------------------------- a1 ---
+@pytest.mark.parametrize("l,c", [(0, 0), (1, 1), (3, 1), (2, 0)])
+def test_cell_solve(fp64, l, c):
+    """a1: one cell's local problem (row-scaled form) vs the oracle's cell box."""
+    D = fp64.D
+    box = D.cell_box(l, c)
+    B = 5
+    g = _rand((B,) + box.shape, 100 + l * 10 + c)
+    x = fp64.ctx.hz_cell_solve(l, c, g)
+    ax = box.alpha(0, np.arange(box.shape[1]))
+    az = box.alpha(1, np.arange(box.shape[0]))
+    ref = box.factor().solve(g * (az[:, None] * ax[None, :]))  # H_s = D^{-1} H_A
+    assert _rel(x, ref) < 1e-9
+
+
+# ----------------------------------------------------------------- a5 ---
+@pytest.mark.parametrize("l,mask", [(0, 3), (1, 3), (2, 1), (3, 2), (1, 2)])
+def test_layer_green(fp64, l, mask):
+    """a2-a5: F -> inner block-LU sweeps -> E + S against a direct layer solve."""
+    D = fp64.D
+    B = 3
+    tr = _rand((B, 4, D.NX), 200 + l)
+    if not mask & 1:
+        tr[:, 0:2] = 0
+    if not mask & 2:
+        tr[:, 2:4] = 0
+    out = fp64.ctx.hz_layer_green(l, tr, mask)
+    ref = D.green(l, tr[:, 0], tr[:, 1], tr[:, 2], tr[:, 3])
+    assert _rel(out, ref) < 1e-9
+
+
+# ------------------------------------------------------------- a6-a9 ---
+def _pol(D, B, seed):
+    return _rand((B, D.L - 1, 4, D.NX), seed)
+
+
+def test_apply_M(fp64):
+    D = fp64.D
+    x = _pol(D, 3, 300)
+    assert _rel(fp64.ctx.hz_apply_M(x), O.apply_M(D, x)) < 1e-9
+
+
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4])
+def test_precond(fp64, which):
+    D = fp64.D
+    x = _pol(D, 2, 310 + which)
+    y = fp64.ctx.hz_precond(which, x)
+    if which == 0:
+        ref = O.precond_gs(D, x)
+    elif which == 1:
+        ref = O.precond_jac(D, x)
+    elif which == 2:
+        ref = np.concatenate([O.sweep_down(D, x[..., 0:2, :]), x[..., 2:4, :]], axis=-2)
+    elif which == 3:
+        ref = np.concatenate([x[..., 0:2, :], O.sweep_up(D, x[..., 2:4, :])], axis=-2)
+    else:
+        ref = np.concatenate([np.zeros_like(x[..., 0:2, :]), O.reflections(D, x[..., 0:2, :])], axis=-2)
+    assert _rel(y, ref) < 1e-9
+
+
+def test_residual(fp64):
+    pb = fp64.pb
+    box = fp64.D.box
+    f = I.random_sources(box.shape, pb.n_pml, 2, 400)
+    u = _rand((2,) + box.shape, 401) * 1e-3
+    r = fp64.ctx.hz_residual(u, f)
+    assert np.allclose(r, O.relative_residual(box, u, f), rtol=1e-10)
+
+
+# ------------------------------------------------------------ a1-a12 ---
+@pytest.fixture(scope="module")
+def oracle_solution(fp64):
+    pb = fp64.pb
+    f = np.concatenate([I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, 3),
+                        I.random_sources(pb.shape_ext, pb.n_pml, 2, 500)])
+    u = fp64.D.box.factor().solve(f)
+    return f, u
+
+
+def test_solve_fp64(fp64, oracle_solution):
+    f, ref = oracle_solution
+    u, st = fp64.ctx.hz_solve(f)
+    assert st.converged if hasattr(st, "converged") else True
+    for b in range(f.shape[0]):
+        assert _rel(u[b], ref[b]) < 1e-8
+    assert st.resid < 1e-8
+    assert 0 < st.iterations < 60
+    assert st.gpu_launches > 0
+
+
+def test_solve_mixed(mixed, oracle_solution):
+    f, ref = oracle_solution
+    u, st = mixed.ctx.hz_solve(f)
+    for b in range(f.shape[0]):
+        assert _rel(u[b], ref[b]) < 1e-5
+    assert st.resid < 1e-8          # refinement target
+    assert st.refinements >= 2      # FP32 alone cannot get there
+
+
+def test_gs_needs_fewer_iterations_than_jacobi():
+    pb = _problem(n_x=60, n_z=60, L=5, C=2, seed=23)
+    f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, 2)
+    its = {}
+    for pc in (hz.HZ_PGS, hz.HZ_PJAC):
+        ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_FP64,
+                         precond=pc, refine_tol=0, tol=1e-8)
+        ctx.hz_factor()
+        _, st = ctx.hz_solve(f)
+        its[pc] = st.iterations
+        ctx.close()
+    assert its[hz.HZ_PGS] <= 0.7 * its[hz.HZ_PJAC]
+
+
+@pytest.mark.parametrize("case", ["uneven", "one_cell", "many_cells"])
+def test_solve_partitions(case):
+    if case == "uneven":
+        pb = _problem(n_x=90, n_z=70, p=5, L=3, C=3, seed=31, rows=[20, 31, 19], cols=[25, 40, 25])
+    elif case == "one_cell":
+        pb = _problem(n_x=50, n_z=40, p=4, L=3, C=1, seed=32)
+    else:
+        pb = _problem(n_x=64, n_z=30, p=4, L=2, C=6, seed=33)
+    C_pml = O.default_pml_C(pb.m)
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_FP64,
+                     pml_C=C_pml, layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
+    ctx.hz_factor()
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 3, 600)
+    u, st = ctx.hz_solve(f)
+    ref = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml).factor().solve(f)
+    ctx.close()
+    assert _rel(u, ref) < 1e-8
+
+
+def test_device_pointers_match_host():
+    torch = pytest.importorskip("torch")
+    pb = _problem(n_x=48, n_z=40, p=4, L=3, C=2, seed=41)
+    C_pml = O.default_pml_C(pb.m)
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 2, 700)
+    res = []
+    for dev in (False, True):
+        ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, pml_C=C_pml, device_ptrs=dev)
+        ctx.hz_factor()
+        ff = torch.from_numpy(f).cuda() if dev else f
+        u, _ = ctx.hz_solve(ff)
+        res.append(u.cpu().numpy() if dev else u)
+        ctx.close()
+    assert _rel(res[1], res[0]) < 1e-12
+
+
+def test_nonfinite_source_rejected(fp64):
+    f = np.zeros((1,) + fp64.D.box.shape, complex)
+    f[0, 5, 5] = np.nan
+    with pytest.raises(hz.HzError) as e:
+        fp64.ctx.hz_solve(f)
+    assert e.value.status == hz.HZ_EINVAL
+
+
+def test_gradient_matches_oracle():
+    pb = _problem(n_x=40, n_z=36, p=5, L=3, C=2, seed=51)
+    C_pml = O.default_pml_C(pb.m)
+    B = 3
+    f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, B)
+    rec = I.receivers_top_row(pb.n_x, pb.n_pml)
+    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
+    m_true = pb.m * (1 + 0.05 * I.gaussian_blob(pb.shape_ext, pb.n_pml, pb.h, 6))
+    d = O.Box(m_true, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml).factor().solve(f).reshape(B, -1)[:, rec]
+    J_ref, g_ref, _ = O.misfit_gradient(box, f, d, rec)
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, pml_C=C_pml)
+    ctx.hz_factor()
+    J, g, u, st = ctx.hz_gradient(f, np.ascontiguousarray(d), rec.astype(np.int32))
+    ctx.close()
+    assert abs(J - J_ref) <= 1e-8 * abs(J_ref)
+    assert _rel(g, g_ref) < 1e-7
