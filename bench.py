@@ -219,7 +219,7 @@ def run_ours(args, rank, world):
 
 
 # ------------------------------------------------- oracle (CPU) timing ---
-def oracle_sample(wl, rows=24, nthreads=None):
+def oracle_sample(wl, rows=4, nthreads=None):
     """Time the CPU oracle (banded LU) on a full-width strip of the workload's
     medium and scale to the full grid: with x-fastest ordering the band width
     is the full extended width, so the cost per grid row is the same as for

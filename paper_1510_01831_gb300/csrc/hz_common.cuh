@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include "../../include/hz.h"
+
 namespace hz {
 
 // ------------------------------------------------------------ complex ---
@@ -92,7 +94,7 @@ struct LayerDesc {
     int cell0;           // index of its first cell
     long long inner_off; // inner vector offset: (C+1) slots of 2 nz (slot 0 and C are zero pads)
     long long W_off;     // C-1 blocks (2nz)^2
-    long long Z_off;     // C-1 blocks nz x 2nz (slot 0 unused)
+    long long P_off;     // C-1 blocks (2nz)^2: P_j = W_j(:, 0:nz) Z_j (slot 0 unused)
     long long V_off;     // C-1 blocks (2nz)^2 (last unused)
 };
 
@@ -156,8 +158,8 @@ void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2
                        int max_nx, cudaStream_t st, int *nl);
 
 template <class T2>
-void launch_inner_chain(const LayerDesc *d_layers, const int *d_layer_ids, int nlayer, const T2 *W,
-                        const T2 *Z, const T2 *V, T2 *inner, int B, int max_nz2, cudaStream_t st, int *nl);
+void launch_inner_sweep(const LayerDesc *d_layers, const int *d_layer_ids, int nlayer, const T2 *P, const T2 *V,
+                        const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st, int *nl);
 
 // offline (FP64)
 void launch_cell_coeffs(const CellDesc *d_cells, int ncell, const double *m, int NX, double omega, double h,

@@ -14,7 +14,7 @@ template <class T2> struct Ops {
     T2 *cellW = nullptr;  // per cell: nz blocks of nx*nx (inverted Schur complements)
     T2 *cz = nullptr;     // per cell: z couplings (nz x nx, last row unused)
     T2 *F = nullptr, *E = nullptr, *S = nullptr;
-    T2 *W = nullptr, *Z = nullptr, *V = nullptr;  // inner block LU
+    T2 *W = nullptr, *P = nullptr, *V = nullptr;  // inner block LU: W_j, P_j = W_j(:,0:nz) Z_j, V_j
 };
 
 // Problem lists of batched GEMMs, kept on the device (built once per workspace).
@@ -32,6 +32,8 @@ template <class T2> struct Work {
     T2 *inner = nullptr;   // inner vectors [tot_inner][B]
     T2 *inner2 = nullptr;  // inner vectors [tot_inner][2B] (polarized operator, two input sets)
     T2 *inner_f = nullptr; // inner right-hand side of the Newton potentials (saved)
+    T2 *innerH = nullptr;  // h_j = W_j g_j, B wide
+    T2 *innerH2 = nullptr; // h_j = W_j g_j, 2B wide
     T2 *lin = nullptr;     // layer-application inputs  [L][4][T][2B]
     T2 *lout = nullptr;    // layer-application outputs [L][4][T][2B]
     T2 *pa = nullptr, *pb = nullptr, *pc = nullptr;  // polarized vectors [K][4][T][B]
@@ -57,6 +59,10 @@ template <class T2> struct Work {
     ProbList<T2> f_refl, es_refl;               // reflections (all layers)
     ProbList<T2> f_rec, e_newton;              // reconstruction F-step, Newton E-step
     std::vector<ProbList<T2>> f_layer, es_layer; // single-layer (component API)
+    // h_j = W_j g_j problems ordered by layer; layers [l0, l1) are problems [hoff[l0], hoff[l1])
+    ProbList<T2> hB, h2B;
+    std::vector<int> hoff;
+    std::vector<double> hbytes, hflops;  // per layer (B wide)
 };
 
 }  // namespace hz
@@ -79,7 +85,7 @@ struct hz_ctx {
     hz::LayerDesc *d_layers = nullptr;
     int *d_layer_ids = nullptr;  // 0..L-1
     long long tot_vol = 0, tot_W = 0, tot_F = 0, tot_E = 0, tot_S = 0, tot_K = 0;
-    long long tot_inner = 0, tot_Wi = 0, tot_Z = 0, tot_V = 0;
+    long long tot_inner = 0, tot_Wi = 0, tot_P = 0, tot_V = 0;
     int max_nx = 0, max_nz = 0, max_no = 0;
     // global medium and PML profiles (FP64)
     double *d_m = nullptr;

@@ -40,7 +40,7 @@ void build_decomposition(hz_ctx *c) {
     const int p = c->p, L = c->L, C = c->C;
     c->cells.clear();
     c->layers.clear();
-    long long vol = 0, Wc = 0, F = 0, E = 0, S = 0, K = 0, inner = 0, Wi = 0, Z = 0, V = 0;
+    long long vol = 0, Wc = 0, F = 0, E = 0, S = 0, K = 0, inner = 0, Wi = 0, Pi = 0, V = 0;
     int s = 0;
     c->max_nx = c->max_nz = c->max_no = 0;
     for (int l = 0; l < L; l++) {
@@ -57,8 +57,8 @@ void build_decomposition(hz_ctx *c) {
         const long long n2 = 2LL * ld.nz;
         ld.W_off = Wi;
         Wi += (long long)std::max(C - 1, 0) * n2 * n2;
-        ld.Z_off = Z;
-        Z += (long long)std::max(C - 1, 0) * ld.nz * n2;
+        ld.P_off = Pi;
+        Pi += (long long)std::max(C - 1, 0) * n2 * n2;
         ld.V_off = V;
         V += (long long)std::max(C - 1, 0) * n2 * n2;
         int t = 0;
@@ -111,7 +111,7 @@ void build_decomposition(hz_ctx *c) {
     c->tot_K = K;
     c->tot_inner = inner;
     c->tot_Wi = Wi;
-    c->tot_Z = Z;
+    c->tot_P = Pi;
     c->tot_V = V;
     c->d_cells = (CellDesc *)c->dalloc(sizeof(CellDesc) * c->cells.size());
     c->d_layers = (LayerDesc *)c->dalloc(sizeof(LayerDesc) * c->layers.size());
@@ -238,14 +238,14 @@ __global__ void k_inner_diag(const LayerDesc *__restrict__ layers, const CellDes
     }
 }
 
-// Z_j = K_j(w-rows, x_{j-1} part)  (nz x 2nz)
+// Z_j = K_j(w-rows, x_{j-1} part)  (nz x 2nz), stored in slot j of a buffer laid out like P
 __global__ void k_inner_z(const LayerDesc *__restrict__ layers, const CellDesc *__restrict__ cells,
                           const double2 *__restrict__ K, double2 *Z, int j) {
     const LayerDesc &ld = layers[blockIdx.y];
     if (j >= ld.C - 1 || j == 0) return;
     const int nz = ld.nz, n2 = 2 * nz;
     const CellDesc &ca = cells[ld.cell0 + j];
-    double2 *Zj = Z + ld.Z_off + (long long)j * nz * n2;
+    double2 *Zj = Z + ld.P_off + (long long)j * n2 * n2;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nz * n2; e += gridDim.x * blockDim.x) {
         int m = e / n2, k = e % n2;
         Zj[e] = K[ca.K_off + (long long)(nz + m) * 4 * nz + k];
@@ -344,8 +344,8 @@ void factor_all(hz_ctx *c) {
 
     // 3. inner block LU per layer: S_j = A_j - [Z_j V_{j-1}; 0], W_j = S_j^{-1},
     //    V_j = W_j(:, nz:2nz) K_{j+1}(1-rows, x_{j+1} part)
-    double2 *Wi = alloc_n<double2>(c, c->tot_Wi), *Zi = alloc_n<double2>(c, c->tot_Z);
-    double2 *Vi = alloc_n<double2>(c, c->tot_V);
+    double2 *Wi = alloc_n<double2>(c, c->tot_Wi), *Zi = alloc_n<double2>(c, c->tot_P);
+    double2 *Pm = alloc_n<double2>(c, c->tot_P), *Vi = alloc_n<double2>(c, c->tot_V);
     const int C = c->C;
     if (C > 1) {
         GemmProb<double2> *d_pr = (GemmProb<double2> *)c->dalloc(sizeof(GemmProb<double2>) * L);
@@ -369,7 +369,7 @@ void factor_all(hz_ctx *c) {
                     const LayerDesc &ld = c->layers[l];
                     const int nz = ld.nz, n2 = 2 * nz;
                     GemmProb<double2> g{};
-                    g.A = Zi + ld.Z_off + (long long)j * nz * n2;
+                    g.A = Zi + ld.P_off + (long long)j * n2 * n2;
                     g.lda = n2;
                     g.M = nz;
                     g.K = n2;
@@ -396,6 +396,32 @@ void factor_all(hz_ctx *c) {
             HZ_CU(cudaMemcpyAsync(d_mats, mats.data(), sizeof(double2 *) * L, cudaMemcpyHostToDevice, st));
             HZ_CU(cudaMemcpyAsync(d_ns, ns.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st));
             launch_gj_inverse(d_mats, d_ns, L, maxn2, d_info, st, nl);
+            if (j > 0) {  // P_j = W_j(:, 0:nz) Z_j: the forward sweep becomes y_j = W_j g_j + P_j y_{j-1}
+                int mt = 0;
+                for (int l = 0; l < L; l++) {
+                    const LayerDesc &ld = c->layers[l];
+                    const int nz = ld.nz, n2 = 2 * nz;
+                    GemmProb<double2> g{};
+                    g.A = Wi + ld.W_off + (long long)j * n2 * n2;
+                    g.lda = n2;
+                    g.M = n2;
+                    g.K = nz;
+                    g.N = n2;
+                    g.xseg = g.yseg = 1 << 30;
+                    g.X[0] = Zi + ld.P_off + (long long)j * n2 * n2;
+                    g.ldx = n2;
+                    g.Y[0] = Pm + ld.P_off + (long long)j * n2 * n2;
+                    g.ldy = n2;
+                    g.beta = 0;
+                    g.alpha = 1.f;
+                    pr[l] = g;
+                    mt = std::max(mt, ((n2 + 63) / 64) * ((n2 + 31) / 32));
+                }
+                HZ_CU(cudaStreamSynchronize(st));  // pr is reused below
+                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
+                launch_gemm<double2>(d_pr, L, mt, st, nl);
+                HZ_CU(cudaStreamSynchronize(st));
+            }
             if (j < C - 2) {  // V_j = W_j(:, nz:) K_{j+1}(1-rows, right part)
                 int mt = 0;
                 for (int l = 0; l < L; l++) {
@@ -429,6 +455,7 @@ void factor_all(hz_ctx *c) {
         c->dfree(d_ns);
     }
     c->dfree(K);
+    c->dfree(Zi);
 
     // 4. keep the operators in the working precision
     if (!c->mixed()) {
@@ -438,7 +465,7 @@ void factor_all(hz_ctx *c) {
         c->o64.E = E;
         c->o64.S = S;
         c->o64.W = Wi;
-        c->o64.Z = Zi;
+        c->o64.P = Pm;
         c->o64.V = Vi;
     } else {
         auto &o = c->o32;
@@ -454,12 +481,12 @@ void factor_all(hz_ctx *c) {
         to_f32(S, o.S, c->tot_S, st, nl);
         o.W = alloc_n<float2>(c, c->tot_Wi);
         to_f32(Wi, o.W, c->tot_Wi, st, nl);
-        o.Z = alloc_n<float2>(c, c->tot_Z);
-        to_f32(Zi, o.Z, c->tot_Z, st, nl);
+        o.P = alloc_n<float2>(c, c->tot_P);
+        to_f32(Pm, o.P, c->tot_P, st, nl);
         o.V = alloc_n<float2>(c, c->tot_V);
         to_f32(Vi, o.V, c->tot_V, st, nl);
         HZ_CU(cudaStreamSynchronize(st));
-        for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Zi, (void *)Vi})
+        for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi})
             c->dfree(q);
     }
     c->dfree(d_info);

@@ -4,6 +4,8 @@
 //     cell volume solves (local solves of Alg. inner_solver) and the inner
 //     compressed-block LU sweeps of Section 4.2.2
 //   * pivoted Gauss-Jordan inversion (offline, FP64)
+#include <cooperative_groups.h>
+
 #include "hz_common.cuh"
 
 namespace hz {
@@ -223,86 +225,184 @@ template void launch_cell_chain<double2>(const CellDesc *, int, const double2 *,
 template void launch_cell_chain<float2>(const CellDesc *, int, const float2 *, const float2 *, float2 *, int, int,
                                         cudaStream_t, int *);
 
-// ======================================================== inner chain ===
-// Block LU sweeps of a layer's inner SIE (Section 4.2.2).  Interface vectors
-// x_j (2 nz: a-column then b-column traces) live in slots j+1 of the layer's
-// inner buffer [(C+1) * 2nz][B]; on entry slot j+1 holds the right-hand side.
-//   forward : t = g_j (+ Z_j y_{j-1} on the a-half), y_j = W_j t
-//   backward: x_j = y_j + V_j x_{j+1}
-template <class T2, int NT>
-__global__ void __launch_bounds__(256) k_inner_chain(const LayerDesc *__restrict__ layers,
-                                                     const int *__restrict__ ids, const T2 *__restrict__ W,
-                                                     const T2 *__restrict__ Z, const T2 *__restrict__ V, T2 *inner,
+// ======================================================== inner sweep ===
+// Block-LU sweeps of a layer's inner SIE (Section 4.2.2) with inverted diagonal
+// blocks.  With h_j = W_j g_j computed beforehand for every interface (one
+// batched product) and P_j = W_j(:, 0:nz) Z_j precomputed offline, both sweeps
+// are the recurrence
+//   forward : y_0 = h_0,        y_j = h_j + P_j y_{j-1}   (j = 1..J-1)
+//   backward: x_{J-1} = y_{J-1}, x_j = y_j + V_j x_{j+1}   (j = J-2..0)
+// One thread-block cluster of R CTAs runs the recurrence of one layer for NB
+// right-hand sides: CTA r owns a slab of rows of every Q_j (prefetched into
+// registers one step ahead), computes its rows of z_j from the full z_{j-1}
+// kept in its shared memory, writes them to global memory and pushes them into
+// the shared memory of every CTA of the cluster (distributed shared memory);
+// one cluster barrier per step publishes z_j.  There are no spin waits.
+// Layout: slot j+1 of the layer's inner buffer holds interface j ([2nz][B]).
+template <class T2, int NB>
+__global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict__ layers,
+                                                     const int *__restrict__ ids, const T2 *__restrict__ P,
+                                                     const T2 *__restrict__ V, const T2 *__restrict__ H, T2 *X,
                                                      int B) {
+    namespace cg = cooperative_groups;
     extern __shared__ __align__(16) unsigned char smraw[];
+    cg::cluster_group cl = cg::this_cluster();
+    const int R = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int grp = blockIdx.x / R;
     const LayerDesc &ld = layers[ids[blockIdx.y]];
     const int nz = ld.nz, n2 = 2 * nz, J = ld.C - 1;
-    const int n0 = blockIdx.x * NT;
-    if (J <= 0 || n0 >= B) return;
-    T2 *tb = reinterpret_cast<T2 *>(smraw);
-    T2 *pb = tb + n2 * NT;
-    T2 *As = pb + n2 * NT;
-    T2 *iv = inner + ld.inner_off * (long long)B;
-    const int tid = threadIdx.x;
+    if (J <= 0) return;  // uniform over the cluster
+    const int n0 = grp * NB;
+    const int rs = (n2 + R - 1) / R;
+    const int r0 = min(n2, rank * rs), r1 = min(n2, r0 + rs), nr = r1 - r0;
+    T2 *zb0 = reinterpret_cast<T2 *>(smraw);
+    T2 *zb1 = zb0 + n2 * NB;
+    T2 *Qs = zb1 + n2 * NB;
     const long long slot = (long long)n2 * B;
-    for (int j = 0; j < J; j++) {
-        T2 *g = iv + (j + 1) * slot;
-        for (int e = tid; e < n2 * NT; e += 256) {
-            int m = e / NT, nn = e % NT;
-            tb[e] = (n0 + nn < B) ? g[(long long)m * B + n0 + nn] : czero<T2>();
-        }
-        __syncthreads();
-        if (j > 0) {
-            panel_gemm<T2, NT>(Z + ld.Z_off + (long long)j * nz * n2, n2, nz, n2, pb, As,
-                               [&](int m, int nn, T2 a) { tb[m * NT + nn] = tb[m * NT + nn] + a; });
-            __syncthreads();
-        }
-        panel_gemm<T2, NT>(W + ld.W_off + (long long)j * n2 * n2, n2, n2, n2, tb, As, [&](int m, int nn, T2 a) {
-            pb[m * NT + nn] = a;
-            if (n0 + nn < B) g[(long long)m * B + n0 + nn] = a;
-        });
-        __syncthreads();
+    const T2 *h = H + ld.inner_off * (long long)B;
+    T2 *x = X + ld.inner_off * (long long)B;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < n2 * NB; e += 256) {
+        int k = e / NB, n = e % NB;
+        zb0[e] = (n0 + n < B) ? h[slot + (long long)k * B + n0 + n] : czero<T2>();
     }
-    for (int j = J - 2; j >= 0; j--) {
-        T2 *y = iv + (j + 1) * slot;
-        panel_gemm<T2, NT>(V + ld.V_off + (long long)j * n2 * n2, n2, n2, n2, pb, As, [&](int m, int nn, T2 a) {
-            T2 x = czero<T2>();
-            if (n0 + nn < B) {
-                x = y[(long long)m * B + n0 + nn] + a;
-                y[(long long)m * B + n0 + nn] = x;
+    for (int e = tid; e < nr * NB; e += 256) {
+        int m = r0 + e / NB, n = e % NB;
+        if (n0 + n < B) x[slot + (long long)m * B + n0 + n] = h[slot + (long long)m * B + n0 + n];
+    }
+    const int S = 2 * (J - 1);
+    const int outs = nr * NB;
+    int ks = 1;
+    while (ks < 32 && outs * ks * 2 <= 256) ks *= 2;
+    constexpr int PF = 12;
+    const int nvec = (int)((long long)nr * n2 * sizeof(T2) / 16);
+    const bool use_pf = nvec <= 256 * PF;
+    int4 pf[PF];
+    auto qptr = [&](int s) -> const T2 * {
+        if (s < J - 1) return P + ld.P_off + (long long)(s + 1) * n2 * n2 + (long long)r0 * n2;
+        const int j = J - 2 - (s - (J - 1));
+        return V + ld.V_off + (long long)j * n2 * n2 + (long long)r0 * n2;
+    };
+    auto prefetch = [&](int s) {
+        if (s >= S || !use_pf) return;
+        const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
+#pragma unroll
+        for (int i = 0; i < PF; i++) {
+            int v = tid + 256 * i;
+            if (v < nvec) pf[i] = src[v];
+        }
+    };
+    prefetch(0);
+    cl.sync();  // every CTA of the cluster has started: remote shared memory is live
+    T2 *cur = zb0, *nxt = zb1;
+    for (int s = 0; s < S; s++) {
+        const bool fwd = s < J - 1;
+        const int j = fwd ? s + 1 : J - 2 - (s - (J - 1));
+        int4 *dq = reinterpret_cast<int4 *>(Qs);
+        if (use_pf) {
+#pragma unroll
+            for (int i = 0; i < PF; i++) {
+                int v = tid + 256 * i;
+                if (v < nvec) dq[v] = pf[i];
             }
-            tb[m * NT + nn] = x;
-        });
+        } else {
+            const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
+            for (int v = tid; v < nvec; v += 256) dq[v] = src[v];
+        }
         __syncthreads();
-        T2 *tmp = tb;
-        tb = pb;
-        pb = tmp;
+        prefetch(s + 1);
+        const T2 *base = (fwd ? h : x) + (long long)(j + 1) * slot;
+        T2 *out = x + (long long)(j + 1) * slot;
+        const int per = 256 / ks;
+        for (int o0 = 0; o0 < outs; o0 += per) {
+            const int o = o0 + tid / ks, kp = tid % ks;
+            T2 acc = czero<T2>();
+            int m = 0, n = 0;
+            if (o < outs) {
+                m = o / NB;
+                n = o % NB;
+                const T2 *q = Qs + m * n2;
+                for (int k = kp; k < n2; k += ks) cmac(acc, q[k], cur[k * NB + n]);
+            }
+            for (int off = ks >> 1; off > 0; off >>= 1) {
+                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+            }
+            if (o < outs && kp == 0) {
+                const int gm = r0 + m;
+                T2 v = czero<T2>();
+                if (n0 + n < B) {
+                    v = base[(long long)gm * B + n0 + n] + acc;
+                    out[(long long)gm * B + n0 + n] = v;
+                }
+                for (int q = 0; q < R; q++) {
+                    T2 *rem = cl.map_shared_rank(nxt, q);
+                    rem[gm * NB + n] = v;
+                }
+            }
+        }
+        cl.sync();
+        T2 *t = cur;
+        cur = nxt;
+        nxt = t;
     }
 }
 
-template <class T2, int NT>
-static void inner_chain_nt(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *W, const T2 *Z,
-                           const T2 *V, T2 *inner, int B, int max_nz2, cudaStream_t st) {
-    size_t sm = (size_t)(2 * max_nz2 * NT + 64 * (PK + 1)) * sizeof(T2);
-    HZ_CU(cudaFuncSetAttribute(k_inner_chain<T2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((B + NT - 1) / NT, nlayer);
-    k_inner_chain<T2, NT><<<grid, 256, sm, st>>>(d_layers, ids, W, Z, V, inner, B);
-    HZ_CU(cudaGetLastError());
+template <class T2, int NB>
+static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
+                           const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st) {
+    const int groups = (B + NB - 1) / NB;
+    auto smem = [&](int R) { return (size_t)(2 * max_n2 * NB + ((max_n2 + R - 1) / R) * max_n2) * sizeof(T2); };
+    // smallest cluster whose row slab fits in shared memory
+    int Rmin = 1;
+    while (Rmin <= 16 && smem(Rmin) > 220 * 1024) Rmin *= 2;
+    if (Rmin > 16) return false;
+    // preferred: enough CTAs to fill the GPU when few chains are in flight
+    int R = Rmin;
+    while (R < 16 && (long long)groups * nlayer * R * 2 <= 304) R *= 2;
+    auto kern = k_inner_sweep<T2, NB>;
+    HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // largest cluster the device can co-schedule
+    for (; R >= Rmin; R /= 2) {
+        cfg.dynamicSmemBytes = smem(R);
+        HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.dynamicSmemBytes));
+        attr[0].val.clusterDim.x = R;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(R * groups, nlayer, 1);
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) == cudaSuccess && ncl > 0) break;
+        cudaGetLastError();
+    }
+    if (R < Rmin) return false;
+    HZ_CU(cudaLaunchKernelEx(&cfg, kern, d_layers, ids, P, V, H, X, B));
+    return true;
 }
 
 template <class T2>
-void launch_inner_chain(const LayerDesc *d_layers, const int *d_ids, int nlayer, const T2 *W, const T2 *Z,
-                        const T2 *V, T2 *inner, int B, int max_nz2, cudaStream_t st, int *nl) {
+void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
+                        const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st, int *nl) {
     if (nlayer <= 0 || B <= 0) return;
-    if ((long long)nlayer * ((B + 15) / 16) >= 64 || B <= 4)
-        inner_chain_nt<T2, 16>(d_layers, d_ids, nlayer, W, Z, V, inner, B, max_nz2, st);
+    bool ok;
+    if ((long long)((B + 7) / 8) * nlayer * 16 <= 304)
+        ok = inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st);
     else
-        inner_chain_nt<T2, 4>(d_layers, d_ids, nlayer, W, Z, V, inner, B, max_nz2, st);
+        ok = inner_sweep_nb<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st) ||
+             inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st);
+    if (!ok) throw HzError(HZ_ENOMEM, "inner sweep: interface blocks too large for shared memory");
     if (nl) (*nl)++;
 }
-template void launch_inner_chain<double2>(const LayerDesc *, const int *, int, const double2 *, const double2 *,
+template void launch_inner_sweep<double2>(const LayerDesc *, const int *, int, const double2 *, const double2 *,
                                           const double2 *, double2 *, int, int, cudaStream_t, int *);
-template void launch_inner_chain<float2>(const LayerDesc *, const int *, int, const float2 *, const float2 *,
+template void launch_inner_sweep<float2>(const LayerDesc *, const int *, int, const float2 *, const float2 *,
                                          const float2 *, float2 *, int, int, cudaStream_t, int *);
 
 // ============================================== offline: coefficients ===

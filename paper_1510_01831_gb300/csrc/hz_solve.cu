@@ -582,12 +582,13 @@ template <class T2> static void cell_chain_cost(hz_ctx *c, int N, double &bytes,
     }
 }
 template <class T2> static void inner_chain_cost(hz_ctx *c, int l0, int nl, int N, double &bytes, double &flops) {
+    // the recurrence part (P_j and V_j products); h_j = W_j g_j is counted with the GEMMs
     const double es = sizeof(T2);
     bytes = flops = 0;
     for (int l = l0; l < l0 + nl; l++) {
-        const double J = c->C - 1, nz = c->layers[l].nz, n2 = 2 * nz;
-        if (J <= 0) continue;
-        const double ent = J * n2 * n2 + (J - 1) * nz * n2 + (J - 1) * n2 * n2;
+        const double J = c->C - 1, n2 = 2.0 * c->layers[l].nz;
+        if (J <= 1) continue;
+        const double ent = 2 * (J - 1) * n2 * n2;
         bytes += es * (ent + 4 * J * n2 * N);
         flops += 8.0 * ent * N;
     }
@@ -706,6 +707,47 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         lb.add_ES(l, 0, in, B, 3, out, B, W.inner, B, B, 1);
     }
     W.e_newton = lb.finish();
+    // h_j = W_j g_j for every interface, ordered by layer (B wide and 2B wide)
+    W.hoff.assign(L + 1, 0);
+    W.hbytes.assign(L, 0.0);
+    W.hflops.assign(L, 0.0);
+    for (int wide = 0; wide < 2; wide++) {
+        const int Bw = wide ? 2 * B : B;
+        T2 *gin = wide ? W.inner2 : W.inner;
+        T2 *hout = wide ? W.innerH2 : W.innerH;
+        int cnt = 0;
+        for (int l = 0; l < L; l++) {
+            const LayerDesc &ld = c->layers[l];
+            const int n2 = 2 * ld.nz;
+            if (!wide) W.hoff[l] = cnt;
+            double b0 = lb.bytes, f0 = lb.flops;
+            for (int j = 0; j < c->C - 1; j++) {
+                GemmProb<T2> g{};
+                g.A = o.W + ld.W_off + (long long)j * n2 * n2;
+                g.lda = n2;
+                g.M = n2;
+                g.K = n2;
+                g.N = Bw;
+                g.xseg = g.yseg = 1 << 30;
+                g.ldx = g.ldy = Bw;
+                g.X[0] = gin + (ld.inner_off + (long long)(j + 1) * n2) * Bw;
+                g.Y[0] = hout + (ld.inner_off + (long long)(j + 1) * n2) * Bw;
+                g.beta = 0;
+                g.alpha = 1.f;
+                lb.push(g);
+                cnt++;
+            }
+            if (!wide) {
+                W.hbytes[l] = lb.bytes - b0;
+                W.hflops[l] = lb.flops - f0;
+            }
+        }
+        if (!wide) W.hoff[L] = cnt;
+        if (wide)
+            W.h2B = lb.finish();
+        else
+            W.hB = lb.finish();
+    }
     // single-layer applications (component entry point), inputs/outputs in lin/lout (B wide)
     W.f_layer.assign(L, ProbList<T2>());
     W.es_layer.assign(L, ProbList<T2>());
@@ -728,7 +770,7 @@ template <> std::unique_ptr<Work<double2>> &work_slot<double2>(hz_ctx *c) { retu
 template <> std::unique_ptr<Work<float2>> &work_slot<float2>(hz_ctx *c) { return c->w32; }
 
 template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
-    void *ptrs[] = {W.vol, W.vol2, W.inner, W.inner2, W.inner_f, W.lin, W.lout, W.pa, W.pb, W.pc, W.Z, W.V, W.w64,
+    void *ptrs[] = {W.vol, W.vol2, W.inner, W.inner2, W.inner_f, W.innerH, W.innerH2, W.lin, W.lout, W.pa, W.pb, W.pc, W.Z, W.V, W.w64,
                     W.rhs64, W.x64, W.dots, W.hbuf, W.gsrc, W.u, W.io, W.rnorm};
     for (void *q : ptrs) c->dfree(q);
     auto fl = [&](ProbList<T2> &pl) { c->dfree(pl.d); };
@@ -738,6 +780,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.es_refl);
     fl(W.f_rec);
     fl(W.e_newton);
+    fl(W.hB);
+    fl(W.h2B);
     for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer})
         for (auto &pl : *vv) fl(pl);
     if (W.hhost) cudaFreeHost(W.hhost);
@@ -763,6 +807,8 @@ template <class T2> Work<T2> &work(hz_ctx *c, int B) {
     W.inner = (T2 *)al(c->tot_inner * B, sizeof(T2));
     W.inner2 = (T2 *)al(c->tot_inner * 2 * B, sizeof(T2));
     W.inner_f = (T2 *)al(c->tot_inner * B, sizeof(T2));
+    W.innerH = (T2 *)al(c->tot_inner * B, sizeof(T2));
+    W.innerH2 = (T2 *)al(c->tot_inner * 2 * B, sizeof(T2));
     HZ_CU(cudaMemset(W.inner, 0, sizeof(T2) * c->tot_inner * B));
     HZ_CU(cudaMemset(W.inner2, 0, sizeof(T2) * c->tot_inner * 2 * B));
     HZ_CU(cudaMemset(W.inner_f, 0, sizeof(T2) * c->tot_inner * B));
@@ -792,14 +838,27 @@ template Work<double2> &work<double2>(hz_ctx *, int);
 template Work<float2> &work<float2>(hz_ctx *, int);
 
 // ------------------------------------------------------- layer pieces ---
-template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, T2 *inner, int l0, int nl, int N) {
+// inner solve of layers [l0, l0+nl): h_j = W_j g_j (batched GEMM) then the
+// block-LU recurrences; `wide` selects the 2B-wide buffers of the polarized operator
+template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, int l0, int nl) {
     if (c->C < 2) return;
     Ops<T2> &o = ops<T2>(c);
+    const ProbList<T2> &all = wide ? W.h2B : W.hB;
+    ProbList<T2> sub = all;
+    sub.d = all.d + W.hoff[l0];
+    sub.n = W.hoff[l0 + nl] - W.hoff[l0];
+    sub.bytes = sub.flops = 0;
+    for (int l = l0; l < l0 + nl; l++) {
+        sub.bytes += W.hbytes[l] * (wide ? 2 : 1);
+        sub.flops += W.hflops[l] * (wide ? 2 : 1);
+    }
+    run(c, sub);
+    const int N = wide ? 2 * W.B : W.B;
     double by = 0, fl = 0;
     if (c->opts.time_kernels) inner_chain_cost<T2>(c, l0, nl, N, by, fl);
     c->kt_begin(1, by, fl);
-    launch_inner_chain<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.W, o.Z, o.V, inner, N, 2 * c->max_nz, c->st,
-                           &c->nl);
+    launch_inner_sweep<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.P, o.V, wide ? W.innerH2 : W.innerH,
+                           wide ? W.inner2 : W.inner, N, 2 * c->max_nz, c->st, &c->nl);
     c->kt_end();
 }
 
@@ -811,7 +870,7 @@ template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, dou
     HZ_CU(cudaGetLastError());
     c->nl++;
     run(c, W.f_full);
-    chain_layers(c, W, W.inner2, 0, c->L, 2 * B);
+    chain_layers(c, W, true, 0, c->L);
     run(c, W.es_bot_A);
     const long long m = c->n_tr() * B;
     k_combine_M<T2><<<grid1(m), 256, 0, c->st>>>(x, W.lout, y, c->L, c->NX, B);
@@ -826,7 +885,7 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
     if (kind == 0 || kind == 1 || kind == 2) {
         for (int k = 1; k <= L - 2; k++) {
             run(c, W.f_down[k]);
-            chain_layers(c, W, W.inner, k, 1, W.B);
+            chain_layers(c, W, false, k, 1);
             run(c, W.es_down[k]);
         }
     }
@@ -841,7 +900,7 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
         HZ_CU(cudaGetLastError());
         c->nl++;
         run(c, W.f_refl);
-        chain_layers(c, W, W.inner, 1, L - 1, W.B);
+        chain_layers(c, W, false, 1, L - 1);
         run(c, W.es_refl);
         if (kind == 4) {
             k_refl_finish<T2><<<grid1((long long)(L - 1) * c->NX * W.B), 256, 0, c->st>>>(W.pb, L - 1, c->NX, W.B);
@@ -852,7 +911,7 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
     if (kind == 0 || kind == 1 || kind == 3) {
         for (int k = L - 3; k >= 0; k--) {
             run(c, W.f_up[k]);
-            chain_layers(c, W, W.inner, k + 1, 1, W.B);
+            chain_layers(c, W, false, k + 1, 1);
             run(c, W.es_up[k]);
         }
     }
@@ -1091,7 +1150,7 @@ static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double t
     }
     // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
-    if (c->C > 1) chain_layers(c, W, W.inner, 0, L, B);
+    chain_layers(c, W, false, 0, L);
     k_samples<T2><<<dim3(64, ncell), 256, 0, st>>>(c->d_cells, W.vol, W.lout, c->NX, B, c->p);
     HZ_CU(cudaGetLastError());
     c->nl++;
@@ -1112,7 +1171,7 @@ static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double t
     c->nl++;
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
     run(c, W.f_rec);
-    if (c->C > 1) chain_layers(c, W, W.inner, 0, L, B);
+    chain_layers(c, W, false, 0, L);
     k_recon_src<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, c->d_layers, W.pc, W.inner, W.vol2, L, c->NX, B, c->p,
                                                      c->h, c->pml_C, c->omega);
     HZ_CU(cudaGetLastError());
@@ -1257,7 +1316,7 @@ template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_de
     HZ_CU(cudaGetLastError());
     c->nl++;
     run(c, W.f_layer[l]);
-    if (c->C > 1) chain_layers(c, W, W.inner, l, 1, B);
+    chain_layers(c, W, false, l, 1);
     run(c, W.es_layer[l]);
     T2 *lout_l = W.lout + (long long)l * 4 * rowsz;
     k_cast<T2, double2><<<grid1(n4 * B), 256, 0, c->st>>>(lout_l, W.io, n4 * B);

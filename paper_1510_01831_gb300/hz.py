@@ -27,8 +27,8 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
 
 # every entry point declared in include/hz.h
 EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_gradient", "hz_cell_solve",
-           "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_set_device_ptrs", "hz_device_bytes",
-           "hz_destroy", "hz_last_error"]
+           "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual",
+           "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
 
 class HzError(RuntimeError):
