@@ -172,6 +172,23 @@ hz_status hz_precond(hz_ctx *ctx, int which, const double *x, int B, double *y);
  * or device per device_ptrs). */
 hz_status hz_residual(hz_ctx *ctx, const double *u, const double *f, int B, double *res);
 
+/* Allocation-free variant of hz_residual, for callers that cannot allocate
+ * device memory when they need the residual (their device memory is reserved
+ * up front by another allocator, or their loop forbids allocation calls,
+ * which synchronise the device).  The paper has no counterpart.
+ *   u, f : device pointers, [B][n_z+2p][n_x+2p] complex (read in place);
+ *   res  : device pointer, [B] relative residuals ||H u - f||_2 / ||f||_2,
+ *          as hz_residual computes them.
+ * Makes no cudaMalloc/cudaFree or allocating library call.  Its scratch is a
+ * fixed 512 KiB device array inside the library (every GPU that loads it
+ * holds it until exit), so B is limited to 256 (HZ_EINVAL beyond).  The first
+ * call on each device looks up that array's device address; make that first
+ * call before any stream capture.  The work is enqueued on the context's
+ * stream and res is valid once the stream reaches it.  All calls share the
+ * scratch array: calls whose kernels overlap on the GPU race.
+ * Errors: HZ_EINVAL (NULL pointer, B out of 1..256), HZ_ECUDA. */
+hz_status hz_residual_noalloc(hz_ctx *ctx, const double *u, const double *f, int B, double *res);
+
 /* Switch the pointer mode of later calls (same meaning as opts.device_ptrs). */
 hz_status hz_set_device_ptrs(hz_ctx *ctx, int device_ptrs);
 

@@ -27,7 +27,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
 
 # every entry point declared in include/hz.h
 EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_gradient", "hz_cell_solve",
-           "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual",
+           "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
            "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
 
@@ -91,6 +91,8 @@ def load() -> ctypes.CDLL:
             L.hz_apply_M.argtypes = [vp, vp, i, vp]
             L.hz_precond.argtypes = [vp, i, vp, i, vp]
             L.hz_residual.argtypes = [vp, vp, vp, i, vp]
+            L.hz_residual_noalloc.argtypes = [vp, vp, vp, i, vp]
+            L.hz_residual_noalloc.restype = ctypes.c_int
             L.hz_set_device_ptrs.argtypes = [vp, i]
             L.hz_set_device_ptrs.restype = ctypes.c_int
             L.hz_device_bytes.argtypes = [vp]
@@ -260,6 +262,16 @@ class Context:
         _check(load().hz_residual(self._ctx, _ptr(u, self.device), _ptr(f, self.device), B, _ptr(r, self.device)),
                self._ctx)
         return r
+
+    def hz_residual_noalloc(self, u, f, res):
+        """Allocation-free residual: u, f, res must be CUDA tensors (res: float64 [B]).
+        Enqueued on the context's stream; no device memory is allocated."""
+        for a in (u, f, res):
+            if not (hasattr(a, "data_ptr") and a.is_cuda and a.is_contiguous()):
+                raise TypeError("hz_residual_noalloc expects contiguous CUDA tensors")
+        _check(load().hz_residual_noalloc(self._ctx, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(f.data_ptr()),
+                                          int(f.shape[0]), ctypes.c_void_p(res.data_ptr())), self._ctx)
+        return res
 
     def hz_set_device_ptrs(self, device: bool):
         _check(load().hz_set_device_ptrs(self._ctx, 1 if device else 0), self._ctx)
