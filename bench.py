@@ -36,6 +36,8 @@ WORKLOADS = {
     "smooth1024": dict(n=1024, n_pml=20, L=16, C=16, B=64, ppw=10.0, seed=2),
     "smooth512": dict(n=512, n_pml=20, L=8, C=8, B=32, ppw=10.0, seed=5),
     "smooth256": dict(n=256, n_pml=16, L=8, C=4, B=16, ppw=10.0, seed=2),
+    # same per-launch shapes as smooth1024 (64-row layers, 64-column cells, 20-point PML, 64 sources)
+    "smooth256_shape1024": dict(n=256, n_pml=20, L=4, C=4, B=64, ppw=10.0, seed=2),
 }
 METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
 UNIT = "RHS*Mdof/s"

@@ -90,6 +90,9 @@ struct hz_ctx {
     // global medium and PML profiles (FP64)
     double *d_m = nullptr;
     double2 *d_ax = nullptr, *d_axh = nullptr, *d_az = nullptr, *d_azh = nullptr;
+    // row-scaled global operator: diagonal, +x and +z couplings, and alpha_x alpha_z (FP64)
+    double2 *d_gdiag = nullptr, *d_gcx = nullptr, *d_gcz = nullptr, *d_gD = nullptr;
+    hz::CellDesc *d_gcell = nullptr;
     // operators
     hz::Ops<double2> o64;
     hz::Ops<float2> o32;
