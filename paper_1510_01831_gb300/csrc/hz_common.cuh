@@ -79,7 +79,8 @@ struct CellDesc {
     int own_lo, no;      // owned local columns [own_lo, own_lo + no)
     int row_lo, row_hi;  // owned local rows [row_lo, row_hi) of the layer
     long long vol_off;   // cell volume buffer offset (in grid points; x B for RHS-major)
-    long long w_off;     // block-tridiagonal inverse blocks: nz blocks of nx*nx
+    long long w_off;     // block-tridiagonal inverse blocks: nz blocks of nx rows x ldw (row stride)
+    int ldw;             // row stride of the W blocks: nx rounded up to even (16-byte rows for async copies)
     long long cz_off;    // z-couplings between consecutive rows: (nz-1) x nx
     long long F_off;     // F: (2 nz) x (4 no)
     long long E_off;     // E: (4 no) x (4 nz)
@@ -96,6 +97,7 @@ struct LayerDesc {
     long long W_off;     // C-1 blocks (2nz)^2
     long long P_off;     // C-1 blocks (2nz)^2: P_j = W_j(:, 0:nz) Z_j (slot 0 unused)
     long long V_off;     // C-1 blocks (2nz)^2 (last unused)
+    long long zoff;      // offset of the layer's per-row arrays (nz entries)
 };
 
 // Batched, segmented complex GEMM problem:  Y (+)= alpha (A X + A2 X2)

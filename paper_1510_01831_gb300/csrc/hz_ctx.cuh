@@ -92,6 +92,10 @@ struct hz_ctx {
     double2 *d_ax = nullptr, *d_axh = nullptr, *d_az = nullptr, *d_azh = nullptr;
     // row-scaled global operator: diagonal, +x and +z couplings, and alpha_x alpha_z (FP64)
     double2 *d_gdiag = nullptr, *d_gcx = nullptr, *d_gcz = nullptr, *d_gD = nullptr;
+    double2 *d_ginvD = nullptr;  // 1 / (alpha_x alpha_z)
+    double2 *d_ggam = nullptr;   // -1 / (alpha_x h^2) per global column (z coupling at interface rows)
+    double2 *d_lbeta = nullptr;  // -1 / (alpha_z h^2) per layer row, layer-local PML (x coupling at cell interfaces)
+    long long tot_z = 0;
     hz::CellDesc *d_gcell = nullptr;
     // operators
     hz::Ops<double2> o64;

@@ -40,6 +40,7 @@ void build_decomposition(hz_ctx *c) {
     const int p = c->p, L = c->L, C = c->C;
     c->cells.clear();
     c->layers.clear();
+    c->tot_z = 0;
     long long vol = 0, Wc = 0, F = 0, E = 0, S = 0, K = 0, inner = 0, Wi = 0, Pi = 0, V = 0;
     int s = 0;
     c->max_nx = c->max_nz = c->max_no = 0;
@@ -52,6 +53,8 @@ void build_decomposition(hz_ctx *c) {
         ld.row_lo = (l == 0) ? 0 : p;
         ld.row_hi = (l == L - 1) ? ld.n + 2 * p : ld.n + p;
         ld.cell0 = (int)c->cells.size();
+        ld.zoff = c->tot_z;
+        c->tot_z += ld.n + 2 * p;
         ld.inner_off = inner;
         inner += (long long)(C + 1) * 2 * ld.nz;
         const long long n2 = 2LL * ld.nz;
@@ -85,7 +88,8 @@ void build_decomposition(hz_ctx *c) {
             cd.cz_off = vol;
             vol += (long long)cd.nx * cd.nz;
             cd.w_off = Wc;
-            Wc += (long long)cd.nz * cd.nx * cd.nx;
+            cd.ldw = (cd.nx + 1) & ~1;
+            Wc += (long long)cd.nz * cd.nx * cd.ldw;
             cd.F_off = F;
             F += 2LL * cd.nz * 4 * cd.no;
             cd.E_off = E;
@@ -291,6 +295,7 @@ void factor_all(hz_ctx *c) {
     double2 *czv = alloc_n<double2>(c, c->tot_vol);
     launch_cell_coeffs(c->d_cells, ncell, c->d_m, c->NX, c->omega, c->h, c->pml_C, p, diag, cxv, czv, st, nl);
     double2 *cellW = alloc_n<double2>(c, c->tot_W);
+    HZ_CU(cudaMemsetAsync(cellW, 0, sizeof(double2) * c->tot_W, st));  // row padding stays zero
     launch_cell_factor(c->d_cells, ncell, diag, cxv, czv, cellW, c->max_nx, d_info, st, nl);
     check_info(d_info, st, "cell factorization");
     c->dfree(diag);

@@ -15,20 +15,28 @@ constexpr int GBM = 64, GBN = 32, GBK = 16;
 
 template <class T2>
 __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ probs) {
-    const GemmProb<T2> &P = probs[blockIdx.y];
+    __shared__ GemmProb<T2> P;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    T2 (*As)[GBK][GBM + 1] = reinterpret_cast<T2 (*)[GBK][GBM + 1]>(gsm);
+    T2 (*Xs)[GBK][GBN] = reinterpret_cast<T2 (*)[GBK][GBN]>(gsm + sizeof(T2) * 2 * GBK * (GBM + 1));
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    if (tid == 0) P = probs[blockIdx.y];
+    __syncthreads();
     const int M = P.M, N = P.N;
     const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
     const int tile = blockIdx.x;
     if (tile >= tilesM * tilesN) return;
     const int m0 = (tile % tilesM) * GBM, n0 = (tile / tilesM) * GBN;
-    __shared__ T2 As[GBK][GBM + 1];
-    __shared__ T2 Xs[GBK][GBN];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     T2 acc[4][2];
 #pragma unroll
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) acc[i][j] = czero<T2>();
+    // load slots of this thread: A elements (mm, kk) for q = 0..3, X elements (kk, nn) for q = 0..1
+    const int a_kk = tid % GBK, a_mm = tid / GBK;  // + 16 q rows
+    const int x_nn = tid % GBN, x_kk = tid / GBN;  // + 8 q rows
+    T2 ra[4], rx[2];
+    int buf = 0;
     for (int pass = 0; pass < 2; pass++) {
         const T2 *A = pass ? P.A2 : P.A;
         const long long lda = pass ? P.lda2 : P.lda;
@@ -36,49 +44,57 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         const int xseg = pass ? P.xseg2 : P.xseg;
         const long long ldx = pass ? P.ldx2 : P.ldx;
         const T2 *const *Xp = pass ? P.X2 : P.X;
-        for (int k0 = 0; k0 < K; k0 += GBK) {
+        if (K <= 0) continue;
+        auto load = [&](int k0) {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                int e = tid + 256 * q, mm = e / GBK, kk = e % GBK;
-                int gm = m0 + mm, gk = k0 + kk;
-                As[kk][mm] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
+                const int gm = m0 + a_mm + 16 * q, gk = k0 + a_kk;
+                ra[q] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
             }
 #pragma unroll
             for (int q = 0; q < 2; q++) {
-                int e = tid + 256 * q, kk = e / GBN, nn = e % GBN;
-                int gk = k0 + kk, gn = n0 + nn;
+                const int gk = k0 + x_kk + 8 * q, gn = n0 + x_nn;
                 T2 v = czero<T2>();
                 if (gk < K && gn < N) {
-                    const T2 *row = Xp[gk / xseg] + (long long)(gk % xseg) * ldx;
-                    v = row[gn];
+                    const int sg = gk / xseg;
+                    v = Xp[sg][(long long)(gk - sg * xseg) * ldx + gn];
                 }
-                Xs[kk][nn] = v;
+                rx[q] = v;
             }
+        };
+        load(0);
+        for (int k0 = 0; k0 < K; k0 += GBK) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) As[buf][a_kk][a_mm + 16 * q] = ra[q];
+#pragma unroll
+            for (int q = 0; q < 2; q++) Xs[buf][x_kk + 8 * q][x_nn] = rx[q];
             __syncthreads();
+            if (k0 + GBK < K) load(k0 + GBK);  // in flight during the products below
 #pragma unroll
             for (int kk = 0; kk < GBK; kk++) {
                 T2 a[4], x[2];
 #pragma unroll
-                for (int i = 0; i < 4; i++) a[i] = As[kk][ty + 16 * i];
+                for (int i = 0; i < 4; i++) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 2; j++) x[j] = Xs[kk][tx + 16 * j];
+                for (int j = 0; j < 2; j++) x[j] = Xs[buf][kk][tx + 16 * j];
 #pragma unroll
                 for (int i = 0; i < 4; i++)
 #pragma unroll
                     for (int j = 0; j < 2; j++) cmac(acc[i][j], a[i], x[j]);
             }
-            __syncthreads();
+            buf ^= 1;  // the other buffer is free: every thread passed this chunk's barrier
         }
     }
     const float al = P.alpha;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
-        int m = m0 + ty + 16 * i;
+        const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
-        T2 *row = P.Y[m / P.yseg] + (long long)(m % P.yseg) * P.ldy;
+        const int sg = m / P.yseg;
+        T2 *row = P.Y[sg] + (long long)(m - sg * P.yseg) * P.ldy;
 #pragma unroll
         for (int j = 0; j < 2; j++) {
-            int n = n0 + tx + 16 * j;
+            const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             T2 v = acc[i][j];
             v.x *= al;
@@ -92,132 +108,216 @@ template <class T2>
 void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, cudaStream_t st, int *nl) {
     if (nprob <= 0 || max_tiles <= 0) return;
     dim3 grid(max_tiles, nprob);
-    k_gemm<T2><<<grid, 256, 0, st>>>(d_probs);
+    const size_t sm = sizeof(T2) * 2 * GBK * (GBM + 1 + GBN);
+    static bool attr = false;
+    if (!attr) {
+        HZ_CU(cudaFuncSetAttribute(k_gemm<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    k_gemm<T2><<<grid, 256, sm, st>>>(d_probs);
     HZ_CU(cudaGetLastError());
     if (nl) (*nl)++;
 }
 template void launch_gemm<double2>(const GemmProb<double2> *, int, int, cudaStream_t, int *);
 template void launch_gemm<float2>(const GemmProb<float2> *, int, int, cudaStream_t, int *);
 
-// ========================================================= panel GEMM ===
-// out(m, n) <- sum_k A[m][k] * ts[k][n] for m < M, n < NT; A row-major in
-// global memory (staged through shared memory in 64 x 32 tiles), ts a
-// K x NT panel in shared memory.  256 threads; each thread owns one column n
-// and RPT rows of every 64-row tile.
-constexpr int PK = 32;
-
-template <class T2, int NT, class Epi>
-__device__ __forceinline__ void panel_gemm(const T2 *__restrict__ A, long long lda, int M, int K,
-                                           const T2 *ts, T2 *As, Epi epi) {
-    constexpr int TPC = 256 / NT;
-    constexpr int RPT = 64 / TPC;
-    const int tid = threadIdx.x, n = tid % NT, r0 = tid / NT;
-    for (int m0 = 0; m0 < M; m0 += 64) {
-        T2 acc[RPT];
-#pragma unroll
-        for (int r = 0; r < RPT; r++) acc[r] = czero<T2>();
-        for (int k0 = 0; k0 < K; k0 += PK) {
-            for (int e = tid; e < 64 * PK; e += 256) {
-                int mm = e / PK, kk = e % PK;
-                int gm = m0 + mm, gk = k0 + kk;
-                As[mm * (PK + 1) + kk] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
-            }
-            __syncthreads();
-            const int kmax = min(PK, K - k0);
-            for (int kk = 0; kk < kmax; kk++) {
-                T2 tv = ts[(k0 + kk) * NT + n];
-#pragma unroll
-                for (int r = 0; r < RPT; r++) cmac(acc[r], As[(r0 + TPC * r) * (PK + 1) + kk], tv);
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int r = 0; r < RPT; r++) {
-            int m = m0 + r0 + TPC * r;
-            if (m < M) epi(m, n, acc[r]);
-        }
-    }
-}
-
 // ========================================================= cell chain ===
-// Solve H^{l,c} x = g for every cell and RHS tile.  H^{l,c} is block
+// Solve H^{l,c} x = g for every cell and RHS group.  H^{l,c} is block
 // tridiagonal over grid rows with diagonal couplings cz between rows; with
 // W_j the inverse of the j-th Schur complement:
 //   y_0 = W_0 g_0,  y_j = W_j (g_j - cz_{j-1} . y_{j-1})
 //   x_{nz-1} = y_{nz-1},  x_j = y_j - W_j (cz_j . x_{j+1})
+// One CTA per (cell, NT columns).  The W blocks are streamed through a
+// ST-stage ring of CH-row chunks with cp.async; the chunk sequence (forward
+// W_0..W_{nz-1}, then backward W_{nz-2}..W_0) is known in advance, so the
+// prefetch runs ahead across step boundaries.  Each thread owns a
+// (CH/16) x (NT/16) tile of complex outputs.
 // vol layout: [cell vol_off + jz*nx + jx][B] (RHS innermost), in place.
-template <class T2, int NT>
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+template <class T2, int NT, int CH, int ST>
 __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__ cells, const T2 *__restrict__ W,
                                                     const T2 *__restrict__ cz, T2 *vol, int B) {
+    constexpr int TM = CH / 16, TN = NT / 16;
+    constexpr int GP = 16;  // register-prefetch slots per thread for the next step's global vector
     extern __shared__ __align__(16) unsigned char smraw[];
     const CellDesc &cd = cells[blockIdx.y];
-    const int nx = cd.nx, nz = cd.nz;
+    const int nx = cd.nx, nz = cd.nz, ldw = cd.ldw;
     const int n0 = blockIdx.x * NT;
     if (n0 >= B) return;
-    T2 *tb = reinterpret_cast<T2 *>(smraw);
-    T2 *pb = tb + nx * NT;
-    T2 *As = pb + nx * NT;
+    T2 *tbuf0 = reinterpret_cast<T2 *>(smraw);  // t of the current step
+    T2 *tbuf1 = tbuf0 + nx * NT;                // t of the next step (built by the epilogue)
+    T2 *gb = tbuf1 + nx * NT;                   // global vector used by this step's epilogue
+    T2 *ring = gb + nx * NT;
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    const int nch = (nx + CH - 1) / CH;
+    const int nsteps = 2 * nz - 1;
+    const int total = nsteps * nch;
     const T2 *Wc = W + cd.w_off;
     const T2 *czc = cz + cd.cz_off;
     T2 *v = vol + cd.vol_off * (long long)B;
-    const int tid = threadIdx.x;
     const long long rs = (long long)nx * B;
-    for (int jz = 0; jz < nz; jz++) {
-        T2 *g = v + jz * rs;
-        for (int e = tid; e < nx * NT; e += 256) {
-            int jx = e / NT, nn = e % NT;
-            T2 val = czero<T2>();
-            if (n0 + nn < B) {
-                val = g[(long long)jx * B + n0 + nn];
-                if (jz > 0) val = val - czc[(long long)(jz - 1) * nx + jx] * pb[e];
-            }
-            tb[e] = val;
+    auto jb_of = [&](int s) { return s < nz ? s : 2 * nz - 2 - s; };
+    auto issue = [&](int q) {
+        if (q < total) {
+            const int s = q / nch, c = q % nch;
+            const int jb = jb_of(s);
+            const int rows = min(CH, nx - c * CH);
+            const char *src = reinterpret_cast<const char *>(Wc + (long long)jb * nx * ldw + (long long)c * CH * ldw);
+            char *dst = reinterpret_cast<char *>(ring + (q % ST) * CH * ldw);
+            const int nbytes = rows * ldw * (int)sizeof(T2);
+            for (int off = tid * 16; off < nbytes; off += 256 * 16) cp_async16(dst + off, src + off);
         }
-        __syncthreads();
-        panel_gemm<T2, NT>(Wc + (long long)jz * nx * nx, nx, nx, nx, tb, As, [&](int m, int nn, T2 a) {
-            pb[m * NT + nn] = a;
-            if (n0 + nn < B) g[(long long)m * B + n0 + nn] = a;
-        });
-        __syncthreads();
-    }
-    for (int jz = nz - 2; jz >= 0; jz--) {
-        for (int e = tid; e < nx * NT; e += 256) {
-            int jx = e / NT;
-            tb[e] = czc[(long long)jz * nx + jx] * pb[e];
-        }
-        __syncthreads();
-        T2 *y = v + jz * rs;
-        panel_gemm<T2, NT>(Wc + (long long)jz * nx * nx, nx, nx, nx, tb, As, [&](int m, int nn, T2 a) {
-            T2 x = czero<T2>();
-            if (n0 + nn < B) {
-                x = y[(long long)m * B + n0 + nn] - a;
-                y[(long long)m * B + n0 + nn] = x;
+        cp_async_commit();
+    };
+    // the global vector an epilogue needs: forward step s -> g of step s+1 (to form t_{s+1});
+    // backward step s -> y of step s (x = y - W t).  Both live at v + jb*rs.
+    auto gvec_step = [&](int s) -> int {
+        if (s < nz - 1) return s + 1;  // forward, next forward step's source
+        if (s < nz) return -1;         // last forward step: t of the first backward step needs no global data
+        return s;                      // backward: its own y
+    };
+    const int nel = nx * NT;
+    const bool gp_ok = nel <= 256 * GP;
+    T2 greg[GP];
+    auto gprefetch = [&](int s) {
+        const int sg = (s < nsteps) ? gvec_step(s) : -1;
+        if (sg < 0) return;
+        const T2 *src = v + jb_of(sg) * rs;
+        if (gp_ok) {
+#pragma unroll
+            for (int i = 0; i < GP; i++) {
+                const int e = tid + 256 * i;
+                if (e < nel) {
+                    const int jx = e / NT, nn = e % NT;
+                    greg[i] = (n0 + nn < B) ? src[(long long)jx * B + n0 + nn] : czero<T2>();
+                }
             }
-            pb[m * NT + nn] = x;
-        });
-        __syncthreads();
+        }
+    };
+    auto gstage = [&](int s) {  // registers (or global) -> gb
+        const int sg = (s < nsteps) ? gvec_step(s) : -1;
+        if (sg < 0) return;
+        if (gp_ok) {
+#pragma unroll
+            for (int i = 0; i < GP; i++) {
+                const int e = tid + 256 * i;
+                if (e < nel) gb[e] = greg[i];
+            }
+        } else {
+            const T2 *src = v + jb_of(sg) * rs;
+            for (int e = tid; e < nel; e += 256) {
+                const int jx = e / NT, nn = e % NT;
+                gb[e] = (n0 + nn < B) ? src[(long long)jx * B + n0 + nn] : czero<T2>();
+            }
+        }
+    };
+#pragma unroll
+    for (int q = 0; q < ST - 1; q++) issue(q);
+    // t_0 = g_0
+    for (int e = tid; e < nel; e += 256) {
+        const int jx = e / NT, nn = e % NT;
+        tbuf0[e] = (n0 + nn < B) ? v[(long long)jx * B + n0 + nn] : czero<T2>();
     }
+    gprefetch(0);
+    int q = 0;
+    T2 *tc = tbuf0, *tn = tbuf1;
+    for (int s = 0; s < nsteps; s++) {
+        const bool fwd = s < nz;
+        const int jb = jb_of(s);
+        if (s > 0) __syncthreads();  // previous step's epilogues done (gb, t of this step complete)
+        gstage(s);                   // gb for this step's epilogue
+        __syncthreads();
+        gprefetch(s + 1);  // in flight during this step
+        T2 *g = v + jb * rs;
+        for (int c = 0; c < nch; c++, q++) {
+            cp_async_wait<ST - 2>();
+            __syncthreads();  // chunk q visible; chunk q-1's slot no longer read
+            issue(q + ST - 1);
+            const T2 *Wq = ring + (q % ST) * CH * ldw;
+            T2 acc[TM][TN];
+#pragma unroll
+            for (int i = 0; i < TM; i++)
+#pragma unroll
+                for (int t = 0; t < TN; t++) acc[i][t] = czero<T2>();
+            const T2 *wr = Wq + (rg * TM) * ldw;
+            const T2 *xr = tc + cg;
+            for (int k = 0; k < nx; k++) {
+                T2 a[TM], xv[TN];
+#pragma unroll
+                for (int i = 0; i < TM; i++) a[i] = wr[i * ldw + k];
+#pragma unroll
+                for (int t = 0; t < TN; t++) xv[t] = xr[k * NT + 16 * t];
+#pragma unroll
+                for (int i = 0; i < TM; i++)
+#pragma unroll
+                    for (int t = 0; t < TN; t++) cmac(acc[i][t], a[i], xv[t]);
+            }
+            // epilogue: this step's output and the next step's t
+#pragma unroll
+            for (int i = 0; i < TM; i++) {
+                const int m = c * CH + rg * TM + i;
+                if (m >= nx) continue;
+#pragma unroll
+                for (int t = 0; t < TN; t++) {
+                    const int nn = cg + 16 * t;
+                    const bool live = n0 + nn < B;
+                    T2 out = acc[i][t], tnext;
+                    if (fwd) {
+                        if (s + 1 < nz)
+                            tnext = gb[m * NT + nn] - czc[(long long)jb * nx + m] * out;  // g_{j+1} - c_j y_j
+                        else if (jb > 0)
+                            tnext = czc[(long long)(jb - 1) * nx + m] * out;  // first backward: c_{nz-2} x_{nz-1}
+                        else
+                            tnext = czero<T2>();
+                    } else {
+                        out = gb[m * NT + nn] - out;  // x_j = y_j - W_j t
+                        tnext = (jb > 0) ? czc[(long long)(jb - 1) * nx + m] * out : czero<T2>();
+                    }
+                    if (!live) {
+                        out = czero<T2>();
+                        tnext = czero<T2>();
+                    }
+                    tn[m * NT + nn] = tnext;
+                    if (live) g[(long long)m * B + n0 + nn] = out;
+                }
+            }
+        }
+        T2 *tt = tc;
+        tc = tn;
+        tn = tt;
+    }
+    cp_async_wait<0>();
 }
 
-template <class T2, int NT>
-static void cell_chain_nt(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B, int max_nx,
-                          cudaStream_t st) {
-    size_t sm = (size_t)(2 * max_nx * NT + 64 * (PK + 1)) * sizeof(T2);
-    HZ_CU(cudaFuncSetAttribute(k_cell_chain<T2, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+template <class T2, int NT, int CH, int ST>
+static bool cell_chain_cfg(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B, int max_nx,
+                           cudaStream_t st) {
+    const int ldw = (max_nx + 1) & ~1;
+    const size_t sm = (size_t)(3 * max_nx * NT + ST * CH * ldw) * sizeof(T2);
+    if (sm > 220 * 1024) return false;
+    HZ_CU(cudaFuncSetAttribute(k_cell_chain<T2, NT, CH, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     dim3 grid((B + NT - 1) / NT, ncell);
-    k_cell_chain<T2, NT><<<grid, 256, sm, st>>>(d_cells, W, cz, vol, B);
+    k_cell_chain<T2, NT, CH, ST><<<grid, 256, sm, st>>>(d_cells, W, cz, vol, B);
     HZ_CU(cudaGetLastError());
+    return true;
 }
 
 template <class T2>
 void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B, int max_nx,
                        cudaStream_t st, int *nl) {
     if (ncell <= 0 || B <= 0) return;
-    // enough CTAs to fill the GPU: wide tiles when there are many cells
-    if ((long long)ncell * ((B + 15) / 16) >= 148 || B <= 4)
-        cell_chain_nt<T2, 16>(d_cells, ncell, W, cz, vol, B, max_nx, st);
-    else
-        cell_chain_nt<T2, 4>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    // widest RHS tile that fits; narrow tiles when few cells would leave SMs idle
+    bool ok = false;
+    if (B > 16) ok = cell_chain_cfg<T2, 32, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    if (!ok) ok = cell_chain_cfg<T2, 16, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    if (!ok) ok = cell_chain_cfg<T2, 16, 16, 2>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    if (!ok) throw HzError(HZ_ENOMEM, "cell solve: cell too wide for shared memory");
     if (nl) (*nl)++;
 }
 template void launch_cell_chain<double2>(const CellDesc *, int, const double2 *, const double2 *, double2 *, int,
@@ -275,30 +375,41 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
     const int outs = nr * NB;
     int ks = 1;
     while (ks < 32 && outs * ks * 2 <= 256) ks *= 2;
+    const int per = 256 / ks;
+    // this thread's output (only one pass when nr * NB <= 256)
+    const bool single = outs <= per;
     constexpr int PF = 12;
     const int nvec = (int)((long long)nr * n2 * sizeof(T2) / 16);
     const bool use_pf = nvec <= 256 * PF;
     int4 pf[PF];
+    auto step_j = [&](int s) { return s < J - 1 ? s + 1 : J - 2 - (s - (J - 1)); };
     auto qptr = [&](int s) -> const T2 * {
         if (s < J - 1) return P + ld.P_off + (long long)(s + 1) * n2 * n2 + (long long)r0 * n2;
-        const int j = J - 2 - (s - (J - 1));
-        return V + ld.V_off + (long long)j * n2 * n2 + (long long)r0 * n2;
+        return V + ld.V_off + (long long)step_j(s) * n2 * n2 + (long long)r0 * n2;
     };
-    auto prefetch = [&](int s) {
-        if (s >= S || !use_pf) return;
-        const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
+    // base of step s: h_j (forward) or y_j (backward, written earlier by this CTA)
+    auto bptr = [&](int s) -> const T2 * { return (s < J - 1 ? h : x) + (long long)(step_j(s) + 1) * slot; };
+    const int o_me = tid / ks, kp = tid % ks;
+    const int m_me = o_me / NB, n_me = o_me % NB;
+    const bool out_me = single && o_me < outs && kp == 0 && n0 + n_me < B;
+    auto prefetch = [&](int s, T2 &bnext) {
+        if (s >= S) return;
+        if (use_pf) {
+            const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
 #pragma unroll
-        for (int i = 0; i < PF; i++) {
-            int v = tid + 256 * i;
-            if (v < nvec) pf[i] = src[v];
+            for (int i = 0; i < PF; i++) {
+                int v = tid + 256 * i;
+                if (v < nvec) pf[i] = src[v];
+            }
         }
+        if (out_me) bnext = bptr(s)[(long long)(r0 + m_me) * B + n0 + n_me];
     };
-    prefetch(0);
+    T2 bcur = czero<T2>(), bnext = czero<T2>();
+    prefetch(0, bcur);
     cl.sync();  // every CTA of the cluster has started: remote shared memory is live
     T2 *cur = zb0, *nxt = zb1;
+    const int rowbytes = nr * NB * (int)sizeof(T2);  // my slab of a z vector, contiguous
     for (int s = 0; s < S; s++) {
-        const bool fwd = s < J - 1;
-        const int j = fwd ? s + 1 : J - 2 - (s - (J - 1));
         int4 *dq = reinterpret_cast<int4 *>(Qs);
         if (use_pf) {
 #pragma unroll
@@ -310,42 +421,70 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
             const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
             for (int v = tid; v < nvec; v += 256) dq[v] = src[v];
         }
+        // deferred global store of the previous step's rows (off the barrier's path)
+        if (s > 0) {
+            T2 *outp = x + (long long)(step_j(s - 1) + 1) * slot;
+            for (int e = tid; e < nr * NB; e += 256) {
+                const int m = r0 + e / NB, n = e % NB;
+                if (n0 + n < B) outp[(long long)m * B + n0 + n] = cur[m * NB + n];
+            }
+        }
         __syncthreads();
-        prefetch(s + 1);
-        const T2 *base = (fwd ? h : x) + (long long)(j + 1) * slot;
-        T2 *out = x + (long long)(j + 1) * slot;
-        const int per = 256 / ks;
+        prefetch(s + 1, bnext);
+        const T2 *base = bptr(s);
         for (int o0 = 0; o0 < outs; o0 += per) {
-            const int o = o0 + tid / ks, kp = tid % ks;
-            T2 acc = czero<T2>();
+            const int o = o0 + o_me;
+            T2 a0 = czero<T2>(), a1 = czero<T2>(), a2 = czero<T2>(), a3 = czero<T2>();
             int m = 0, n = 0;
             if (o < outs) {
                 m = o / NB;
                 n = o % NB;
                 const T2 *q = Qs + m * n2;
-                for (int k = kp; k < n2; k += ks) cmac(acc, q[k], cur[k * NB + n]);
+                const T2 *zc = cur + n;
+                int k = kp;
+                for (; k + 3 * ks < n2; k += 4 * ks) {
+                    cmac(a0, q[k], zc[k * NB]);
+                    cmac(a1, q[k + ks], zc[(k + ks) * NB]);
+                    cmac(a2, q[k + 2 * ks], zc[(k + 2 * ks) * NB]);
+                    cmac(a3, q[k + 3 * ks], zc[(k + 3 * ks) * NB]);
+                }
+                for (; k < n2; k += ks) cmac(a0, q[k], zc[k * NB]);
             }
+            T2 acc = (a0 + a1) + (a2 + a3);
             for (int off = ks >> 1; off > 0; off >>= 1) {
                 acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
                 acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
             }
             if (o < outs && kp == 0) {
-                const int gm = r0 + m;
                 T2 v = czero<T2>();
-                if (n0 + n < B) {
-                    v = base[(long long)gm * B + n0 + n] + acc;
-                    out[(long long)gm * B + n0 + n] = v;
-                }
-                for (int q = 0; q < R; q++) {
-                    T2 *rem = cl.map_shared_rank(nxt, q);
-                    rem[gm * NB + n] = v;
-                }
+                if (n0 + n < B) v = (single ? bcur : base[(long long)(r0 + m) * B + n0 + n]) + acc;
+                nxt[(r0 + m) * NB + n] = v;
+            }
+        }
+        __syncthreads();  // my rows of z_j are in my own buffer
+        // push my slab to the other CTAs of the cluster (16-byte vectors)
+        {
+            const int nv = rowbytes / 16;
+            const int4 *srcv = reinterpret_cast<const int4 *>(nxt + r0 * NB);
+            for (int e = tid; e < nv * (R - 1); e += 256) {
+                const int qr = e / nv, v = e % nv;
+                const int dst = qr < rank ? qr : qr + 1;
+                int4 *rem = reinterpret_cast<int4 *>(cl.map_shared_rank(nxt + r0 * NB, dst));
+                rem[v] = srcv[v];
             }
         }
         cl.sync();
         T2 *t = cur;
         cur = nxt;
         nxt = t;
+        bcur = bnext;
+    }
+    if (S > 0) {
+        T2 *outp = x + (long long)(step_j(S - 1) + 1) * slot;
+        for (int e = tid; e < nr * NB; e += 256) {
+            const int m = r0 + e / NB, n = e % NB;
+            if (n0 + n < B) outp[(long long)m * B + n0 + n] = cur[m * NB + n];
+        }
     }
 }
 
@@ -358,9 +497,9 @@ static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer
     int Rmin = 1;
     while (Rmin <= 16 && smem(Rmin) > 220 * 1024) Rmin *= 2;
     if (Rmin > 16) return false;
-    // preferred: enough CTAs to fill the GPU when few chains are in flight
-    int R = Rmin;
-    while (R < 16 && (long long)groups * nlayer * R * 2 <= 304) R *= 2;
+    // preferred: the largest cluster (smallest row slab per CTA, so the
+    // slab fits the register prefetch and each step's dot products are short)
+    int R = 16;
     auto kern = k_inner_sweep<T2, NB>;
     HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
@@ -392,7 +531,7 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
                         const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st, int *nl) {
     if (nlayer <= 0 || B <= 0) return;
     bool ok;
-    if ((long long)((B + 7) / 8) * nlayer * 16 <= 304)
+    if ((long long)((B + 7) / 8) * nlayer * 16 <= 608)
         ok = inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st);
     else
         ok = inner_sweep_nb<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st) ||
@@ -587,7 +726,8 @@ __global__ void __launch_bounds__(256) k_cell_factor(const CellDesc *__restrict_
     int *perm = reinterpret_cast<int *>(colk + nx);
     __shared__ double redv[32];
     __shared__ int redi[32];
-    const long long nn = (long long)nx * nx;
+    const int ldw = cd.ldw;
+    const long long nn = (long long)nx * ldw;
     for (int jz = 0; jz < nz; jz++) {
         double2 *S = W + cd.w_off + jz * nn;
         const double2 *Wp = S - nn;
@@ -603,12 +743,12 @@ __global__ void __launch_bounds__(256) k_cell_factor(const CellDesc *__restrict_
                 a = cxv[o + k];
             if (jz > 0) {
                 const double2 c1 = czv[o - nx + i], c2 = czv[o - nx + k];
-                a = a - (c1 * Wp[e]) * c2;
+                a = a - (c1 * Wp[(long long)i * ldw + k]) * c2;
             }
-            S[e] = a;
+            S[(long long)i * ldw + k] = a;
         }
         __syncthreads();
-        int r = gj_inverse(S, nx, nx, rowk, colk, perm, redv, redi);
+        int r = gj_inverse(S, nx, ldw, rowk, colk, perm, redv, redi);
         if (r) {
             if (threadIdx.x == 0) atomicCAS(info, 0, (blockIdx.x + 1));
             return;

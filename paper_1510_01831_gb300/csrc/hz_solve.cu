@@ -51,25 +51,59 @@ __global__ void k_global_alpha(int NX, int NZ, int nxi, int nzi, int p, double h
     }
 }
 
-// f [B][N] (batch outer) -> fs [N][B] = f / (alpha_x alpha_z): the row-scaled source
-__global__ void k_src_in(const double2 *__restrict__ f, double2 *fs, const double2 *__restrict__ ax,
-                         const double2 *__restrict__ az, int NX, long long N, int B, int scale) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * B; e += (long long)gridDim.x * blockDim.x) {
-        long long g = e / B;
-        int b = (int)(e % B);
-        double2 v = f[(long long)b * N + g];
-        if (scale) v = cdiv(v, ax[g % NX] * az[g / NX]);
-        fs[e] = v;
+// f [B][N] (batch outer) -> fs [N][B] = f / (alpha_x alpha_z): the row-scaled
+// source.  32 x 32 tiles through shared memory keep both sides coalesced.
+__global__ void k_src_in(const double2 *__restrict__ f, double2 *fs, const double2 *__restrict__ Dg, long long N,
+                         int B, int scale) {
+    __shared__ double2 t[32][33];
+    const long long g0 = (long long)blockIdx.x * 32;
+    const int b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r;
+        const long long g = g0 + threadIdx.x;
+        if (b < B && g < N) {
+            double2 v = f[(long long)b * N + g];
+            if (scale) v = v * Dg[g];
+            t[r][threadIdx.x] = v;
+        }
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long g = g0 + r;
+        const int b = b0 + threadIdx.x;
+        if (b < B && g < N) fs[g * B + b] = t[threadIdx.x][r];
     }
 }
 
 // u [N][B] -> out [B][N]
 __global__ void k_out(const double2 *__restrict__ u, double2 *out, long long N, int B) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * B; e += (long long)gridDim.x * blockDim.x) {
-        long long g = e % N;
-        int b = (int)(e / N);
-        out[e] = u[g * B + b];
+    __shared__ double2 t[32][33];
+    const long long g0 = (long long)blockIdx.x * 32;
+    const int b0 = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long g = g0 + r;
+        const int b = b0 + threadIdx.x;
+        if (b < B && g < N) t[r][threadIdx.x] = u[g * B + b];
     }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int b = b0 + r;
+        const long long g = g0 + threadIdx.x;
+        if (b < B && g < N) out[(long long)b * N + g] = t[threadIdx.x][r];
+    }
+}
+
+static void transpose_in(hz_ctx *c, const double2 *f, double2 *fs, long long N, int B, bool scale) {
+    dim3 grid((unsigned)((N + 31) / 32), (B + 31) / 32), blk(32, 8);
+    k_src_in<<<grid, blk, 0, c->st>>>(f, fs, c->d_ginvD, N, B, scale ? 1 : 0);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+}
+static void transpose_out(hz_ctx *c, const double2 *u, double2 *out, long long N, int B) {
+    dim3 grid((unsigned)((N + 31) / 32), (B + 31) / 32), blk(32, 8);
+    k_out<<<grid, blk, 0, c->st>>>(u, out, N, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
 }
 
 // r = fs - H_s u  (row-scaled operator on the global box, precomputed
@@ -113,9 +147,27 @@ __global__ void k_residual(const double2 *__restrict__ u, const double2 *__restr
 }
 
 __global__ void k_global_D(const double2 *__restrict__ ax, const double2 *__restrict__ az, int NX, long long N,
-                           double2 *D) {
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x)
+                           double2 *D, double2 *invD) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
         D[g] = ax[g % NX] * az[g / NX];
+        invD[g] = cdiv(make_double2(1.0, 0.0), D[g]);
+    }
+}
+
+// interface couplings: gamma per global column, beta per layer row (layer-local PML)
+__global__ void k_couplings(const LayerDesc *__restrict__ layers, int L, const double2 *__restrict__ ax, int NX,
+                            int p, double h, double C, double omega, double2 *gam, double2 *beta) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const double h2 = h * h;
+    if (blockIdx.y == 0) {
+        if (i < NX) gam[i] = cdiv(make_double2(-1.0, 0.0), h2 * ax[i]);
+        return;
+    }
+    const LayerDesc &ld = layers[blockIdx.y - 1];
+    if (i < ld.nz) {
+        double2 az = pml_alpha_s(i - p + 1.0, ld.n, p, h, C, omega);
+        beta[ld.zoff + i] = cdiv(make_double2(-1.0, 0.0), h2 * az);
+    }
 }
 
 __global__ void k_reduce_parts(const double *__restrict__ part, int nchunk, int width, double *out) {
@@ -299,48 +351,55 @@ __global__ void k_traces(const double2 *__restrict__ x, T2 *tr, int K, int NX, i
 
 // reconstruction source of every cell: outer interface forcing on rows
 // (0,1,n,n+1) x owned columns from the traces, inner interface forcing on
-// columns (0,1,w,w+1) from the inner traces (Appendix C forcing, both levels)
+// columns (0,1,w,w+1) from the inner traces (Appendix C forcing, both levels).
+// The volume is cleared beforehand; threads visit only the forced points
+// (points on both sets get the same value from two threads).
 template <class T2>
 __global__ void k_recon_src(const CellDesc *__restrict__ cells, const LayerDesc *__restrict__ layers,
                             const T2 *__restrict__ tr, const T2 *__restrict__ inner, T2 *vol2, int L, int NX, int B,
-                            int p, double h, double Cp, double omega) {
+                            int p, const double2 *__restrict__ ggam, const double2 *__restrict__ lbeta) {
     const CellDesc &cd = cells[blockIdx.y];
     const LayerDesc &ld = layers[cd.l];
     const int nx = cd.nx, nz = cd.nz;
     const long long rowsz = (long long)NX * B;
-    const double h2 = h * h;
-    const long long n = (long long)nx * nz * B;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
-        long long pt = e / B;
-        int jz = (int)(pt / nx), jx = (int)(pt % nx);
+    const int npts = 4 * cd.no + 4 * nz;
+    const int r0 = p - 1, r1 = p, rn = p + cd.n - 1, rn1 = p + cd.n;
+    const int c0 = p - 1, c1 = p, cw = p + cd.w - 1, cw1 = p + cd.w;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)npts * B;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % B);
+        const int q = (int)(e / B);
+        int jz, jx;
+        if (q < 4 * cd.no) {
+            const int rr = q / cd.no;
+            jz = rr == 0 ? r0 : (rr == 1 ? r1 : (rr == 2 ? rn : rn1));
+            jx = cd.own_lo + q % cd.no;
+        } else {
+            const int qq = q - 4 * cd.no, cc = qq / nz;
+            jz = qq % nz;
+            jx = cc == 0 ? c0 : (cc == 1 ? c1 : (cc == 2 ? cw : cw1));
+        }
         double2 v = make_double2(0.0, 0.0);
         // outer rows: source row node 0 <- +gamma t(row 1), node 1 <- -gamma t(row 0),
         // node n <- -gamma t(row n+1), node n+1 <- +gamma t(row n)
-        if (jx >= cd.own_lo && jx < cd.own_lo + cd.no) {
-            const int r0 = p - 1, r1 = p, rn = p + cd.n - 1, rn1 = p + cd.n;
-            if (jz == r0 || jz == r1 || jz == rn || jz == rn1) {
-                double2 ax = pml_alpha_s(jx - p + 1.0, cd.w, p, h, Cp, omega);
-                double2 gam = cdiv(make_double2(-1.0, 0.0), h2 * ax);
-                const long long gx = (long long)(cd.t + jx) * B + b;
-                double2 s = make_double2(0.0, 0.0);
-                if (cd.l > 0) {  // top pair: interface l-1
-                    const T2 *I = tr + (long long)(cd.l - 1) * 2 * rowsz + gx;
-                    if (jz == r0) s = s + to2(I[rowsz], double2{});
-                    if (jz == r1) s = s - to2(I[0], double2{});
-                }
-                if (cd.l < L - 1) {  // bottom pair: interface l
-                    const T2 *I = tr + (long long)cd.l * 2 * rowsz + gx;
-                    if (jz == rn) s = s - to2(I[rowsz], double2{});
-                    if (jz == rn1) s = s + to2(I[0], double2{});
-                }
-                v = v + gam * s;
+        if (jx >= cd.own_lo && jx < cd.own_lo + cd.no && (jz == r0 || jz == r1 || jz == rn || jz == rn1)) {
+            const double2 gam = ggam[cd.t + jx];  // owned columns: cell-local alpha_x = global alpha_x
+            const long long gx = (long long)(cd.t + jx) * B + b;
+            double2 s = make_double2(0.0, 0.0);
+            if (cd.l > 0) {  // top pair: interface l-1
+                const T2 *I = tr + (long long)(cd.l - 1) * 2 * rowsz + gx;
+                if (jz == r0) s = s + to2(I[rowsz], double2{});
+                if (jz == r1) s = s - to2(I[0], double2{});
             }
+            if (cd.l < L - 1) {  // bottom pair: interface l
+                const T2 *I = tr + (long long)cd.l * 2 * rowsz + gx;
+                if (jz == rn) s = s - to2(I[rowsz], double2{});
+                if (jz == rn1) s = s + to2(I[0], double2{});
+            }
+            v = v + gam * s;
         }
-        const int c0 = p - 1, c1 = p, cw = p + cd.w - 1, cw1 = p + cd.w;
         if (jx == c0 || jx == c1 || jx == cw || jx == cw1) {
-            double2 az = pml_alpha_s(jz - p + 1.0, cd.n, p, h, Cp, omega);
-            double2 beta = cdiv(make_double2(-1.0, 0.0), h2 * az);
+            const double2 beta = lbeta[ld.zoff + jz];
             const long long n2 = 2LL * nz;
             const T2 *Il = inner + (ld.inner_off + (long long)cd.c * n2) * B;        // interface c-1 (slot c)
             const T2 *Ir = inner + (ld.inner_off + (long long)(cd.c + 1) * n2) * B;  // interface c (slot c+1)
@@ -351,7 +410,7 @@ __global__ void k_recon_src(const CellDesc *__restrict__ cells, const LayerDesc 
             if (jx == cw1) s = s + to2(Ir[(long long)jz * B + b], double2{});         // + x_{c,a}
             v = v + beta * s;
         }
-        vol2[cd.vol_off * B + e] = to2(v, T2{});
+        vol2[(cd.vol_off + (long long)jz * nx + jx) * B + b] = to2(v, T2{});
     }
 }
 
@@ -576,7 +635,7 @@ template <class T2> static void cell_chain_cost(hz_ctx *c, int N, double &bytes,
     bytes = flops = 0;
     for (const CellDesc &cd : c->cells) {
         const double nx = cd.nx, nz = cd.nz;
-        bytes += es * (2 * nz * nx * nx + 2 * (nz - 1) * nx + 4 * nz * nx * N);
+        bytes += es * ((2 * nz - 1) * nx * nx + 2 * (nz - 1) * nx + 4 * nz * nx * N);
         flops += 8.0 * (2 * nz - 1) * nx * nx * N;
     }
 }
@@ -1171,8 +1230,9 @@ static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double t
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
     run(c, W.f_rec);
     chain_layers(c, W, false, 0, L);
-    k_recon_src<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, c->d_layers, W.pc, W.inner, W.vol2, L, c->NX, B, c->p,
-                                                     c->h, c->pml_C, c->omega);
+    HZ_CU(cudaMemsetAsync(W.vol2, 0, sizeof(T2) * c->tot_vol * B, st));
+    k_recon_src<T2><<<dim3(64, ncell), 256, 0, st>>>(c->d_cells, c->d_layers, W.pc, W.inner, W.vol2, L, c->NX, B, c->p,
+                                                     c->d_ggam, c->d_lbeta);
     HZ_CU(cudaGetLastError());
     c->nl++;
     cell_chain<T2>(c, W.vol2, B);
@@ -1222,10 +1282,19 @@ void init_global_alpha(hz_ctx *c) {
     c->d_gcx = (double2 *)c->dalloc(sizeof(double2) * N);
     c->d_gcz = (double2 *)c->dalloc(sizeof(double2) * N);
     c->d_gD = (double2 *)c->dalloc(sizeof(double2) * N);
+    c->d_ginvD = (double2 *)c->dalloc(sizeof(double2) * N);
+    c->d_ggam = (double2 *)c->dalloc(sizeof(double2) * c->NX);
+    c->d_lbeta = (double2 *)c->dalloc(sizeof(double2) * std::max(c->tot_z, 1LL));
     launch_cell_coeffs(c->d_gcell, 1, c->d_m, c->NX, c->omega, c->h, c->pml_C, c->p, c->d_gdiag, c->d_gcx, c->d_gcz,
                        c->st, nullptr);
-    k_global_D<<<1024, 256, 0, c->st>>>(c->d_ax, c->d_az, c->NX, N, c->d_gD);
+    k_global_D<<<1024, 256, 0, c->st>>>(c->d_ax, c->d_az, c->NX, N, c->d_gD, c->d_ginvD);
     HZ_CU(cudaGetLastError());
+    {
+        int mx = std::max(c->NX, c->max_nz);
+        k_couplings<<<dim3((mx + 255) / 256, c->L + 1), 256, 0, c->st>>>(c->d_layers, c->L, c->d_ax, c->NX, c->p, c->h,
+                                                                         c->pml_C, c->omega, c->d_ggam, c->d_lbeta);
+        HZ_CU(cudaGetLastError());
+    }
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 
@@ -1239,9 +1308,7 @@ int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats 
     hz_stats s{};
     double t0 = now_ms();
     // source in the row-scaled form, [N][B]
-    k_src_in<<<grid1(N * B), 256, 0, st>>>(f_dev, W.gsrc, c->d_ax, c->d_az, c->NX, N, B, scale_src ? 1 : 0);
-    HZ_CU(cudaGetLastError());
-    c->nl++;
+    transpose_in(c, f_dev, W.gsrc, N, B, scale_src);
     HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, st));
     std::vector<double> fn(B), rn(B);
     residual_norms(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
@@ -1280,9 +1347,7 @@ int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats 
     }
     if (rtol > 0 && worst > rtol) status = HZ_ENOTCONV;
     s.resid = worst;
-    k_out<<<grid1(N * B), 256, 0, st>>>(W.u, u_dev, N, B);
-    HZ_CU(cudaGetLastError());
-    c->nl++;
+    transpose_out(c, W.u, u_dev, N, B);
     HZ_CU(cudaStreamSynchronize(st));
     s.t_total_ms = now_ms() - t0;
     s.t_local_ms = tm.local;
@@ -1306,17 +1371,16 @@ template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev
     const CellDesc &cd = c->cells[ci];
     const long long npt = (long long)cd.nx * cd.nz;
     // g [B][npt] -> vol (cell slot, [npt][B])
-    k_src_in<<<grid1(npt * B), 256, 0, c->st>>>(g_dev, W.io, nullptr, nullptr, 1, npt, B, 0);
-    HZ_CU(cudaGetLastError());
+    transpose_in(c, g_dev, W.io, npt, B, false);
     k_cast<double2, T2><<<grid1(npt * B), 256, 0, c->st>>>(W.io, W.vol + cd.vol_off * B, npt * B);
     HZ_CU(cudaGetLastError());
-    c->nl += 2;
+    c->nl++;
     launch_cell_chain<T2>(c->d_cells + ci, 1, o.cellW, o.cz, W.vol, B, c->max_nx, c->st, &c->nl);
     k_cast<T2, double2><<<grid1(npt * B), 256, 0, c->st>>>(W.vol + cd.vol_off * B, W.io, npt * B);
     HZ_CU(cudaGetLastError());
-    k_out<<<grid1(npt * B), 256, 0, c->st>>>(W.io, x_dev, npt, B);
     HZ_CU(cudaGetLastError());
-    c->nl += 2;
+    c->nl++;
+    transpose_out(c, W.io, x_dev, npt, B);
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 template void comp_cell_solve<double2>(hz_ctx *, int, const double2 *, int, double2 *);
@@ -1328,9 +1392,7 @@ template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_de
     const long long n4 = 4LL * c->NX;
     const long long rowsz = (long long)c->NX * B;
     // [B][4*NX] -> [4*NX][B] into io, mask rows, cast into lin (layer l block)
-    k_src_in<<<grid1(n4 * B), 256, 0, c->st>>>(tr_dev, W.io, nullptr, nullptr, 1, n4, B, 0);
-    HZ_CU(cudaGetLastError());
-    c->nl++;
+    transpose_in(c, tr_dev, W.io, n4, B, false);
     if (!(mask & 1)) HZ_CU(cudaMemsetAsync(W.io, 0, sizeof(double2) * 2 * rowsz, c->st));
     if (!(mask & 2)) HZ_CU(cudaMemsetAsync(W.io + 2 * rowsz, 0, sizeof(double2) * 2 * rowsz, c->st));
     T2 *lin_l = W.lin + (long long)l * 4 * rowsz;
@@ -1343,9 +1405,9 @@ template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_de
     T2 *lout_l = W.lout + (long long)l * 4 * rowsz;
     k_cast<T2, double2><<<grid1(n4 * B), 256, 0, c->st>>>(lout_l, W.io, n4 * B);
     HZ_CU(cudaGetLastError());
-    k_out<<<grid1(n4 * B), 256, 0, c->st>>>(W.io, out_dev, n4, B);
     HZ_CU(cudaGetLastError());
-    c->nl += 2;
+    c->nl++;
+    transpose_out(c, W.io, out_dev, n4, B);
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 template void comp_layer_green<double2>(hz_ctx *, int, const double2 *, int, int, double2 *);
@@ -1355,9 +1417,7 @@ template void comp_layer_green<float2>(hz_ctx *, int, const double2 *, int, int,
 template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, int B, double2 *y_dev) {
     Work<T2> &W = work<T2>(c, B);
     const long long n = c->n_tr(), nB = n * B;
-    k_src_in<<<grid1(nB), 256, 0, c->st>>>(x_dev, W.w64, nullptr, nullptr, 1, n, B, 0);
-    HZ_CU(cudaGetLastError());
-    c->nl++;
+    transpose_in(c, x_dev, W.w64, n, B, false);
     if (which < 0) {
         k_cast<double2, T2><<<grid1(nB), 256, 0, c->st>>>(W.w64, W.pa, nB);
         HZ_CU(cudaGetLastError());
@@ -1372,9 +1432,7 @@ template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, 
         HZ_CU(cudaGetLastError());
         c->nl++;
     }
-    k_out<<<grid1(nB), 256, 0, c->st>>>(W.x64, y_dev, n, B);
-    HZ_CU(cudaGetLastError());
-    c->nl++;
+    transpose_out(c, W.x64, y_dev, n, B);
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 template void comp_polar<double2>(hz_ctx *, int, const double2 *, int, double2 *);
@@ -1383,10 +1441,8 @@ template void comp_polar<float2>(hz_ctx *, int, const double2 *, int, double2 *)
 template <class T2> void comp_residual(hz_ctx *c, const double2 *u_dev, const double2 *f_dev, int B, double *res_host) {
     Work<T2> &W = work<T2>(c, B);
     const long long N = (long long)c->NX * c->NZ;
-    k_src_in<<<grid1(N * B), 256, 0, c->st>>>(f_dev, W.gsrc, c->d_ax, c->d_az, c->NX, N, B, 1);
-    k_src_in<<<grid1(N * B), 256, 0, c->st>>>(u_dev, W.u, nullptr, nullptr, 1, N, B, 0);
-    HZ_CU(cudaGetLastError());
-    c->nl += 2;
+    transpose_in(c, f_dev, W.gsrc, N, B, true);
+    transpose_in(c, u_dev, W.u, N, B, false);
     std::vector<double> fn(B);
     residual_norms(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
     for (int b = 0; b < B; b++) fn[b] = std::sqrt(W.rhost[b]);
