@@ -38,6 +38,11 @@ WORKLOADS = {
     "smooth256": dict(n=256, n_pml=16, L=8, C=4, B=16, ppw=10.0, seed=2),
     # same per-launch shapes as smooth1024 (64-row layers, 64-column cells, 20-point PML, 64 sources)
     "smooth256_shape1024": dict(n=256, n_pml=20, L=4, C=4, B=64, ppw=10.0, seed=2),
+    # a 1024-wide, 256-deep strip: every launch has the shape of the 1024x1024 workload (16 cells per layer)
+    "strip1024x256": dict(n=1024, n_z=256, n_pml=20, L=4, C=16, B=64, ppw=10.0, seed=2),
+    # three frequencies (6, 8, 10 ppw) of one 512x512 smooth random medium, uneven layers and cells
+    # (24-64 points), 256 sources each, solved as one group (one context and stream per frequency)
+    "multifreq512": dict(n=512, n_pml=20, B=256, ppws=(6.0, 8.0, 10.0), seed=4, part_seed=40),
 }
 METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
 UNIT = "RHS*Mdof/s"
@@ -105,8 +110,46 @@ class Clocks:
                 "samples": len(self.samples)}
 
 
+def reduce_max(value, world):
+    """Max of a scalar over all ranks (the step time of the slowest replica)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as tdist
+    dev = "cuda" if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, B, mdof, ms_per_step):
+    """Whole-job RHS*Mdof/s: every replica solves its own batch of B sources."""
+    return world * B * mdof / (ms_per_step / 1e3)
+
+
+def make_problems(wl):
+    """[(problem, sources)] of a workload: one entry, or one per frequency."""
+    if "ppws" in wl:
+        probs = I.uneven_multifreq(n=wl["n"], n_pml=wl["n_pml"], seed=wl["seed"], part_seed=wl["part_seed"],
+                                   ppw_list=wl["ppws"])
+        return [(pb, I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, wl["B"])) for pb in probs]
+    return [make_problem(wl)]
+
+
+def describe(wl, pbs, B, precision):
+    pb = pbs[0]
+    if "ppws" in wl:
+        return (f"smooth random c in [1.5,4.5] corr 20h, {pb.n_x}x{pb.n_z}+{pb.n_pml} PML, "
+                f"{len(pbs)} frequencies ({'/'.join(f'{v:g}' for v in wl['ppws'])} ppw) solved as one group, "
+                f"uneven layers/cells 24-64 pts (L={pb.L} x C={pb.C}), {B} point sources row 1 per frequency, "
+                f"{precision}")
+    return (f"smooth random c in [1.5,4.5] corr 20h, {pb.n_x}x{pb.n_z}+{pb.n_pml} PML, {wl['ppw']:g} ppw, "
+            f"L={pb.L} x C={pb.C}, {B} point sources row 1, {precision}")
+
+
 def make_problem(wl):
-    pb = I.smooth_random(wl["n"], n_pml=wl["n_pml"], L=wl["L"], C=wl["C"], seed=wl["seed"], ppw=wl["ppw"])
+    pb = I.smooth_random(wl["n"], n_pml=wl["n_pml"], L=wl["L"], C=wl["C"], seed=wl["seed"], ppw=wl["ppw"],
+                         n_z=wl.get("n_z"))
     f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, wl["B"])
     return pb, f
 
@@ -121,60 +164,74 @@ def run_ours(args, rank, world):
     wl = dict(WORKLOADS[args.workload])
     if args.B:
         wl["B"] = args.B
-    pb, f = make_problem(wl)
-    B = f.shape[0]
+    items = make_problems(wl)
+    pbs = [pb for pb, _ in items]
+    B = items[0][1].shape[0]
     prec = hz.HZ_MIXED if args.precision == "mixed" else hz.HZ_FP64
-    stream = torch.cuda.Stream()
-    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec, device_ptrs=True,
-                     stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8)
+    streams = [torch.cuda.Stream() for _ in items]
+    ctxs = []
     t0 = time.time()
-    ctx.hz_factor()
+    for (pb, _), stream in zip(items, streams):
+        kw = {}
+        if pb.layer_rows is not None:
+            kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
+        ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
+                         device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8, **kw)
+        ctx.hz_factor()
+        ctxs.append(ctx)
     t_factor = time.time() - t0
-    f_dev = torch.from_numpy(f).to("cuda")
-    u_dev = torch.empty_like(f_dev)
+    f_dev = [torch.from_numpy(f).to("cuda") for _, f in items]
+    u_dev = [torch.empty_like(x) for x in f_dev]
+
+    def step(fs, us):
+        if len(ctxs) == 1:
+            _, st = ctxs[0].hz_solve(fs[0], us[0])
+            return [st]
+        _, sts = hz.hz_solve_group(ctxs, fs, us)
+        return sts
+
     torch.cuda.synchronize()
     for _ in range(args.warmup):
-        _, st = ctx.hz_solve(f_dev, u_dev)
+        step(f_dev, u_dev)
     dist = world > 1
     if dist:
         import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []
+    stats = []  # one list of member stats per step
+    # every member stream has finished when a step returns, so events on the first stream bracket all of them
     with Clocks(int(os.environ.get("LOCAL_RANK", 0))) as clk:
-        ev0.record(stream)
+        ev0.record(streams[0])
         for _ in range(args.steps):
-            _, st = ctx.hz_solve(f_dev, u_dev)
-            stats.append(st.as_dict())
-        ev1.record(stream)
+            stats.append([st.as_dict() for st in step(f_dev, u_dev)])
+        ev1.record(streams[0])
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-    mdof = pb.n_x * pb.n_z / 1e6
-    value = world * B * mdof / (ms / 1e3)
+    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, world)
+    mdof = sum(pb.n_x * pb.n_z for pb in pbs) / 1e6
+    value = job_throughput(world, B, mdof, ms)
     # end-to-end through the same entry point with pinned host buffers
-    f_host = torch.from_numpy(f).pin_memory()
-    u_host = torch.empty_like(f_host).pin_memory()
-    ctx.hz_set_device_ptrs(False)
-    fh, uh = f_host.numpy(), u_host.numpy()
-    ctx.hz_solve(fh, uh)
+    f_host = [torch.from_numpy(f).pin_memory() for _, f in items]
+    u_host = [torch.empty_like(x).pin_memory() for x in f_host]
+    for c in ctxs:
+        c.hz_set_device_ptrs(False)
+    fh, uh = [x.numpy() for x in f_host], [x.numpy() for x in u_host]
+    step(fh, uh)
     torch.cuda.synchronize()
     e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e_steps):
-        ctx.hz_solve(fh, uh)
+        step(fh, uh)
     torch.cuda.synchronize()
     e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
-    ctx.hz_set_device_ptrs(True)
+    for c in ctxs:
+        c.hz_set_device_ptrs(True)
+    flat = [m for st in stats for m in st]
     # kernel-class timings over the timed region
-    kt_ms = np.sum([s["kt_ms"] for s in stats], axis=0)
-    kt_n = np.sum([s["kt_launches"] for s in stats], axis=0)
-    kt_b = np.sum([s["kt_bytes"] for s in stats], axis=0)
-    kt_f = np.sum([s["kt_flops"] for s in stats], axis=0)
+    kt_ms = np.sum([s["kt_ms"] for s in flat], axis=0)
+    kt_n = np.sum([s["kt_launches"] for s in flat], axis=0)
+    kt_b = np.sum([s["kt_bytes"] for s in flat], axis=0)
+    kt_f = np.sum([s["kt_flops"] for s in flat], axis=0)
     names = ["cell_chain", "inner_chain", "batched_fes_gemm"]
     top = int(np.argmax(kt_ms))
     peaks, src = _peaks()
@@ -197,26 +254,30 @@ def run_ours(args, rank, world):
                  "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
                  "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)}})
     last = stats[-1]
+    pb = pbs[0]
+    nbytes = sum(f.nbytes for _, f in items)
+    solve = [{"iterations": m["iterations"], "refinements": m["refinements"], "resid": m["resid"],
+              "gmres_resid": m["gmres_resid"],
+              "phase_ms": {k: round(m[k], 2) for k in ("t_local_ms", "t_gmres_ms", "t_recon_ms", "t_resid_ms",
+                                                       "t_total_ms")}} for m in last]
+    solve[0]["t_factor_s"] = round(t_factor, 2)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64" if prec == hz.HZ_MIXED else "c128", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: smooth random c in [1.5,4.5] corr 20h, "
-                               f"{pb.n_x}x{pb.n_z}+{pb.n_pml} PML, {wl['ppw']:g} ppw, L={pb.L} x C={pb.C}, "
-                               f"{B} point sources row 1, {args.precision}",
+        "config": {"workload": f"{args.workload}: " + describe(wl, pbs, B, args.precision),
                    "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
+                   "frequencies": len(pbs),
                    "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
-        "gpu_launches": int(sum(s["gpu_launches"] for s in stats)),
-        "solve": {"iterations": last["iterations"], "refinements": last["refinements"],
-                  "resid": last["resid"], "gmres_resid": last["gmres_resid"], "t_factor_s": round(t_factor, 2),
-                  "phase_ms": {k: round(last[k], 2) for k in ("t_local_ms", "t_gmres_ms", "t_recon_ms",
-                                                             "t_resid_ms", "t_total_ms")}},
+        "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
+        "solve": solve[0] if len(solve) == 1 else solve,
         "roofline": roof,
         "e2e": {"value": round(world * B * mdof / (e_ms / 1e3), 3), "unit": UNIT,
-                "h2d_bytes_per_step": int(f.nbytes), "d2h_bytes_per_step": int(f.nbytes)},
+                "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)},
         "clocks": clk.summary(),
     }
-    ctx.close()
+    for c in ctxs:
+        c.close()
     return out
 
 
@@ -225,23 +286,30 @@ def oracle_sample(wl, rows=4, nthreads=None):
     """Time the CPU oracle (banded LU) on a full-width strip of the workload's
     medium and scale to the full grid: with x-fastest ordering the band width
     is the full extended width, so the cost per grid row is the same as for
-    the full problem."""
+    the full problem.  A multi-frequency workload times one strip per
+    frequency."""
     import oracle as O
-    pb, f = make_problem(wl)
-    p = pb.n_pml
-    NZs = rows + 2 * p
-    m = np.ascontiguousarray(pb.m[:NZs, :])
-    fs = np.ascontiguousarray(f[:, :NZs, :])
-    box = O.Box(m, pb.n_x, rows, p, pb.omega, pb.h, O.default_pml_C(pb.m))
-    t0 = time.perf_counter()
-    fac = box.factor(order=1)
-    t1 = time.perf_counter()
-    fac.solve(fs)
-    t2 = time.perf_counter()
-    scale = (pb.n_z + 2 * p) / NZs
-    t_full = (t2 - t0) * scale
-    value = f.shape[0] * pb.n_x * pb.n_z / 1e6 / t_full
-    return value, {"factor_s": round(t1 - t0, 2), "solve_s": round(t2 - t1, 2), "rows": rows, "scale": scale}
+    t_full = t_fac = t_sol = 0.0
+    work = 0.0
+    for pb, f in make_problems(wl):
+        p = pb.n_pml
+        NZs = rows + 2 * p
+        m = np.ascontiguousarray(pb.m[:NZs, :])
+        fs = np.ascontiguousarray(f[:, :NZs, :])
+        box = O.Box(m, pb.n_x, rows, p, pb.omega, pb.h, O.default_pml_C(pb.m))
+        t0 = time.perf_counter()
+        fac = box.factor(order=1)
+        t1 = time.perf_counter()
+        fac.solve(fs)
+        t2 = time.perf_counter()
+        scale = (pb.n_z + 2 * p) / NZs
+        t_full += (t2 - t0) * scale
+        t_fac += t1 - t0
+        t_sol += t2 - t1
+        work += f.shape[0] * pb.n_x * pb.n_z / 1e6
+    value = work / t_full
+    return value, {"factor_s": round(t_fac, 2), "solve_s": round(t_sol, 2), "rows": rows, "scale": scale,
+                   "work": work}
 
 
 def run_reference(args, rank, world):
@@ -255,7 +323,7 @@ def run_reference(args, rank, world):
         v, det = oracle_sample(wl)
         steps.append(v)
     v = float(np.mean(steps[args.warmup:]))
-    ms = wl["B"] * wl["n"] * wl["n"] / 1e6 / v * 1e3
+    ms = det["work"] / v * 1e3
     sample = (f"banded LU (x-fastest, band = full extended width) of a {det['rows']}-row full-width strip of the "
               f"workload, factor + {wl['B']} solves, time scaled by {det['scale']:.1f} to the full grid")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,

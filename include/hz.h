@@ -126,6 +126,22 @@ hz_status hz_factor(hz_ctx *ctx);
  * Errors: HZ_ESTATE (not factored), HZ_EINVAL (B < 1, NULL, non-finite f). */
 hz_status hz_solve(hz_ctx *ctx, const double *f, int B, double *u, hz_stats *st);
 
+/* Solve of G problems at once (several frequencies or media sharing a device,
+ * e.g. the frequencies of one inversion step; not in the paper).  Each member
+ * is an hz_solve on its own context and stream; the members' Newton stages,
+ * GMRES iterations, reconstructions and residuals are enqueued together and
+ * the host waits once per step for all of them, so their kernels overlap.
+ *   ctxs : G distinct factored contexts, same precision and device; give each
+ *          its own stream (opts.stream) for overlap (same stream: serialised).
+ *   f[i], u[i] : as hz_solve for ctxs[i] (host or device per its device_ptrs).
+ *   st   : NULL or G stats, one per member.
+ * Returns the worst member status (HZ_ENOTCONV if any member missed its
+ * target; every u[i] written).  Errors: HZ_EINVAL (NULL, G < 1, mixed
+ * precisions or devices, repeated ctx), HZ_ESTATE, and those of hz_solve;
+ * the message is on ctxs[0]. */
+hz_status hz_solve_group(hz_ctx **ctxs, int G, const double *const *f, int B,
+                         double *const *u, hz_stats *st);
+
 /* Receiver misfit J = 1/2 sum_s ||R u_s - d_s||^2 and its gradient with respect
  * to m on the extended grid (not in the paper; adjoint state).  One forward
  * solve per source, one adjoint solve reusing the factors (the row-scaled
@@ -139,6 +155,18 @@ hz_status hz_solve(hz_ctx *ctx, const double *f, int B, double *u, hz_stats *st)
 hz_status hz_gradient(hz_ctx *ctx, const double *f, int B, const double *d,
                       const int *rec_idx, int n_rec, double *J, double *grad_m,
                       double *u_out, hz_stats *st);
+
+/* Adjoint of hz_solve for an arbitrary real loss L(u) (not in the paper; the
+ * differentiation pattern of the solver): with gu = dL/dRe(u) + i dL/dIm(u)
+ * (PyTorch's gradient convention for complex tensors),
+ *   mu     = H^{-T} conj(gu)                 (transposed Appendix A system,
+ *                                             solved with the forward factors),
+ *   grad_m = omega^2 sum_s Re(mu_s . u_s)    (dL/dm, real, [grid]),
+ *   grad_f = conj(mu)                        (dL/df in the same convention; may be NULL).
+ *   u, gu : [B][grid] complex (forward fields and their gradients).
+ * Errors as hz_solve. */
+hz_status hz_adjoint(hz_ctx *ctx, const double *u, const double *gu, int B, double *grad_m, double *grad_f,
+                     hz_stats *st);
 
 /* ---- component entry points (each runs one step of the online path on the
  * device, used to test that step alone; inputs/outputs follow the conventions

@@ -48,6 +48,21 @@ __global__ void k_grad(const double2 *__restrict__ lam, const double2 *__restric
     }
 }
 
+// out = conj(a)
+__global__ void k_conj(const double2 *__restrict__ a, double2 *out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = make_double2(a[i].x, -a[i].y);
+}
+
+// mu = D^{-1} lam (lam solves the row-scaled system with source conj(gu)), grad_f = conj(mu)
+__global__ void k_mu_conj(const double2 *__restrict__ lam, const double2 *__restrict__ invD, long long N, int B,
+                          double2 *gf) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * B; e += (long long)gridDim.x * blockDim.x) {
+        double2 mu = hz::operator*(lam[e], invD[e % N]);
+        gf[e] = make_double2(mu.x, -mu.y);
+    }
+}
+
 hz_status fail(hz_ctx *c, int code, const std::string &msg) {
     if (c)
         c->err = msg;
@@ -154,6 +169,7 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     c->NX = n_x + 2 * n_pml;
     c->NZ = n_z + 2 * n_pml;
     c->st = (cudaStream_t)c->opts.stream;
+    if (cudaGetDevice(&c->dev) != cudaSuccess) c->dev = -1;
     const long long N = (long long)c->NX * c->NZ;
     double cmax = 0;
     for (long long i = 0; i < N; i++) {
@@ -237,6 +253,58 @@ hz_status hz_solve(hz_ctx *c, const double *f, int B, double *u, hz_stats *st) {
             }
         }
         if (s == HZ_ENOTCONV) c->err = "tolerance not reached; best iterate written";
+        return (hz_status)s;
+    });
+}
+
+hz_status hz_solve_group(hz_ctx **cs, int G, const double *const *f, int B, double *const *u, hz_stats *st) {
+    if (!cs || G < 1) return fail(nullptr, HZ_EINVAL, "ctxs must be non-NULL and G >= 1");
+    for (int i = 0; i < G; i++)
+        if (!cs[i]) return fail(nullptr, HZ_EINVAL, "a ctx in the group is NULL");
+    hz_ctx *c0 = cs[0];
+    if (!f || !u || B < 1) return fail(c0, HZ_EINVAL, "f, u must be non-NULL and B >= 1");
+    int dev0 = c0->dev;
+    for (int i = 0; i < G; i++) {
+        if (!cs[i]->factored) return fail(c0, HZ_ESTATE, "hz_solve_group before hz_factor on every member");
+        if (cs[i]->mixed() != c0->mixed()) return fail(c0, HZ_EINVAL, "group members must share the precision");
+        if (cs[i]->dev != dev0) return fail(c0, HZ_EINVAL, "group members must share the device");
+        if (!f[i] || !u[i]) return fail(c0, HZ_EINVAL, "f[i], u[i] must be non-NULL");
+        for (int j = 0; j < i; j++)
+            if (cs[j] == cs[i]) return fail(c0, HZ_EINVAL, "a ctx appears twice in the group");
+    }
+    for (int i = 0; i < G; i++) cs[i]->nl = 0;
+    return guarded(c0, [&]() -> hz_status {
+        std::vector<hz_ctx *> v(cs, cs + G);
+        std::vector<const double2 *> fd(G);
+        std::vector<double2 *> ud(G);
+        for (int i = 0; i < G; i++) {
+            hz_ctx *c = cs[i];
+            const long long N = (long long)c->NX * c->NZ;
+            double2 *buf = stage(c, 2 * N * B);
+            fd[i] = to_dev(c, f[i], N * B, buf);
+            check_finite(c, (const double *)fd[i], 2 * N * B, "f");
+            ud[i] = c->opts.device_ptrs ? (double2 *)u[i] : buf + N * B;
+            c->kt_reset();
+        }
+        std::vector<hz_stats> sts;
+        int s = c0->mixed() ? hz::solve_group_impl<float2>(v, fd, B, ud, sts, true)
+                            : hz::solve_group_impl<double2>(v, fd, B, ud, sts, true);
+        for (int i = 0; i < G; i++) {
+            hz_ctx *c = cs[i];
+            from_dev(c, u[i], ud[i], (long long)c->NX * c->NZ * B);
+            c->kt_collect();
+            if (st) {
+                st[i] = sts[i];
+                st[i].gpu_launches = c->nl;
+                for (int k = 0; k < 3; k++) {
+                    st[i].kt_launches[k] = c->kt_launches[k];
+                    st[i].kt_ms[k] = c->kt_ms[k];
+                    st[i].kt_bytes[k] = c->kt_bytes[k];
+                    st[i].kt_flops[k] = c->kt_flops[k];
+                }
+            }
+        }
+        if (s == HZ_ENOTCONV) c0->err = "tolerance not reached by a group member; best iterates written";
         return (hz_status)s;
     });
 }
@@ -326,6 +394,63 @@ hz_status hz_gradient(hz_ctx *c, const double *f, int B, const double *d, const 
             }
         }
         return (hz_status)(sf != HZ_OK ? sf : sa);
+    });
+}
+
+hz_status hz_adjoint(hz_ctx *c, const double *u, const double *gu, int B, double *grad_m, double *grad_f,
+                     hz_stats *st) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_adjoint before hz_factor");
+    if (!u || !gu || !grad_m || B < 1) return fail(c, HZ_EINVAL, "NULL argument or B < 1");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        cudaStream_t s_ = c->st;
+        double2 *buf = stage(c, 2 * N * B);
+        const double2 *ud = to_dev(c, u, N * B, buf);
+        double2 *gbuf = (double2 *)c->dalloc(sizeof(double2) * N * B);
+        double2 *lam = (double2 *)c->dalloc(sizeof(double2) * N * B);
+        double *gd = (double *)c->dalloc(sizeof(double) * N);
+        struct Free {
+            hz_ctx *c;
+            std::vector<void *> v;
+            ~Free() {
+                for (void *p : v) c->dfree(p);
+            }
+        } fr{c, {gbuf, lam, gd}};
+        const double2 *gud = to_dev(c, gu, N * B, buf + N * B);
+        check_finite(c, (const double *)gud, 2 * N * B, "gu");
+        k_conj<<<256, 256, 0, s_>>>(gud, gbuf, N * B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        c->kt_reset();
+        hz_stats s1{};
+        // H^T = (D H_s)^T = H_s D: mu = D^{-1} H_s^{-1} conj(gu); the symmetric solve takes
+        // conj(gu) as its row-scaled source directly
+        int sa = c->mixed() ? hz::solve_impl<float2>(c, gbuf, B, lam, &s1, false)
+                            : hz::solve_impl<double2>(c, gbuf, B, lam, &s1, false);
+        k_grad<<<256, 256, 0, s_>>>(lam, ud, c->d_ax, c->d_az, c->NX, N, B, c->omega * c->omega, gd);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        if (grad_f) {
+            double2 *gfd = c->opts.device_ptrs ? (double2 *)grad_f : gbuf;  // gbuf no longer needed
+            k_mu_conj<<<256, 256, 0, s_>>>(lam, c->d_ginvD, N, B, gfd);
+            HZ_CU(cudaGetLastError());
+            c->nl++;
+            if (!c->opts.device_ptrs)
+                HZ_CU(cudaMemcpyAsync(grad_f, gfd, sizeof(double2) * N * B, cudaMemcpyDeviceToHost, s_));
+        }
+        if (c->opts.device_ptrs)
+            HZ_CU(cudaMemcpyAsync(grad_m, gd, sizeof(double) * N, cudaMemcpyDeviceToDevice, s_));
+        else
+            HZ_CU(cudaMemcpyAsync(grad_m, gd, sizeof(double) * N, cudaMemcpyDeviceToHost, s_));
+        HZ_CU(cudaStreamSynchronize(s_));
+        c->kt_collect();
+        if (st) {
+            *st = s1;
+            st->gpu_launches = c->nl;
+        }
+        return (hz_status)sa;
     });
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 #include <map>
 #include <memory>
+#include <vector>
 
 #include "../../include/hz.h"
 #include "hz_common.cuh"
@@ -121,6 +122,8 @@ struct hz_ctx {
     double2 *stage = nullptr;
     long long stage_n = 0;
     int *d_flag = nullptr;
+    int *d_err = nullptr;  // device error word: 1 = a bounded wait in a kernel gave up
+    int dev = 0;           // CUDA device current at hz_setup
     // allocations
     std::map<void *, size_t> allocs;
     long long dev_bytes = 0;
@@ -136,6 +139,9 @@ void build_decomposition(hz_ctx *c);
 void factor_all(hz_ctx *c);
 void init_global_alpha(hz_ctx *c);
 template <class T2> int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st, bool scale_src);
+template <class T2>
+int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const double2 *> &f_dev, int B,
+                     const std::vector<double2 *> &u_dev, std::vector<hz_stats> &stats, bool scale_src);
 template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev, int B, double2 *x_dev);
 template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_dev, int mask, int B, double2 *out_dev);
 template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, int B, double2 *y_dev);

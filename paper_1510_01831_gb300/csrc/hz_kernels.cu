@@ -140,13 +140,25 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// two complex values held as one 16-byte (float) or two 16-byte (double) registers
+template <class T2> struct Pair {
+    T2 a, b;
+};
+template <class T2> __device__ __forceinline__ Pair<T2> ld_pair(const T2 *p) {
+    return Pair<T2>{p[0], p[1]};
+}
+template <> __device__ __forceinline__ Pair<float2> ld_pair<float2>(const float2 *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return Pair<float2>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
 template <class T2, int NT, int CH, int ST>
 __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__ cells, const T2 *__restrict__ W,
                                                     const T2 *__restrict__ cz, T2 *vol, int B) {
     constexpr int TM = CH / 16, TN = NT / 16;
     constexpr int GP = 16;  // register-prefetch slots per thread for the next step's global vector
     extern __shared__ __align__(16) unsigned char smraw[];
-    const CellDesc &cd = cells[blockIdx.y];
+    const CellDesc cd = cells[blockIdx.y];  // fields in registers
     const int nx = cd.nx, nz = cd.nz, ldw = cd.ldw;
     const int n0 = blockIdx.x * NT;
     if (n0 >= B) return;
@@ -246,17 +258,52 @@ __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__
 #pragma unroll
                 for (int t = 0; t < TN; t++) acc[i][t] = czero<T2>();
             const T2 *wr = Wq + (rg * TM) * ldw;
-            const T2 *xr = tc + cg;
-            for (int k = 0; k < nx; k++) {
-                T2 a[TM], xv[TN];
+            if constexpr (TN % 2 == 0) {
+                // columns 2cg, 2cg+1 (+32 per extra pair): 16-byte loads of adjacent
+                // columns and of W(k), W(k+1)
+                const T2 *xr = tc + 2 * cg;
+                int k = 0;
+                for (; k + 1 < nx; k += 2) {
+                    Pair<T2> w[TM];
 #pragma unroll
-                for (int i = 0; i < TM; i++) a[i] = wr[i * ldw + k];
+                    for (int i = 0; i < TM; i++) w[i] = ld_pair(wr + i * ldw + k);
 #pragma unroll
-                for (int t = 0; t < TN; t++) xv[t] = xr[k * NT + 16 * t];
+                    for (int tp = 0; tp < TN / 2; tp++) {
+                        const Pair<T2> x0 = ld_pair(xr + k * NT + 32 * tp);
+                        const Pair<T2> x1 = ld_pair(xr + (k + 1) * NT + 32 * tp);
 #pragma unroll
-                for (int i = 0; i < TM; i++)
+                        for (int i = 0; i < TM; i++) {
+                            cmac(acc[i][2 * tp], w[i].a, x0.a);
+                            cmac(acc[i][2 * tp + 1], w[i].a, x0.b);
+                            cmac(acc[i][2 * tp], w[i].b, x1.a);
+                            cmac(acc[i][2 * tp + 1], w[i].b, x1.b);
+                        }
+                    }
+                }
+                if (k < nx) {
 #pragma unroll
-                    for (int t = 0; t < TN; t++) cmac(acc[i][t], a[i], xv[t]);
+                    for (int tp = 0; tp < TN / 2; tp++) {
+                        const Pair<T2> x0 = ld_pair(xr + k * NT + 32 * tp);
+#pragma unroll
+                        for (int i = 0; i < TM; i++) {
+                            cmac(acc[i][2 * tp], wr[i * ldw + k], x0.a);
+                            cmac(acc[i][2 * tp + 1], wr[i * ldw + k], x0.b);
+                        }
+                    }
+                }
+            } else {
+                const T2 *xr = tc + cg;
+                for (int k = 0; k < nx; k++) {
+                    T2 a[TM], xv[TN];
+#pragma unroll
+                    for (int i = 0; i < TM; i++) a[i] = wr[i * ldw + k];
+#pragma unroll
+                    for (int t = 0; t < TN; t++) xv[t] = xr[k * NT + 16 * t];
+#pragma unroll
+                    for (int i = 0; i < TM; i++)
+#pragma unroll
+                        for (int t = 0; t < TN; t++) cmac(acc[i][t], a[i], xv[t]);
+                }
             }
             // epilogue: this step's output and the next step's t
 #pragma unroll
@@ -265,7 +312,7 @@ __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__
                 if (m >= nx) continue;
 #pragma unroll
                 for (int t = 0; t < TN; t++) {
-                    const int nn = cg + 16 * t;
+                    const int nn = (TN % 2 == 0) ? 2 * cg + (t & 1) + 32 * (t >> 1) : cg + 16 * t;
                     const bool live = n0 + nn < B;
                     T2 out = acc[i][t], tnext;
                     if (fwd) {
@@ -314,7 +361,8 @@ void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2
     if (ncell <= 0 || B <= 0) return;
     // widest RHS tile that fits; narrow tiles when few cells would leave SMs idle
     bool ok = false;
-    if (B > 16) ok = cell_chain_cfg<T2, 32, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    if (B > 16) ok = cell_chain_cfg<T2, 32, 64, 2>(d_cells, ncell, W, cz, vol, B, max_nx, st);
+    if (!ok && B > 16) ok = cell_chain_cfg<T2, 32, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
     if (!ok) ok = cell_chain_cfg<T2, 16, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
     if (!ok) ok = cell_chain_cfg<T2, 16, 16, 2>(d_cells, ncell, W, cz, vol, B, max_nx, st);
     if (!ok) throw HzError(HZ_ENOMEM, "cell solve: cell too wide for shared memory");
@@ -339,30 +387,76 @@ template void launch_cell_chain<float2>(const CellDesc *, int, const float2 *, c
 // the shared memory of every CTA of the cluster (distributed shared memory);
 // one cluster barrier per step publishes z_j.  There are no spin waits.
 // Layout: slot j+1 of the layer's inner buffer holds interface j ([2nz][B]).
+// shared-memory / cluster helpers (inline PTX)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned cluster_map(unsigned addr, int rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_init(unsigned mb, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned mb, unsigned tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bulk copy of `bytes` from this CTA's shared memory to another CTA of the
+// cluster, completing on that CTA's mbarrier
+__device__ __forceinline__ void bulk_to_peer(unsigned dst_cluster, unsigned src_cta, unsigned bytes,
+                                             unsigned mbar_cluster) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            dst_cluster),
+        "r"(src_cta), "r"(bytes), "r"(mbar_cluster)
+        : "memory");
+}
+
+// padded row stride of the Q slab in shared memory (breaks bank aliasing of
+// rows that are 2*nz complex apart, keeps 16-byte alignment)
+template <class T2> __host__ __device__ inline int q_ld(int n2) { return sizeof(T2) == 8 ? n2 + 2 : n2 + 1; }
+
 template <class T2, int NB>
 __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict__ layers,
                                                      const int *__restrict__ ids, const T2 *__restrict__ P,
                                                      const T2 *__restrict__ V, const T2 *__restrict__ H, T2 *X,
-                                                     int B) {
+                                                     int B, int *err) {
     namespace cg = cooperative_groups;
+    constexpr int NP = NB / 2;  // column pairs
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long mbar[2];
     cg::cluster_group cl = cg::this_cluster();
     const int R = (int)cl.num_blocks();
     const int rank = (int)cl.block_rank();
     const int grp = blockIdx.x / R;
-    const LayerDesc &ld = layers[ids[blockIdx.y]];
+    const LayerDesc ld = layers[ids[blockIdx.y]];  // fields in registers
     const int nz = ld.nz, n2 = 2 * nz, J = ld.C - 1;
     if (J <= 0) return;  // uniform over the cluster
     const int n0 = grp * NB;
     const int rs = (n2 + R - 1) / R;
     const int r0 = min(n2, rank * rs), r1 = min(n2, r0 + rs), nr = r1 - r0;
+    const int ldq = q_ld<T2>(n2);
     T2 *zb0 = reinterpret_cast<T2 *>(smraw);
     T2 *zb1 = zb0 + n2 * NB;
     T2 *Qs = zb1 + n2 * NB;
     const long long slot = (long long)n2 * B;
     const T2 *h = H + ld.inner_off * (long long)B;
     T2 *x = X + ld.inner_off * (long long)B;
+    const T2 *Pl = P + ld.P_off, *Vl = V + ld.V_off;
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     for (int e = tid; e < n2 * NB; e += 256) {
         int k = e / NB, n = e % NB;
         zb0[e] = (n0 + n < B) ? h[slot + (long long)k * B + n0 + n] : czero<T2>();
@@ -372,27 +466,27 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
         if (n0 + n < B) x[slot + (long long)m * B + n0 + n] = h[slot + (long long)m * B + n0 + n];
     }
     const int S = 2 * (J - 1);
-    const int outs = nr * NB;
+    // thread -> (row m, column pair np, K part kp); K parts are contiguous even-length ranges
+    const int outs = nr * NP;
     int ks = 1;
     while (ks < 32 && outs * ks * 2 <= 256) ks *= 2;
     const int per = 256 / ks;
-    // this thread's output (only one pass when nr * NB <= 256)
     const bool single = outs <= per;
+    // Q slab prefetch: nr rows of n2 complex, as 16-byte vectors (rows are contiguous in global memory)
     constexpr int PF = 12;
-    const int nvec = (int)((long long)nr * n2 * sizeof(T2) / 16);
+    const int vrow = (int)(n2 * sizeof(T2) / 16);  // vectors per row
+    const int nvec = nr * vrow;
     const bool use_pf = nvec <= 256 * PF;
     int4 pf[PF];
     auto step_j = [&](int s) { return s < J - 1 ? s + 1 : J - 2 - (s - (J - 1)); };
     auto qptr = [&](int s) -> const T2 * {
-        if (s < J - 1) return P + ld.P_off + (long long)(s + 1) * n2 * n2 + (long long)r0 * n2;
-        return V + ld.V_off + (long long)step_j(s) * n2 * n2 + (long long)r0 * n2;
+        return (s < J - 1 ? Pl : Vl) + (long long)step_j(s) * n2 * n2 + (long long)r0 * n2;
     };
-    // base of step s: h_j (forward) or y_j (backward, written earlier by this CTA)
     auto bptr = [&](int s) -> const T2 * { return (s < J - 1 ? h : x) + (long long)(step_j(s) + 1) * slot; };
     const int o_me = tid / ks, kp = tid % ks;
-    const int m_me = o_me / NB, n_me = o_me % NB;
-    const bool out_me = single && o_me < outs && kp == 0 && n0 + n_me < B;
-    auto prefetch = [&](int s, T2 &bnext) {
+    const int m_me = o_me / NP, np_me = o_me % NP;
+    const bool out_me = single && o_me < outs && kp == 0;
+    auto prefetch = [&](int s, Pair<T2> &bnext) {
         if (s >= S) return;
         if (use_pf) {
             const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
@@ -402,27 +496,41 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
                 if (v < nvec) pf[i] = src[v];
             }
         }
-        if (out_me) bnext = bptr(s)[(long long)(r0 + m_me) * B + n0 + n_me];
+        if (out_me) {
+            const T2 *bp = bptr(s) + (long long)(r0 + m_me) * B + n0 + 2 * np_me;
+            bnext.a = (n0 + 2 * np_me < B) ? bp[0] : czero<T2>();
+            bnext.b = (n0 + 2 * np_me + 1 < B) ? bp[1] : czero<T2>();
+        }
     };
-    T2 bcur = czero<T2>(), bnext = czero<T2>();
+    auto qstore = [&](const int4 *src) {  // vectors -> padded rows of Qs
+        for (int v = tid; v < nvec; v += 256) {
+            const int row = v / vrow, col = v % vrow;
+            reinterpret_cast<int4 *>(Qs + row * ldq)[col] = src[v];
+        }
+    };
+    Pair<T2> bcur{czero<T2>(), czero<T2>()}, bnext{czero<T2>(), czero<T2>()};
     prefetch(0, bcur);
-    cl.sync();  // every CTA of the cluster has started: remote shared memory is live
-    T2 *cur = zb0, *nxt = zb1;
-    const int rowbytes = nr * NB * (int)sizeof(T2);  // my slab of a z vector, contiguous
+    cl.sync();  // all CTAs started, mbarriers initialised: peers may copy into us from now on
+    const unsigned rx_bytes = (unsigned)((n2 - nr) * NB * sizeof(T2));
+    const unsigned my_bytes = (unsigned)(nr * NB * sizeof(T2));
+    unsigned ph0 = 0u, ph1 = 0u;
+    bool dead = false;
     for (int s = 0; s < S; s++) {
-        int4 *dq = reinterpret_cast<int4 *>(Qs);
+        const int bo = (s & 1) ^ 1;  // input z_s in zb[s&1], output z_{s+1} into zb[bo]
+        T2 *cur = bo ? zb0 : zb1, *nxt = bo ? zb1 : zb0;
         if (use_pf) {
 #pragma unroll
             for (int i = 0; i < PF; i++) {
-                int v = tid + 256 * i;
-                if (v < nvec) dq[v] = pf[i];
+                const int v = tid + 256 * i;
+                if (v < nvec) {
+                    const int row = v / vrow, col = v % vrow;
+                    reinterpret_cast<int4 *>(Qs + row * ldq)[col] = pf[i];
+                }
             }
         } else {
-            const int4 *src = reinterpret_cast<const int4 *>(qptr(s));
-            for (int v = tid; v < nvec; v += 256) dq[v] = src[v];
+            qstore(reinterpret_cast<const int4 *>(qptr(s)));
         }
-        // deferred global store of the previous step's rows (off the barrier's path)
-        if (s > 0) {
+        if (s > 0) {  // previous step's rows to global memory
             T2 *outp = x + (long long)(step_j(s - 1) + 1) * slot;
             for (int e = tid; e < nr * NB; e += 256) {
                 const int m = r0 + e / NB, n = e % NB;
@@ -434,65 +542,99 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
         const T2 *base = bptr(s);
         for (int o0 = 0; o0 < outs; o0 += per) {
             const int o = o0 + o_me;
-            T2 a0 = czero<T2>(), a1 = czero<T2>(), a2 = czero<T2>(), a3 = czero<T2>();
-            int m = 0, n = 0;
+            T2 a0 = czero<T2>(), a1 = czero<T2>(), c0 = czero<T2>(), c1 = czero<T2>();
+            const int m = o / NP, np = o % NP;
             if (o < outs) {
-                m = o / NB;
-                n = o % NB;
-                const T2 *q = Qs + m * n2;
-                const T2 *zc = cur + n;
+                // K interleaved over the ks lanes of an output (adjacent rows of z fall in
+                // different banks); z read as 16-byte column pairs
+                const T2 *q = Qs + m * ldq;
+                const T2 *zc = cur + 2 * np;
                 int k = kp;
-                for (; k + 3 * ks < n2; k += 4 * ks) {
-                    cmac(a0, q[k], zc[k * NB]);
-                    cmac(a1, q[k + ks], zc[(k + ks) * NB]);
-                    cmac(a2, q[k + 2 * ks], zc[(k + 2 * ks) * NB]);
-                    cmac(a3, q[k + 3 * ks], zc[(k + 3 * ks) * NB]);
+                for (; k + ks < n2; k += 2 * ks) {
+                    const T2 q0 = q[k], q1 = q[k + ks];
+                    const Pair<T2> z0 = ld_pair(zc + k * NB);
+                    const Pair<T2> z1 = ld_pair(zc + (k + ks) * NB);
+                    cmac(a0, q0, z0.a);
+                    cmac(a1, q0, z0.b);
+                    cmac(c0, q1, z1.a);
+                    cmac(c1, q1, z1.b);
                 }
-                for (; k < n2; k += ks) cmac(a0, q[k], zc[k * NB]);
+                if (k < n2) {
+                    const Pair<T2> z0 = ld_pair(zc + k * NB);
+                    cmac(a0, q[k], z0.a);
+                    cmac(a1, q[k], z0.b);
+                }
             }
-            T2 acc = (a0 + a1) + (a2 + a3);
+            T2 acc0 = a0 + c0, acc1 = a1 + c1;
             for (int off = ks >> 1; off > 0; off >>= 1) {
-                acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-                acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+                acc0.x += __shfl_down_sync(0xffffffffu, acc0.x, off);
+                acc0.y += __shfl_down_sync(0xffffffffu, acc0.y, off);
+                acc1.x += __shfl_down_sync(0xffffffffu, acc1.x, off);
+                acc1.y += __shfl_down_sync(0xffffffffu, acc1.y, off);
             }
             if (o < outs && kp == 0) {
-                T2 v = czero<T2>();
-                if (n0 + n < B) v = (single ? bcur : base[(long long)(r0 + m) * B + n0 + n]) + acc;
-                nxt[(r0 + m) * NB + n] = v;
+                const int n = 2 * np;
+                Pair<T2> bv;
+                if (single) {
+                    bv = bcur;
+                } else {
+                    const T2 *bp = base + (long long)(r0 + m) * B + n0 + n;
+                    bv.a = (n0 + n < B) ? bp[0] : czero<T2>();
+                    bv.b = (n0 + n + 1 < B) ? bp[1] : czero<T2>();
+                }
+                T2 *dst = nxt + (r0 + m) * NB + n;
+                dst[0] = (n0 + n < B) ? bv.a + acc0 : czero<T2>();
+                dst[1] = (n0 + n + 1 < B) ? bv.b + acc1 : czero<T2>();
             }
         }
-        __syncthreads();  // my rows of z_j are in my own buffer
-        // push my slab to the other CTAs of the cluster (16-byte vectors)
-        {
-            const int nv = rowbytes / 16;
-            const int4 *srcv = reinterpret_cast<const int4 *>(nxt + r0 * NB);
-            for (int e = tid; e < nv * (R - 1); e += 256) {
-                const int qr = e / nv, v = e % nv;
-                const int dst = qr < rank ? qr : qr + 1;
-                int4 *rem = reinterpret_cast<int4 *>(cl.map_shared_rank(nxt + r0 * NB, dst));
-                rem[v] = srcv[v];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> async-proxy reads
+        __syncthreads();  // my slab of z_{s+1} complete
+        if (tid == 0) {
+            const unsigned mb_local = smem_u32(&mbar[bo]);
+            mbar_arrive_tx(mb_local, rx_bytes);
+            if (my_bytes > 0) {
+                const unsigned src = smem_u32(nxt + r0 * NB);
+                for (int d = 0; d < R; d++) {
+                    if (d == rank) continue;
+                    bulk_to_peer(cluster_map(src, d), src, my_bytes, cluster_map(mb_local, d));
+                }
             }
         }
-        cl.sync();
-        T2 *t = cur;
-        cur = nxt;
-        nxt = t;
+        {   // wait for every peer's slab (bounded; a timeout marks the run failed and
+            // later waits use a short limit so the kernel still terminates)
+            const unsigned mb_local = smem_u32(&mbar[bo]);
+            const unsigned par = bo ? ph1 : ph0;
+            const long long limit = dead ? 4096 : (1LL << 26);
+            long long it = 0;
+            while (!mbar_try(mb_local, par)) {
+                if (++it >= limit) {
+                    if (!dead && tid == 0) atomicExch(err, 1);
+                    dead = true;
+                    break;
+                }
+            }
+            if (bo) ph1 ^= 1u; else ph0 ^= 1u;
+        }
         bcur = bnext;
     }
     if (S > 0) {
+        const T2 *cur = (S & 1) ? zb1 : zb0;
         T2 *outp = x + (long long)(step_j(S - 1) + 1) * slot;
         for (int e = tid; e < nr * NB; e += 256) {
             const int m = r0 + e / NB, n = e % NB;
             if (n0 + n < B) outp[(long long)m * B + n0 + n] = cur[m * NB + n];
         }
     }
+    cl.sync();  // no CTA leaves while peers may still copy into or out of it
 }
 
 template <class T2, int NB>
 static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
-                           const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st) {
+                           const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
     const int groups = (B + NB - 1) / NB;
-    auto smem = [&](int R) { return (size_t)(2 * max_n2 * NB + ((max_n2 + R - 1) / R) * max_n2) * sizeof(T2); };
+    auto smem = [&](int R) {
+        return (size_t)(2 * max_n2 * NB + ((max_n2 + R - 1) / R) * q_ld<T2>(max_n2)) * sizeof(T2);
+    };
     // smallest cluster whose row slab fits in shared memory
     int Rmin = 1;
     while (Rmin <= 16 && smem(Rmin) > 220 * 1024) Rmin *= 2;
@@ -522,27 +664,27 @@ static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer
         cudaGetLastError();
     }
     if (R < Rmin) return false;
-    HZ_CU(cudaLaunchKernelEx(&cfg, kern, d_layers, ids, P, V, H, X, B));
+    HZ_CU(cudaLaunchKernelEx(&cfg, kern, d_layers, ids, P, V, H, X, B, err));
     return true;
 }
 
 template <class T2>
 void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
-                        const T2 *H, T2 *X, int B, int max_n2, cudaStream_t st, int *nl) {
+                        const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl) {
     if (nlayer <= 0 || B <= 0) return;
     bool ok;
     if ((long long)((B + 7) / 8) * nlayer * 16 <= 608)
-        ok = inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st);
+        ok = inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     else
-        ok = inner_sweep_nb<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st) ||
-             inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, st);
+        ok = inner_sweep_nb<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st) ||
+             inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) throw HzError(HZ_ENOMEM, "inner sweep: interface blocks too large for shared memory");
     if (nl) (*nl)++;
 }
 template void launch_inner_sweep<double2>(const LayerDesc *, const int *, int, const double2 *, const double2 *,
-                                          const double2 *, double2 *, int, int, cudaStream_t, int *);
+                                          const double2 *, double2 *, int, int, int *, cudaStream_t, int *);
 template void launch_inner_sweep<float2>(const LayerDesc *, const int *, int, const float2 *, const float2 *,
-                                         const float2 *, float2 *, int, int, cudaStream_t, int *);
+                                         const float2 *, float2 *, int, int, int *, cudaStream_t, int *);
 
 // ============================================== offline: coefficients ===
 // PML stretching alpha = 1/(1 + i sigma/omega), sigma(d) = (C/delta)(d/delta)^2

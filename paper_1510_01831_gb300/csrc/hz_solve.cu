@@ -916,7 +916,7 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     if (c->opts.time_kernels) inner_chain_cost<T2>(c, l0, nl, N, by, fl);
     c->kt_begin(1, by, fl);
     launch_inner_sweep<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.P, o.V, wide ? W.innerH2 : W.innerH,
-                           wide ? W.inner2 : W.inner, N, 2 * c->max_nz, c->st, &c->nl);
+                           wide ? W.inner2 : W.inner, N, 2 * c->max_nz, c->d_err, c->st, &c->nl);
     c->kt_end();
 }
 
@@ -981,203 +981,271 @@ struct GmresOut {
     double resid = 0;
 };
 
-template <class T2>
-static GmresOut fgmres(hz_ctx *c, Work<T2> &W, double tol, int maxit, int kind) {
-    const int B = W.B, m = W.restart;
-    const long long n = c->n_tr(), nB = n * B;
-    cudaStream_t st = c->st;
-    const int nchunk = (int)std::min<long long>(64, std::max<long long>(1, n / 256));
-    dim3 dblk(32, 8);
-    auto dots = [&](const double2 *V, long long vs, int nvec, const double2 *w, double2 *h, int accum) {
-        dim3 g(nchunk, (B + 31) / 32, nvec);
-        k_dots<<<g, dblk, 0, st>>>(V, vs, w, n, B, nchunk, (double2 *)W.dots);
+// Flexible GMRES on the polarized system, one state per context so that
+// several contexts (frequencies) can advance in lockstep on their own
+// streams.  Right preconditioning stores z_j = P v_j (FGMRES); the Arnoldi
+// basis, CGS2 orthogonalisation and the per-RHS Givens recurrences are FP64.
+// One host synchronisation per iteration: both CGS2 passes and the norm of
+// the new vector are reduced on the device and copied back together.
+template <class T2> struct Fgmres {
+    hz_ctx *c = nullptr;
+    Work<T2> *W = nullptr;
+    double tol = 0;
+    int maxit = 0, kind = 0, B = 0, m = 0, nchunk = 1;
+    long long n = 0, nB = 0;
+    std::vector<std::vector<double2>> Hm, g, cs, sn;
+    std::vector<double> beta0, res;
+    std::vector<int> kb, conv, act;
+    std::vector<double2> y;
+    const double2 *r = nullptr;
+    int total = 0, j = 0;
+    bool finished = false;
+
+    void dots(const double2 *V, long long vs, int nvec, const double2 *w, double2 *h) {
+        dim3 g3(nchunk, (B + 31) / 32, nvec), blk(32, 8);
+        k_dots<<<g3, blk, 0, c->st>>>(V, vs, w, n, B, nchunk, (double2 *)W->dots);
         HZ_CU(cudaGetLastError());
-        k_dots_final<<<(nvec * B + 255) / 256, 256, 0, st>>>((double2 *)W.dots, nchunk, B, nvec, h, accum);
+        k_dots_final<<<(nvec * B + 255) / 256, 256, 0, c->st>>>((double2 *)W->dots, nchunk, B, nvec, h, 0);
         HZ_CU(cudaGetLastError());
         c->nl += 2;
-    };
-    double2 *H = (double2 *)W.hbuf;  // device: [m+2][B]
-    double2 *Hh = (double2 *)W.hhost;
-    double *scale_h = W.rhost;
-    double *scale_d = W.rnorm;
-    // host Hessenberg state per RHS
-    std::vector<std::vector<double2>> Hm(B, std::vector<double2>((size_t)(m + 1) * m));
-    std::vector<std::vector<double2>> g(B, std::vector<double2>(m + 1)), cs(B, std::vector<double2>(m)),
-        sn(B, std::vector<double2>(m));
-    std::vector<double> beta0(B), res(B, 1.0);
-    std::vector<int> kb(B), conv(B, 0);
-    std::vector<double2> y((size_t)m * B);
-    double2 *y_d = (double2 *)W.dots;  // reuse (synchronised before reuse)
-
-    HZ_CU(cudaMemsetAsync(W.x64, 0, sizeof(double2) * nB, st));
-    // ||rhs||
-    dots(W.rhs64, 0, 1, W.rhs64, H, 0);
-    HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
-    HZ_CU(cudaStreamSynchronize(st));
-    for (int b = 0; b < B; b++) {
-        beta0[b] = std::sqrt(std::max(Hh[b].x, 0.0));
-        if (!(beta0[b] > 0)) {
-            conv[b] = 1;
-            res[b] = 0;
-        }
     }
-    const double2 *r = W.rhs64;  // first cycle: r = rhs (x0 = 0)
-    int total = 0;
-    GmresOut out;
-    while (true) {
-        // beta = ||r||, V0 = r / beta
-        dots(r, 0, 1, r, H, 0);
-        HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
-        HZ_CU(cudaStreamSynchronize(st));
-        std::vector<int> act(B);
+    double2 *H() { return (double2 *)W->hbuf; }
+    double2 *Hh() { return (double2 *)W->hhost; }
+
+    void init(hz_ctx *c_, Work<T2> &W_, double tol_, int maxit_, int kind_) {
+        c = c_;
+        W = &W_;
+        tol = tol_;
+        maxit = maxit_;
+        kind = kind_;
+        B = W->B;
+        m = W->restart;
+        n = c->n_tr();
+        nB = n * B;
+        nchunk = (int)std::min<long long>(64, std::max<long long>(1, n / 256));
+        Hm.assign(B, std::vector<double2>((size_t)(m + 1) * m));
+        g.assign(B, std::vector<double2>(m + 1));
+        cs.assign(B, std::vector<double2>(m));
+        sn.assign(B, std::vector<double2>(m));
+        beta0.assign(B, 0.0);
+        res.assign(B, 1.0);
+        kb.assign(B, 0);
+        conv.assign(B, 0);
+        act.assign(B, 0);
+        y.assign((size_t)m * B, make_double2(0, 0));
+        total = 0;
+        finished = false;
+        HZ_CU(cudaMemsetAsync(W->x64, 0, sizeof(double2) * nB, c->st));
+        dots(W->rhs64, 0, 1, W->rhs64, H());
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * B, cudaMemcpyDeviceToHost, c->st));
+    }
+    void init_host() {  // after a sync
         for (int b = 0; b < B; b++) {
-            double be = std::sqrt(std::max(Hh[b].x, 0.0));
+            beta0[b] = std::sqrt(std::max(Hh()[b].x, 0.0));
+            if (!(beta0[b] > 0)) {
+                conv[b] = 1;
+                res[b] = 0;
+            }
+        }
+        r = W->rhs64;
+        bool all = true;
+        for (int b = 0; b < B; b++)
+            if (!conv[b]) all = false;
+        finished = all;
+    }
+    // cycle start: ||r|| to the host
+    void cycle_enqueue() {
+        dots(r, 0, 1, r, H());
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * B, cudaMemcpyDeviceToHost, c->st));
+    }
+    void cycle_host() {  // after a sync: V_0 = r / beta
+        double *scale_h = W->rhost;
+        for (int b = 0; b < B; b++) {
+            double be = std::sqrt(std::max(Hh()[b].x, 0.0));
             act[b] = !conv[b] && be > 0;
             scale_h[b] = act[b] ? 1.0 / be : 0.0;
             std::fill(g[b].begin(), g[b].end(), make_double2(0, 0));
             g[b][0] = make_double2(be, 0);
             kb[b] = 0;
         }
-        HZ_CU(cudaMemcpyAsync(scale_d, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, st));
-        k_scale<<<grid1(nB), 256, 0, st>>>(r, scale_d, W.V, n, B);
+        HZ_CU(cudaMemcpyAsync(W->rnorm, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, c->st));
+        k_scale<<<grid1(nB), 256, 0, c->st>>>(r, W->rnorm, W->V, n, B);
         HZ_CU(cudaGetLastError());
         c->nl++;
-        int j = 0;
-        bool stop = false;
-        for (; j < m && !stop; j++) {
-            double2 *Vj = W.V + (long long)j * nB;
-            T2 *Zj = W.Z + (long long)j * nB;
-            // z_j = P v_j
-            k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(Vj, W.pb, nB);
+        j = 0;
+    }
+    // one Arnoldi step: z_j = P v_j, w = M z_j, CGS2, ||w||; all reductions copied in one go
+    void iter_enqueue() {
+        cudaStream_t st = c->st;
+        double2 *Vj = W->V + (long long)j * nB;
+        T2 *Zj = W->Z + (long long)j * nB;
+        k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(Vj, W->pb, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        if (kind != HZ_PNONE) precond_inplace(c, *W, kind == HZ_PJAC ? 1 : 0);
+        HZ_CU(cudaMemcpyAsync(Zj, W->pb, sizeof(T2) * nB, cudaMemcpyDeviceToDevice, st));
+        apply_M(c, *W, Zj, W->w64);
+        double2 *h1 = H(), *h2 = H() + (long long)(j + 1) * B, *nr = H() + (long long)(2 * j + 2) * B;
+        dots(W->V, nB, j + 1, W->w64, h1);
+        k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W->V, nB, h1, j + 1, W->w64, n, B);
+        HZ_CU(cudaGetLastError());
+        dots(W->V, nB, j + 1, W->w64, h2);
+        k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W->V, nB, h2, j + 1, W->w64, n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl += 2;
+        dots(W->w64, 0, 1, W->w64, nr);
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * (2 * j + 3) * B, cudaMemcpyDeviceToHost, st));
+    }
+    // after a sync: Givens update; returns true when the cycle ends
+    bool iter_host() {
+        const double2 *h1 = Hh(), *h2 = Hh() + (long long)(j + 1) * B, *nrm2 = Hh() + (long long)(2 * j + 2) * B;
+        double *scale_h = W->rhost;
+        total++;
+        bool all = true;
+        for (int b = 0; b < B; b++) {
+            const double nrm = std::sqrt(std::max(nrm2[b].x, 0.0));
+            scale_h[b] = 0.0;
+            if (!act[b]) continue;
+            auto &Hb = Hm[b];
+            for (int i = 0; i <= j; i++) Hb[(size_t)i * m + j] = h1[(size_t)i * B + b] + h2[(size_t)i * B + b];
+            Hb[(size_t)(j + 1) * m + j] = make_double2(nrm, 0);
+            for (int i = 0; i < j; i++) {  // previous rotations [c s; -conj(s) c], c real
+                double2 a = Hb[(size_t)i * m + j], bb = Hb[(size_t)(i + 1) * m + j];
+                double2 csi = cs[b][i], sni = sn[b][i];
+                double2 t1 = make_double2(csi.x * a.x + (sni.x * bb.x - sni.y * bb.y),
+                                          csi.x * a.y + (sni.x * bb.y + sni.y * bb.x));
+                double2 t2 = make_double2(-(sni.x * a.x + sni.y * a.y) + csi.x * bb.x,
+                                          -(sni.x * a.y - sni.y * a.x) + csi.x * bb.y);
+                Hb[(size_t)i * m + j] = t1;
+                Hb[(size_t)(i + 1) * m + j] = t2;
+            }
+            double2 a = Hb[(size_t)j * m + j];
+            double an = std::hypot(a.x, a.y);
+            double den = std::hypot(an, nrm);
+            double2 csj, snj;
+            if (den == 0) {
+                csj = make_double2(1, 0);
+                snj = make_double2(0, 0);
+            } else if (an == 0) {
+                csj = make_double2(0, 0);
+                snj = make_double2(1, 0);
+            } else {
+                csj = make_double2(an / den, 0);
+                snj = make_double2(a.x / an * nrm / den, a.y / an * nrm / den);
+            }
+            cs[b][j] = csj;
+            sn[b][j] = snj;
+            Hb[(size_t)j * m + j] = make_double2(csj.x * a.x + snj.x * nrm, csj.x * a.y + snj.y * nrm);
+            Hb[(size_t)(j + 1) * m + j] = make_double2(0, 0);
+            double2 gj = g[b][j];
+            g[b][j] = make_double2(csj.x * gj.x, csj.x * gj.y);
+            g[b][j + 1] = make_double2(-(snj.x * gj.x + snj.y * gj.y), -(snj.x * gj.y - snj.y * gj.x));
+            kb[b] = j + 1;
+            res[b] = std::hypot(g[b][j + 1].x, g[b][j + 1].y) / beta0[b];
+            if (res[b] <= tol) {
+                conv[b] = 1;
+                act[b] = 0;
+            } else if (nrm > 1e-300) {
+                scale_h[b] = 1.0 / nrm;
+            } else {  // exact breakdown: the solution is in the current space
+                act[b] = 0;
+                conv[b] = 1;
+            }
+            if (act[b]) all = false;
+        }
+        j++;
+        const bool stop = all || total >= maxit || j >= m;
+        if (!stop) {
+            HZ_CU(cudaMemcpyAsync(W->rnorm, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, c->st));
+            k_scale<<<grid1(nB), 256, 0, c->st>>>(W->w64, W->rnorm, W->V + (long long)j * nB, n, B);
             HZ_CU(cudaGetLastError());
             c->nl++;
-            if (kind != HZ_PNONE) precond_inplace(c, W, kind == HZ_PJAC ? 1 : 0);
-            HZ_CU(cudaMemcpyAsync(Zj, W.pb, sizeof(T2) * nB, cudaMemcpyDeviceToDevice, st));
-            // w = M z_j
-            apply_M(c, W, Zj, W.w64);
-            // CGS2
-            dots(W.V, nB, j + 1, W.w64, H, 0);
-            k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W.V, nB, H, j + 1, W.w64, n, B);
-            HZ_CU(cudaGetLastError());
-            dots(W.V, nB, j + 1, W.w64, H + (long long)(j + 1) * B, 0);
-            k_axpy_multi<<<grid1(nB), 256, 0, st>>>(W.V, nB, H + (long long)(j + 1) * B, j + 1, W.w64, n, B);
-            HZ_CU(cudaGetLastError());
-            c->nl += 2;
-            // host copy of both passes, then the norm
-            std::vector<double2> h1((size_t)(j + 1) * B), h2((size_t)(j + 1) * B);
-            HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * (j + 1) * B, cudaMemcpyDeviceToHost, st));
-            HZ_CU(cudaStreamSynchronize(st));
-            std::memcpy(h1.data(), Hh, sizeof(double2) * (j + 1) * B);
-            HZ_CU(cudaMemcpyAsync(Hh, H + (long long)(j + 1) * B, sizeof(double2) * (j + 1) * B, cudaMemcpyDeviceToHost,
-                                  st));
-            HZ_CU(cudaStreamSynchronize(st));
-            std::memcpy(h2.data(), Hh, sizeof(double2) * (j + 1) * B);
-            dots(W.w64, 0, 1, W.w64, H, 0);
-            HZ_CU(cudaMemcpyAsync(Hh, H, sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
-            HZ_CU(cudaStreamSynchronize(st));
-            total++;
-            bool all = true;
-            for (int b = 0; b < B; b++) {
-                double nrm = std::sqrt(std::max(Hh[b].x, 0.0));
-                scale_h[b] = 0.0;
-                if (!act[b]) continue;
-                auto &Hb = Hm[b];
-                for (int i = 0; i <= j; i++) Hb[(size_t)i * m + j] = h1[(size_t)i * B + b] + h2[(size_t)i * B + b];
-                Hb[(size_t)(j + 1) * m + j] = make_double2(nrm, 0);
-                // apply previous rotations
-                for (int i = 0; i < j; i++) {
-                    double2 a = Hb[(size_t)i * m + j], bb = Hb[(size_t)(i + 1) * m + j];
-                    double2 csi = cs[b][i], sni = sn[b][i];
-                    // [c s; -conj(s) c] with c real
-                    double2 t1 = make_double2(csi.x * a.x + (sni.x * bb.x - sni.y * bb.y),
-                                              csi.x * a.y + (sni.x * bb.y + sni.y * bb.x));
-                    double2 t2 = make_double2(-(sni.x * a.x + sni.y * a.y) + csi.x * bb.x,
-                                              -(sni.x * a.y - sni.y * a.x) + csi.x * bb.y);
-                    Hb[(size_t)i * m + j] = t1;
-                    Hb[(size_t)(i + 1) * m + j] = t2;
-                }
-                double2 a = Hb[(size_t)j * m + j];
-                double bn = nrm;
-                double an = std::hypot(a.x, a.y);
-                double den = std::hypot(an, bn);
-                double2 csj, snj;
-                if (den == 0) {
-                    csj = make_double2(1, 0);
-                    snj = make_double2(0, 0);
-                } else if (an == 0) {
-                    csj = make_double2(0, 0);
-                    snj = make_double2(1, 0);
-                } else {
-                    csj = make_double2(an / den, 0);
-                    // s = (a/|a|) * conj(b) / den, b real here
-                    snj = make_double2(a.x / an * bn / den, a.y / an * bn / den);
-                }
-                cs[b][j] = csj;
-                sn[b][j] = snj;
-                Hb[(size_t)j * m + j] = make_double2(csj.x * a.x + (snj.x * bn), csj.x * a.y + (snj.y * bn));
-                Hb[(size_t)(j + 1) * m + j] = make_double2(0, 0);
-                double2 gj = g[b][j];
-                g[b][j] = make_double2(csj.x * gj.x, csj.x * gj.y);
-                g[b][j + 1] = make_double2(-(snj.x * gj.x + snj.y * gj.y), -(snj.x * gj.y - snj.y * gj.x));
-                kb[b] = j + 1;
-                res[b] = std::hypot(g[b][j + 1].x, g[b][j + 1].y) / beta0[b];
-                if (res[b] <= tol) {
-                    conv[b] = 1;
-                    act[b] = 0;
-                } else if (nrm > 1e-300) {
-                    scale_h[b] = 1.0 / nrm;
-                } else {
-                    act[b] = 0;  // exact breakdown: solution in the current space
-                    conv[b] = 1;
-                }
-                if (act[b]) all = false;
-            }
-            if (all || total >= maxit) stop = true;
-            if (!stop && j + 1 < m) {
-                HZ_CU(cudaMemcpyAsync(scale_d, scale_h, sizeof(double) * B, cudaMemcpyHostToDevice, st));
-                k_scale<<<grid1(nB), 256, 0, st>>>(W.w64, scale_d, W.V + (long long)(j + 1) * nB, n, B);
-                HZ_CU(cudaGetLastError());
-                c->nl++;
-            }
         }
-        // y = R^{-1} g per RHS, x += Z y
-        const int jj = j;
+        return stop;
+    }
+    // cycle end: x += Z y; returns true when FGMRES is done, else enqueues the restart residual
+    bool cycle_finish() {
+        cudaStream_t st = c->st;
         std::fill(y.begin(), y.end(), make_double2(0, 0));
         for (int b = 0; b < B; b++) {
-            int k = kb[b];
+            const int k = kb[b];
             auto &Hb = Hm[b];
             std::vector<double2> yb(k);
             for (int i = k - 1; i >= 0; i--) {
-                double2 s = g[b][i];
-                for (int q = i + 1; q < k; q++) s = s - Hb[(size_t)i * m + q] * yb[q];
-                yb[i] = cdiv(s, Hb[(size_t)i * m + i]);
+                double2 sacc = g[b][i];
+                for (int q = i + 1; q < k; q++) sacc = sacc - Hb[(size_t)i * m + q] * yb[q];
+                yb[i] = cdiv(sacc, Hb[(size_t)i * m + i]);
             }
             for (int i = 0; i < k; i++) y[(size_t)i * B + b] = yb[i];
         }
-        HZ_CU(cudaStreamSynchronize(st));
-        HZ_CU(cudaMemcpyAsync(y_d, y.data(), sizeof(double2) * jj * B, cudaMemcpyHostToDevice, st));
-        k_update_x<T2><<<grid1(nB), 256, 0, st>>>(W.Z, nB, y_d, jj, W.x64, n, B);
+        double2 *y_d = (double2 *)W->dots;  // reduction scratch is idle here
+        HZ_CU(cudaMemcpyAsync(y_d, y.data(), sizeof(double2) * j * B, cudaMemcpyHostToDevice, st));
+        k_update_x<T2><<<grid1(nB), 256, 0, st>>>(W->Z, nB, y_d, j, W->x64, n, B);
         HZ_CU(cudaGetLastError());
         c->nl++;
-        HZ_CU(cudaStreamSynchronize(st));
         bool all = true;
         for (int b = 0; b < B; b++)
             if (!conv[b]) all = false;
-        if (all || total >= maxit) break;
-        // restart: r = rhs - M x
-        k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(W.x64, W.pa, nB);
+        if (all || total >= maxit) {
+            finished = true;
+            return true;
+        }
+        k_cast<double2, T2><<<grid1(nB), 256, 0, st>>>(W->x64, W->pa, nB);
         HZ_CU(cudaGetLastError());
         c->nl++;
-        apply_M(c, W, W.pa, W.w64);
-        k_sub<<<grid1(nB), 256, 0, st>>>(W.rhs64, W.w64, W.w64, nB);
+        apply_M(c, *W, W->pa, W->w64);
+        k_sub<<<grid1(nB), 256, 0, st>>>(W->rhs64, W->w64, W->w64, nB);
         HZ_CU(cudaGetLastError());
         c->nl++;
-        r = W.w64;
+        r = W->w64;
+        return false;
     }
-    out.iters = total;
-    out.resid = 0;
-    for (int b = 0; b < B; b++) out.resid = std::max(out.resid, res[b]);
-    return out;
+    GmresOut out() const {
+        GmresOut o;
+        o.iters = total;
+        for (int b = 0; b < B; b++) o.resid = std::max(o.resid, res[b]);
+        return o;
+    }
+};
+
+static void sync_all(const std::vector<hz_ctx *> &cs) {
+    for (hz_ctx *c : cs) HZ_CU(cudaStreamSynchronize(c->st));
+}
+
+// Lockstep FGMRES over several contexts (each on its own stream)
+template <class T2> static void fgmres_group(std::vector<Fgmres<T2> *> &gs) {
+    std::vector<hz_ctx *> cs;
+    for (auto *g : gs) cs.push_back(g->c);
+    sync_all(cs);
+    for (auto *g : gs) g->init_host();
+    while (true) {
+        std::vector<Fgmres<T2> *> live;
+        for (auto *g : gs)
+            if (!g->finished) live.push_back(g);
+        if (live.empty()) break;
+        for (auto *g : live) g->cycle_enqueue();
+        sync_all(cs);
+        for (auto *g : live) g->cycle_host();
+        std::vector<Fgmres<T2> *> in_cycle = live;
+        while (!in_cycle.empty()) {
+            for (auto *g : in_cycle) g->iter_enqueue();
+            sync_all(cs);
+            std::vector<Fgmres<T2> *> next;
+            for (auto *g : in_cycle)
+                if (!g->iter_host()) next.push_back(g);
+                else g->cycle_finish();
+            in_cycle.swap(next);
+        }
+    }
+}
+
+template <class T2>
+static GmresOut fgmres(hz_ctx *c, Work<T2> &W, double tol, int maxit, int kind) {
+    Fgmres<T2> g;
+    g.init(c, W, tol, maxit, kind);
+    std::vector<Fgmres<T2> *> gs{&g};
+    fgmres_group(gs);
+    return g.out();
 }
 
 // ------------------------------------------------------- nested solve ---
@@ -1188,15 +1256,14 @@ static double now_ms() {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// One pass of Alg. matrix_free_solver on the symmetric-form source src
-// ([N][B], FP64); the volume correction is added to W.u.
-template <class T2>
-static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double tol, int maxit, Timers &tm) {
+// Stage 1 of a pass of Alg. matrix_free_solver (lines 2-7) on the
+// symmetric-form source src ([N][B], FP64): Newton potentials of every layer
+// through cell solves and inner sweeps, sampled into the polarized
+// right-hand side.
+template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const double2 *src) {
     cudaStream_t st = c->st;
     const int B = W.B, L = c->L, ncell = (int)c->cells.size();
     const int nb = (int)std::min<long long>(1024, (c->tot_vol * B / ncell + 255) / 256 + 1);
-    double t0 = now_ms();
-    // 1. Newton potentials: cell solves of the partitioned source
     k_scatter<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, src, W.vol, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
@@ -1216,14 +1283,13 @@ static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double t
     k_pol_rhs<T2><<<grid1(c->n_tr() * B), 256, 0, st>>>(W.lout, W.rhs64, L - 1, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
-    HZ_CU(cudaStreamSynchronize(st));
-    double t1 = now_ms();
-    tm.local += t1 - t0;
-    // 2. traces
-    GmresOut go = fgmres(c, W, tol, maxit, c->opts.precond);
-    double t2 = now_ms();
-    tm.gmres += t2 - t1;
-    // 3. reconstruction
+}
+
+// Stage 3 (lines 10-18): the volume from the traces, added to W.u.
+template <class T2> static void recon_enqueue(hz_ctx *c, Work<T2> &W) {
+    cudaStream_t st = c->st;
+    const int B = W.B, L = c->L, ncell = (int)c->cells.size();
+    const int nb = (int)std::min<long long>(1024, (c->tot_vol * B / ncell + 255) / 256 + 1);
     k_traces<T2><<<grid1((long long)(L - 1) * 2 * c->NX * B), 256, 0, st>>>(W.x64, W.pc, L - 1, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
@@ -1239,12 +1305,24 @@ static GmresOut nested_pass(hz_ctx *c, Work<T2> &W, const double2 *src, double t
     k_accum_u<T2><<<dim3(nb, ncell), 256, 0, st>>>(c->d_cells, W.vol, W.vol2, W.u, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
-    HZ_CU(cudaStreamSynchronize(st));
-    tm.recon += now_ms() - t2;
-    return go;
 }
 
-// per-RHS ||alpha r||^2 partial sums -> host (mode 0 writes r = fs - H u)
+// per-RHS ||alpha r||^2 partial sums -> host buffer (mode 0 writes r = fs - H u);
+// enqueued only: valid after the stream synchronises
+static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
+                             int mode, double *part) {
+    const int nchunk = 256;
+    dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
+    k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ, B, part,
+                                     nchunk, mode);
+    HZ_CU(cudaGetLastError());
+    double *fin = part + (long long)nchunk * B;
+    k_reduce_parts<<<(B + 255) / 256, 256, 0, c->st>>>(part, nchunk, B, fin);
+    HZ_CU(cudaGetLastError());
+    c->nl += 2;
+    HZ_CU(cudaMemcpyAsync(out_host, fin, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st));
+}
+
 static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
                            int mode, double *part) {
     const int nchunk = 256;
@@ -1261,6 +1339,8 @@ static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, doubl
 }
 
 void init_global_alpha(hz_ctx *c) {
+    c->d_err = (int *)c->dalloc(sizeof(int));
+    HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
     c->d_ax = (double2 *)c->dalloc(sizeof(double2) * c->NX);
     c->d_axh = (double2 *)c->dalloc(sizeof(double2) * (c->NX + 1));
     c->d_az = (double2 *)c->dalloc(sizeof(double2) * c->NZ);
@@ -1298,68 +1378,142 @@ void init_global_alpha(hz_ctx *c) {
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 
-// Full solve: f (device, batch-outer [B][N]) -> u (device, batch-outer), stats.
+// Solve of a group of contexts (one medium/frequency each, each on its own
+// stream), advanced in lockstep: Newton potentials, FGMRES, reconstruction
+// and the FP64 residual of every member are enqueued before the host waits,
+// so members overlap on the GPU.  A single context is a group of one.
+// f_dev[i], u_dev[i]: device, batch-outer [B][N].
+template <class T2>
+int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const double2 *> &f_dev, int B,
+                     const std::vector<double2 *> &u_dev, std::vector<hz_stats> &stats, bool scale_src) {
+    const int G = (int)cs.size();
+    std::vector<Work<T2> *> Ws(G);
+    std::vector<std::vector<double>> fn(G, std::vector<double>(B)), rn(G, std::vector<double>(B));
+    std::vector<Timers> tm(G);
+    std::vector<int> status(G, HZ_OK), pass_done(G, 0);
+    std::vector<double> prev(G, 1.0), worst(G, 0.0);
+    std::vector<const double2 *> src(G);
+    stats.assign(G, hz_stats{});
+    const double t0 = now_ms();
+    for (int i = 0; i < G; i++) {
+        hz_ctx *c = cs[i];
+        Ws[i] = &work<T2>(c, B);
+        Work<T2> &W = *Ws[i];
+        const long long N = (long long)c->NX * c->NZ;
+        transpose_in(c, f_dev[i], W.gsrc, N, B, scale_src);
+        HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, c->st));
+        residual_enqueue(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
+        src[i] = W.gsrc;
+    }
+    sync_all(cs);
+    for (int i = 0; i < G; i++)
+        for (int b = 0; b < B; b++) fn[i][b] = std::sqrt(Ws[i]->rhost[b]);
+    const int max_pass = std::max(1, cs[0]->opts.refine_tol > 0 ? cs[0]->opts.max_refine : 1);
+    std::vector<int> live(G, 1);
+    for (int pass = 0; pass < max_pass; pass++) {
+        std::vector<int> idx;
+        for (int i = 0; i < G; i++)
+            if (live[i]) idx.push_back(i);
+        if (idx.empty()) break;
+        std::vector<hz_ctx *> cl;
+        for (int i : idx) cl.push_back(cs[i]);
+        double ta = now_ms();
+        for (int i : idx) newton_enqueue<T2>(cs[i], *Ws[i], src[i]);
+        sync_all(cl);
+        double tb = now_ms();
+        std::vector<Fgmres<T2>> gm(idx.size());
+        std::vector<Fgmres<T2> *> gp;
+        for (size_t q = 0; q < idx.size(); q++) {
+            hz_ctx *c = cs[idx[q]];
+            const double tol = c->opts.tol, rtol = c->opts.refine_tol;
+            double ptol = tol;
+            // a pass on the residual only has to shrink it to the target, with a 10x margin
+            if (pass > 0 && rtol > 0) ptol = std::min(0.1, std::max(tol, 0.1 * rtol / std::max(prev[idx[q]], 1e-300)));
+            gm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
+            gp.push_back(&gm[q]);
+        }
+        fgmres_group(gp);
+        double tc = now_ms();
+        for (int i : idx) recon_enqueue<T2>(cs[i], *Ws[i]);
+        sync_all(cl);
+        double td = now_ms();
+        for (int i : idx) {
+            Work<T2> &W = *Ws[i];
+            residual_enqueue(cs[i], W.u, W.gsrc, W.io, B, W.rhost, 0, W.rnorm);
+        }
+        sync_all(cl);
+        double te = now_ms();
+        for (size_t q = 0; q < idx.size(); q++) {
+            const int i = idx[q];
+            hz_ctx *c = cs[i];
+            Work<T2> &W = *Ws[i];
+            tm[i].local += tb - ta;
+            tm[i].gmres += tc - tb;
+            tm[i].recon += td - tc;
+            tm[i].resid += te - td;
+            GmresOut go = gm[q].out();
+            stats[i].iterations += go.iters;
+            stats[i].gmres_resid = go.resid;
+            stats[i].refinements = pass + 1;
+            worst[i] = 0;
+            for (int b = 0; b < B; b++) {
+                rn[i][b] = fn[i][b] > 0 ? std::sqrt(W.rhost[b]) / fn[i][b] : 0.0;
+                worst[i] = std::max(worst[i], rn[i][b]);
+            }
+            const double rtol = c->opts.refine_tol;
+            if (go.resid > gm[q].tol && !c->mixed()) status[i] = HZ_ENOTCONV;
+            prev[i] = worst[i];
+            if (rtol <= 0 || worst[i] <= rtol) {
+                live[i] = 0;
+            } else {
+                src[i] = W.io;  // next pass solves for the correction from the FP64 residual
+            }
+        }
+    }
+    for (int i = 0; i < G; i++) {
+        hz_ctx *c = cs[i];
+        Work<T2> &W = *Ws[i];
+        const double rtol = c->opts.refine_tol;
+        if (rtol > 0 && worst[i] > rtol) status[i] = HZ_ENOTCONV;
+        stats[i].resid = worst[i];
+        transpose_out(c, W.u, u_dev[i], (long long)c->NX * c->NZ, B);
+    }
+    sync_all(cs);
+    for (int i = 0; i < G; i++) {
+        hz_ctx *c = cs[i];
+        int e = 0;
+        HZ_CU(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e) {
+            HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
+            throw HzError(HZ_ETIMEOUT, "an inter-CTA exchange in the inner sweep timed out; results are invalid");
+        }
+        stats[i].t_total_ms = now_ms() - t0;
+        stats[i].t_local_ms = tm[i].local;
+        stats[i].t_gmres_ms = tm[i].gmres;
+        stats[i].t_recon_ms = tm[i].recon;
+        stats[i].t_resid_ms = tm[i].resid;
+    }
+    int worst_status = HZ_OK;
+    for (int i = 0; i < G; i++)
+        if (status[i] != HZ_OK) worst_status = status[i];
+    return worst_status;
+}
+template int solve_group_impl<double2>(const std::vector<hz_ctx *> &, const std::vector<const double2 *> &, int,
+                                       const std::vector<double2 *> &, std::vector<hz_stats> &, bool);
+template int solve_group_impl<float2>(const std::vector<hz_ctx *> &, const std::vector<const double2 *> &, int,
+                                      const std::vector<double2 *> &, std::vector<hz_stats> &, bool);
+
+// Full solve of one context: f (device, batch-outer [B][N]) -> u (device), stats.
 template <class T2>
 int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st_out, bool scale_src) {
-    Work<T2> &W = work<T2>(c, B);
-    cudaStream_t st = c->st;
-    const long long N = (long long)c->NX * c->NZ;
-    Timers tm;
-    hz_stats s{};
-    double t0 = now_ms();
-    // source in the row-scaled form, [N][B]
-    transpose_in(c, f_dev, W.gsrc, N, B, scale_src);
-    HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, st));
-    std::vector<double> fn(B), rn(B);
-    residual_norms(c, W.u, W.gsrc, nullptr, B, W.rhost, 1, W.rnorm);
-    for (int b = 0; b < B; b++) fn[b] = std::sqrt(W.rhost[b]);
-    const bool mixed = c->mixed();
-    double tol = c->opts.tol;
-    const double rtol = c->opts.refine_tol;
-    const int max_pass = rtol > 0 ? std::max(1, c->opts.max_refine) : 1;
-    const double2 *src = W.gsrc;
-    int status = HZ_OK;
-    double worst = 0;
-    double prev = 1.0;  // residual (relative to f) before the pass
-    for (int pass = 0; pass < max_pass; pass++) {
-        // a pass on the residual only has to shrink it to the target, with a
-        // 10x margin; the precision floor keeps the first pass at opts.tol
-        double ptol = tol;
-        if (pass > 0 && rtol > 0) ptol = std::min(0.1, std::max(tol, 0.1 * rtol / std::max(prev, 1e-300)));
-        GmresOut go = nested_pass<T2>(c, W, src, ptol, c->opts.max_it, tm);
-        s.iterations += go.iters;
-        s.gmres_resid = go.resid;
-        s.refinements = pass + 1;
-        double tr0 = now_ms();
-        // residual r = fs - H u into io (reused as the next source)
-        residual_norms(c, W.u, W.gsrc, W.io, B, W.rhost, 0, W.rnorm);
-        tm.resid += now_ms() - tr0;
-        worst = 0;
-        for (int b = 0; b < B; b++) {
-            rn[b] = fn[b] > 0 ? std::sqrt(W.rhost[b]) / fn[b] : 0.0;
-            worst = std::max(worst, rn[b]);
-        }
-        if (go.resid > ptol && !mixed) status = HZ_ENOTCONV;
-        prev = worst;
-        if (rtol <= 0 || worst <= rtol) break;
-        src = W.io;
-        (void)mixed;
-    }
-    if (rtol > 0 && worst > rtol) status = HZ_ENOTCONV;
-    s.resid = worst;
-    transpose_out(c, W.u, u_dev, N, B);
-    HZ_CU(cudaStreamSynchronize(st));
-    s.t_total_ms = now_ms() - t0;
-    s.t_local_ms = tm.local;
-    s.t_gmres_ms = tm.gmres;
-    s.t_recon_ms = tm.recon;
-    s.t_resid_ms = tm.resid;
+    std::vector<hz_stats> sts;
+    int r = solve_group_impl<T2>({c}, {f_dev}, B, {u_dev}, sts, scale_src);
     if (st_out) {
         int keep = st_out->gpu_launches;
-        *st_out = s;
+        *st_out = sts[0];
         st_out->gpu_launches = keep;
     }
-    return status;
+    return r;
 }
 template int solve_impl<double2>(hz_ctx *, const double2 *, int, double2 *, hz_stats *, bool);
 template int solve_impl<float2>(hz_ctx *, const double2 *, int, double2 *, hz_stats *, bool);

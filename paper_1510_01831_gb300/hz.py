@@ -26,7 +26,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
                 "HZ_ESINGULAR"]
 
 # every entry point declared in include/hz.h
-EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_gradient", "hz_cell_solve",
+EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_cell_solve",
            "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
            "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
@@ -85,7 +85,9 @@ def load() -> ctypes.CDLL:
             L.hz_setup.argtypes = [P(vp), vp, i, i, d, d, i, i, i, P(HzOpts)]
             L.hz_factor.argtypes = [vp]
             L.hz_solve.argtypes = [vp, vp, i, vp, P(HzStats)]
+            L.hz_solve_group.argtypes = [P(vp), i, P(vp), i, P(vp), P(HzStats)]
             L.hz_gradient.argtypes = [vp, vp, i, vp, vp, i, P(d), vp, vp, P(HzStats)]
+            L.hz_adjoint.argtypes = [vp, vp, vp, i, vp, vp, P(HzStats)]
             L.hz_cell_solve.argtypes = [vp, i, i, vp, i, vp]
             L.hz_layer_green.argtypes = [vp, i, vp, i, i, vp]
             L.hz_apply_M.argtypes = [vp, vp, i, vp]
@@ -101,7 +103,7 @@ def load() -> ctypes.CDLL:
             L.hz_destroy.restype = None
             L.hz_last_error.argtypes = [vp]
             L.hz_last_error.restype = ctypes.c_char_p
-            for name in ("hz_setup", "hz_factor", "hz_solve", "hz_gradient", "hz_cell_solve", "hz_layer_green",
+            for name in ("hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_cell_solve", "hz_layer_green",
                          "hz_apply_M", "hz_precond", "hz_residual"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -228,6 +230,21 @@ class Context:
             _check(st, self._ctx)
         return J.value, grad, u, s
 
+    def hz_adjoint(self, u, gu, want_grad_f=True):
+        """(grad_m, grad_f, stats) for a loss with gradient gu = dL/dRe(u) + i dL/dIm(u)."""
+        u, gu = self._in(u), self._in(gu)
+        B = u.shape[0]
+        grad_m = self._alloc((self.NZ, self.NX), np.float64, like=u)
+        grad_f = self._alloc(tuple(u.shape), like=u) if want_grad_f else None
+        s = HzStats()
+        st = load().hz_adjoint(self._ctx, _ptr(u, self.device), _ptr(gu, self.device), B, _ptr(grad_m, self.device),
+                               _ptr(grad_f, self.device) if grad_f is not None else None, ctypes.byref(s))
+        if st == HZ_ENOTCONV:
+            s.converged = False
+        else:
+            _check(st, self._ctx)
+        return grad_m, grad_f, s
+
     def hz_cell_solve(self, l, c, g):
         g = self._in(g)
         x = self._alloc(tuple(g.shape), like=g)
@@ -279,3 +296,30 @@ class Context:
 
     def hz_device_bytes(self) -> int:
         return int(load().hz_device_bytes(self._ctx))
+
+
+def hz_solve_group(ctxs, fs, us=None):
+    """Solve the G problems ctxs[i] H u_i = fs[i] together (one batch size B for
+    all; each context on its own stream for overlap).  Returns (us, stats)."""
+    G = len(ctxs)
+    if G < 1 or len(fs) != G:
+        raise ValueError("need one source array per context")
+    fs = [c._in(f) for c, f in zip(ctxs, fs)]
+    B = fs[0].shape[0]
+    if any(f.shape[0] != B for f in fs):
+        raise ValueError("every member needs the same batch size B")
+    if us is None:
+        us = [c._alloc(tuple(f.shape), like=f) for c, f in zip(ctxs, fs)]
+    vp = ctypes.c_void_p
+    hs = (vp * G)(*[c._ctx for c in ctxs])
+    fp = (vp * G)(*[_ptr(f, c.device) for c, f in zip(ctxs, fs)])
+    up = (vp * G)(*[_ptr(u, c.device) for c, u in zip(ctxs, us)])
+    sts = (HzStats * G)()
+    st = load().hz_solve_group(hs, G, fp, B, up, sts)
+    stats = [sts[i] for i in range(G)]
+    if st == HZ_ENOTCONV:
+        for s in stats:
+            s.converged = False
+    else:
+        _check(st, ctxs[0]._ctx)
+    return us, stats

@@ -92,3 +92,8 @@ def test_null_context_calls_fail_cleanly():
     assert lib.hz_solve(None, None, 1, None, None) == hz.HZ_EINVAL
     assert lib.hz_device_bytes(None) == 0
     lib.hz_destroy(None)
+    assert lib.hz_solve_group(None, 1, None, 1, None, None) == hz.HZ_EINVAL
+    G = 2
+    hs = (ctypes.c_void_p * G)(None, None)
+    assert lib.hz_solve_group(hs, G, None, 1, None, None) == hz.HZ_EINVAL
+    assert lib.hz_solve_group(hs, 0, None, 1, None, None) == hz.HZ_EINVAL

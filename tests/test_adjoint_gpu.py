@@ -1,0 +1,70 @@
+"""Adjoint entry point and the PyTorch autograd wrapper against the oracle."""
+import numpy as np
+import pytest
+
+import hz_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+hz = pytest.importorskip("paper_1510_01831_gb300.hz")
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def case():
+    pb = I.smooth_random(48, n_pml=5, L=3, C=2, seed=71, ppw=8, corr_pts=8, n_z=40)
+    C_pml = O.default_pml_C(pb.m)
+    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
+    return pb, C_pml, box, box.factor()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("mixed", 1e-5)])
+def test_hz_adjoint_matches_oracle(case, precision, tol):
+    pb, C_pml, box, fac = case
+    B = 3
+    f = I.random_sources(pb.shape_ext, pb.n_pml, B, 72)
+    rng = np.random.default_rng(73)
+    gu = rng.standard_normal(f.shape) + 1j * rng.standard_normal(f.shape)
+    prec = hz.HZ_FP64 if precision == "fp64" else hz.HZ_MIXED
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec, pml_C=C_pml)
+    ctx.hz_factor()
+    u, _ = ctx.hz_solve(f)
+    gm, gf, st = ctx.hz_adjoint(u, gu)
+    ctx.close()
+    uo = fac.solve(f)
+    mu = fac.solve(np.conj(gu), trans=True)
+    gm_ref = pb.omega ** 2 * np.sum(np.real(mu * uo), axis=0)
+    assert _rel(gm, gm_ref) < tol
+    assert _rel(gf, np.conj(mu)) < tol
+
+
+def test_autograd_matches_finite_differences(case):
+    torch = pytest.importorskip("torch")
+    from paper_1510_01831_gb300 import torch_ops
+    pb, C_pml, box, fac = case
+    B = 2
+    f = torch.from_numpy(I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, B)).cuda()
+    w = torch.from_numpy(np.random.default_rng(74).random(pb.shape_ext)).cuda()
+    m = torch.from_numpy(pb.m.copy()).cuda().requires_grad_(True)
+    op = torch_ops.HelmholtzOperator(m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, pml_C=C_pml)
+    u = op(m, f)
+    loss = (w * u.abs() ** 2).sum()
+    loss.backward()
+    g = m.grad.cpu().numpy()
+    op.close()
+
+    def J(mm):
+        uu = O.Box(mm, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml).factor().solve(f.cpu().numpy())
+        return float(np.sum(w.cpu().numpy() * np.abs(uu) ** 2))
+    rng = np.random.default_rng(75)
+    for i in rng.choice(pb.m.size, 6, replace=False):
+        eps = 1e-6 * pb.m.reshape(-1)[i]
+        mp, mm_ = pb.m.copy(), pb.m.copy()
+        mp.reshape(-1)[i] += eps
+        mm_.reshape(-1)[i] -= eps
+        fd = (J(mp) - J(mm_)) / (2 * eps)
+        assert abs(fd - g.reshape(-1)[i]) <= 1e-5 * np.abs(g).max() + 1e-4 * abs(fd)
