@@ -380,12 +380,14 @@ template void launch_cell_chain<float2>(const CellDesc *, int, const float2 *, c
 // are the recurrence
 //   forward : y_0 = h_0,        y_j = h_j + P_j y_{j-1}   (j = 1..J-1)
 //   backward: x_{J-1} = y_{J-1}, x_j = y_j + V_j x_{j+1}   (j = J-2..0)
-// One thread-block cluster of R CTAs runs the recurrence of one layer for NB
-// right-hand sides: CTA r owns a slab of rows of every Q_j (prefetched into
-// registers one step ahead), computes its rows of z_j from the full z_{j-1}
-// kept in its shared memory, writes them to global memory and pushes them into
-// the shared memory of every CTA of the cluster (distributed shared memory);
-// one cluster barrier per step publishes z_j.  There are no spin waits.
+// One thread-block cluster of R CTAs runs the recurrence of one layer for a
+// tile of right-hand sides.  CTA r owns a slab of rows of every Q_j and of z_j;
+// each step it computes its rows of z_j from the whole z_{j-1} held in its
+// shared memory, stores them to global memory and pushes them into the shared
+// memory of every CTA of the cluster (distributed shared memory), where they
+// complete a transaction-count mbarrier.  Every wait is bounded: a CTA that
+// gives up sets the error word (HZ_ETIMEOUT on the host) and the kernel still
+// ends.
 // Layout: slot j+1 of the layer's inner buffer holds interface j ([2nz][B]).
 // shared-memory / cluster helpers (inline PTX)
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -420,12 +422,65 @@ __device__ __forceinline__ void bulk_to_peer(unsigned dst_cluster, unsigned src_
         : "memory");
 }
 
+__device__ __forceinline__ bool mbar_try_acq_cluster(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bulk (TMA) copy global -> this CTA's shared memory, completing on its mbarrier
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+// 16-byte store into a CTA of the cluster, completing on that CTA's mbarrier
+__device__ __forceinline__ void st_async16(unsigned dst, uint4 v, unsigned mb) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     dst),
+                 "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(mb)
+                 : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// wait for phase `parity` of an mbarrier for at most 1 s (1 ms once the
+// thread has already given up somewhere); on expiry set the error word and
+// `dead` and return false
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned mb, unsigned parity, bool cluster_scope, bool &dead,
+                                                  int *err) {
+    const unsigned long long limit_ns = dead ? 1000000ull : 1000000000ull;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; it++) {
+        if (cluster_scope ? mbar_try_acq_cluster(mb, parity) : mbar_try(mb, parity)) return true;
+        if ((it & 63u) == 63u) {
+            const unsigned long long t = global_ns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > limit_ns) {
+                if (!dead) atomicExch(err, 1);
+                dead = true;
+                return false;
+            }
+        }
+    }
+}
+
 // padded row stride of the Q slab in shared memory (breaks bank aliasing of
 // rows that are 2*nz complex apart, keeps 16-byte alignment)
 template <class T2> __host__ __device__ inline int q_ld(int n2) { return sizeof(T2) == 8 ? n2 + 2 : n2 + 1; }
 
+// Fallback form for operators whose row slabs do not fit the staged kernel
+// below (e.g. FP64 with 2nz' > 256): the Q slab is prefetched through
+// registers one step ahead and slabs move between CTAs by bulk copies.
 template <class T2, int NB>
-__global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict__ layers,
+__global__ void __launch_bounds__(256) k_inner_sweep_regq(const LayerDesc *__restrict__ layers,
                                                      const int *__restrict__ ids, const T2 *__restrict__ P,
                                                      const T2 *__restrict__ V, const T2 *__restrict__ H, T2 *X,
                                                      int B, int *err) {
@@ -515,7 +570,8 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
     const unsigned my_bytes = (unsigned)(nr * NB * sizeof(T2));
     unsigned ph0 = 0u, ph1 = 0u;
     bool dead = false;
-    for (int s = 0; s < S; s++) {
+    // CTAs without rows (2nz' < R * rows-per-CTA) neither send nor receive
+    for (int s = 0; s < S && nr > 0; s++) {
         const int bo = (s & 1) ^ 1;  // input z_s in zb[s&1], output z_{s+1} into zb[bo]
         T2 *cur = bo ? zb0 : zb1, *nxt = bo ? zb1 : zb0;
         if (use_pf) {
@@ -595,29 +651,19 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
             if (my_bytes > 0) {
                 const unsigned src = smem_u32(nxt + r0 * NB);
                 for (int d = 0; d < R; d++) {
-                    if (d == rank) continue;
+                    if (d == rank || d * rs >= n2) continue;
                     bulk_to_peer(cluster_map(src, d), src, my_bytes, cluster_map(mb_local, d));
                 }
             }
         }
-        {   // wait for every peer's slab (bounded; a timeout marks the run failed and
-            // later waits use a short limit so the kernel still terminates)
-            const unsigned mb_local = smem_u32(&mbar[bo]);
-            const unsigned par = bo ? ph1 : ph0;
-            const long long limit = dead ? 4096 : (1LL << 26);
-            long long it = 0;
-            while (!mbar_try(mb_local, par)) {
-                if (++it >= limit) {
-                    if (!dead && tid == 0) atomicExch(err, 1);
-                    dead = true;
-                    break;
-                }
-            }
-            if (bo) ph1 ^= 1u; else ph0 ^= 1u;
-        }
+        // wait for every peer's slab (bounded: a timeout sets the error word and the
+        // whole CTA leaves the steps together)
+        mbar_wait_bounded(smem_u32(&mbar[bo]), bo ? ph1 : ph0, false, dead, err);
+        if (bo) ph1 ^= 1u; else ph0 ^= 1u;
+        if (__syncthreads_or(dead)) break;
         bcur = bnext;
     }
-    if (S > 0) {
+    if (S > 0 && !dead) {
         const T2 *cur = (S & 1) ? zb1 : zb0;
         T2 *outp = x + (long long)(step_j(S - 1) + 1) * slot;
         for (int e = tid; e < nr * NB; e += 256) {
@@ -626,10 +672,11 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
         }
     }
     cl.sync();  // no CTA leaves while peers may still copy into or out of it
+    if (__syncthreads_or(dead)) __nanosleep(20000);  // copies a timed-out peer issued may still be landing
 }
 
 template <class T2, int NB>
-static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
+static bool inner_sweep_regq(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
                            const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
     const int groups = (B + NB - 1) / NB;
     auto smem = [&](int R) {
@@ -642,7 +689,7 @@ static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer
     // preferred: the largest cluster (smallest row slab per CTA, so the
     // slab fits the register prefetch and each step's dot products are short)
     int R = 16;
-    auto kern = k_inner_sweep<T2, NB>;
+    auto kern = k_inner_sweep_regq<T2, NB>;
     HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
@@ -668,16 +715,302 @@ static bool inner_sweep_nb(const LayerDesc *d_layers, const int *ids, int nlayer
     return true;
 }
 
+
+// 16-byte chunks of complex values: two float2 or one double2
+template <class T2> struct Chunk16;
+template <> struct Chunk16<float2> {
+    static constexpr int n = 2;
+    __device__ static void load(const float2 *p, float2 (&o)[2]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = make_float2(v.x, v.y);
+        o[1] = make_float2(v.z, v.w);
+    }
+    __device__ static uint4 bits(const float2 (&o)[2]) {
+        return make_uint4(__float_as_uint(o[0].x), __float_as_uint(o[0].y), __float_as_uint(o[1].x),
+                          __float_as_uint(o[1].y));
+    }
+};
+template <> struct Chunk16<double2> {
+    static constexpr int n = 1;
+    __device__ static void load(const double2 *p, double2 (&o)[1]) { o[0] = *p; }
+    __device__ static uint4 bits(const double2 (&o)[1]) {
+        return make_uint4((unsigned)__double2loint(o[0].x), (unsigned)__double2hiint(o[0].x),
+                          (unsigned)__double2loint(o[0].y), (unsigned)__double2hiint(o[0].y));
+    }
+};
+
+// Staged form (the default).  CTA r of the cluster owns rows [r0, r0+nr) of
+// z_j; its slab of Q_j (nr x 2nz', contiguous in global memory) is staged in
+// shared memory by a bulk (TMA) copy issued a step ahead.  A warp owns RW rows;
+// its 32 lanes split the K dimension, so every z_{j-1} element read from shared
+// memory feeds RW rows x NBT columns of multiply-adds.  A butterfly reduce-
+// scatter over the lanes leaves one finished complex per lane (or per lane
+// pair/quad); the finished rows are pushed as 16-byte chunks to every CTA of
+// the cluster, itself included, so one transaction-count mbarrier per step
+// covers the whole z_j and no CTA-wide barrier is needed.
+template <class T2, int NBT, int RW>
+__global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict__ layers,
+                                                     const int *__restrict__ ids, const T2 *__restrict__ P,
+                                                     const T2 *__restrict__ V, const T2 *__restrict__ H, T2 *X, int B,
+                                                     int *err) {
+    namespace cg = cooperative_groups;
+    using Re = decltype(T2::x);
+    using CK = Chunk16<T2>;
+    constexpr int CPC = CK::n;           // complex values per 16-byte chunk
+    constexpr int NBP = NBT + CPC;       // padded z row: 16-byte aligned, rows fall in different banks
+    constexpr int NCH = NBT / CPC;       // chunks per row
+    constexpr int VC = RW * NBT;         // complex outputs of a warp
+    constexpr int SH = VC >= 32 ? 0 : (VC == 16 ? 1 : 2);  // lanes per output = 1 << SH
+    constexpr int G = RW * NCH;          // chunks of a warp
+    constexpr int LPC = 32 / G;          // lanes per chunk
+    constexpr int PPL = 16 / LPC;        // pushes per lane (offsets 0..15 of the cluster)
+    constexpr int QST = 2;               // Q slab stages
+    static_assert(VC == 8 || VC == 16 || VC == 32, "warp output tile");
+    static_assert(G >= 2 && G <= 32 && 32 % G == 0 && LPC <= 16, "chunk layout");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long zbar[2], qbar[QST];
+    cg::cluster_group cl = cg::this_cluster();
+    const int R = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    const int grp = blockIdx.x / R;
+    const LayerDesc ld = layers[ids[blockIdx.y]];
+    const int n2 = 2 * ld.nz, J = ld.C - 1;
+    if (J <= 0) return;  // uniform over the cluster
+    const int n0 = grp * NBT;
+    const int rs = (n2 + R - 1) / R;
+    const int r0 = min(n2, rank * rs), nr = min(n2, r0 + rs) - r0;
+    T2 *zb0 = reinterpret_cast<T2 *>(smraw);
+    T2 *zb1 = zb0 + n2 * NBP;
+    T2 *qs = zb1 + n2 * NBP;  // QST slabs of rs x n2
+    const long long slot = (long long)n2 * B;
+    const T2 *h = H + ld.inner_off * (long long)B;
+    T2 *x = X + ld.inner_off * (long long)B;
+    const T2 *Pl = P + ld.P_off, *Vl = V + ld.V_off;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int mw = (tid >> 5) * RW;  // first row of this warp within the slab
+    const bool wvalid = mw < nr;
+    const int S = 2 * (J - 1);
+    auto step_j = [&](int s) { return s < J - 1 ? s + 1 : J - 2 - (s - (J - 1)); };
+    const unsigned qbytes = (unsigned)((long long)nr * n2 * sizeof(T2));
+    auto issue_q = [&](int s) {  // one thread
+        if (s >= S || qbytes == 0) return;
+        const int b = s % QST;
+        const unsigned mb = smem_u32(&qbar[b]);
+        mbar_arrive_tx(mb, qbytes);
+        const T2 *src = (s < J - 1 ? Pl : Vl) + (long long)step_j(s) * n2 * n2 + (long long)r0 * n2;
+        bulk_g2s(smem_u32(qs + (long long)b * rs * n2), src, qbytes, mb);
+    };
+    if (tid == 0) {
+        mbar_init(smem_u32(&zbar[0]), 1);
+        mbar_init(smem_u32(&zbar[1]), 1);
+        for (int i = 0; i < QST; i++) mbar_init(smem_u32(&qbar[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        issue_q(0);
+    }
+    // z_0 = h_0 into the first buffer; x_0's rows of this CTA start as h_0
+    for (int e = tid; e < n2 * NBT; e += blockDim.x) {
+        const int k = e / NBT, n = e % NBT;
+        zb0[k * NBP + n] = (n0 + n < B) ? h[slot + (long long)k * B + n0 + n] : czero<T2>();
+    }
+    for (int e = tid; e < nr * NBT; e += blockDim.x) {
+        const int m = r0 + e / NBT, n = e % NBT;
+        if (n0 + n < B) x[slot + (long long)m * B + n0 + n] = h[slot + (long long)m * B + n0 + n];
+    }
+    // the finished output a lane holds after the reduction: row mw + r_me, column c_me
+    const int f_me = lane >> SH;
+    const int r_me = f_me / NBT, c_me = f_me % NBT;
+    const bool own_valid = mw + r_me < nr && n0 + c_me < B;
+    // the chunk a lane pushes (row gr, columns gc..gc+CPC-1) and its cluster offsets d0 + t * LPC
+    const int g_me = lane % G, d0 = lane / G;
+    const int gr = g_me / NCH, gc = CPC * (g_me % NCH);
+    const bool push_valid = wvalid && mw + gr < nr;
+    T2 bc = czero<T2>(), bn = czero<T2>();
+    auto loadb = [&](int s, T2 &b) {
+        if (s >= S) return;
+        b = czero<T2>();
+        if (own_valid)
+            b = ((s < J - 1 ? h : x) + (long long)(step_j(s) + 1) * slot + (long long)(r0 + mw + r_me) * B + n0 +
+                 c_me)[0];
+    };
+    loadb(0, bc);
+    cl.sync();  // mbarriers initialised and z_0 written in every CTA
+    const unsigned rx_bytes = (unsigned)((long long)n2 * NBT * sizeof(T2));
+    unsigned zph = 0u, qph = 0u;
+    bool dead = false;
+    int q_next = 1;  // thread 0: next step whose Q slab it issues (step 0 was issued above)
+    // Only warps that own rows take part in the steps.  Every such warp gates
+    // every CTA of the cluster through its pushes, so no CTA runs more than one
+    // step ahead of another and a phase of a barrier never receives bytes of a
+    // later phase.  Warps (and whole CTAs, when 2nz' < R * rows-per-CTA) with no
+    // rows receive nothing and wait for nothing; they go straight to the final
+    // cluster barrier.
+    for (int s = 0; s < S && wvalid; s++) {
+        const int bo = (s & 1) ^ 1;  // z_s in buffer s&1, z_{s+1} into buffer bo
+        const T2 *cur = bo ? zb0 : zb1;
+        T2 *nxt = bo ? zb1 : zb0;
+        if (tid == 0) {
+            mbar_arrive_tx(smem_u32(&zbar[bo]), rx_bytes);
+            issue_q(s + 1);  // its buffer was last read in step s-1, which every warp has left
+            q_next = s + 2;
+        }
+        loadb(s + 1, bn);
+        const int qb = s % QST;
+        mbar_wait_bounded(smem_u32(&qbar[qb]), (qph >> qb) & 1u, false, dead, err);
+        qph ^= 1u << qb;
+        if (__any_sync(0xffffffffu, dead)) break;
+        T2 acc[RW][NBT];
+#pragma unroll
+        for (int r = 0; r < RW; r++)
+#pragma unroll
+            for (int c = 0; c < NBT; c++) acc[r][c] = czero<T2>();
+        if (wvalid) {
+            const T2 *qrow = qs + (long long)qb * rs * n2 + (long long)mw * n2;
+            for (int k = lane; k < n2; k += 32) {
+                T2 q[RW];
+#pragma unroll
+                for (int r = 0; r < RW; r++) q[r] = (mw + r < nr) ? qrow[r * n2 + k] : czero<T2>();
+                const T2 *zr = cur + k * NBP;
+#pragma unroll
+                for (int ch = 0; ch < NCH; ch++) {
+                    T2 z[CPC];
+                    CK::load(zr + ch * CPC, z);
+#pragma unroll
+                    for (int i = 0; i < CPC; i++)
+#pragma unroll
+                        for (int r = 0; r < RW; r++) cmac(acc[r][ch * CPC + i], q[r], z[i]);
+                }
+            }
+        }
+        // reduce-scatter of the warp's RW x NBT complex sums over its 32 lanes
+        Re w[2 * VC];
+#pragma unroll
+        for (int r = 0; r < RW; r++)
+#pragma unroll
+            for (int c = 0; c < NBT; c++) {
+                w[2 * (r * NBT + c)] = acc[r][c].x;
+                w[2 * (r * NBT + c) + 1] = acc[r][c].y;
+            }
+#pragma unroll
+        for (int o = 16, cnt = 2 * VC; cnt > 2; o >>= 1, cnt >>= 1) {
+            const bool up = (lane & o) != 0;
+            const int hf = cnt / 2;
+#pragma unroll
+            for (int j = 0; j < hf; j++) {
+                const Re send = up ? w[j] : w[j + hf];
+                const Re keep = up ? w[j + hf] : w[j];
+                w[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < (1 << SH); o <<= 1) {
+            w[0] += __shfl_xor_sync(0xffffffffu, w[0], o);
+            w[1] += __shfl_xor_sync(0xffffffffu, w[1], o);
+        }
+        T2 y;
+        y.x = w[0] + bc.x;
+        y.y = w[1] + bc.y;
+        if (n0 + c_me >= B) y = czero<T2>();
+        T2 pk[CPC];
+#pragma unroll
+        for (int i = 0; i < CPC; i++) {
+            const int src = (gr * NBT + gc + i) << SH;
+            pk[i].x = __shfl_sync(0xffffffffu, y.x, src);
+            pk[i].y = __shfl_sync(0xffffffffu, y.y, src);
+        }
+        if (push_valid) {
+            const int row = r0 + mw + gr;
+            const unsigned a = smem_u32(nxt + row * NBP + gc);
+            const unsigned mb = smem_u32(&zbar[bo]);
+            const uint4 v = CK::bits(pk);
+            if (d0 == 0) {
+                T2 *outp = x + (long long)(step_j(s) + 1) * slot + (long long)row * B + n0 + gc;
+#pragma unroll
+                for (int i = 0; i < CPC; i++)
+                    if (n0 + gc + i < B) outp[i] = pk[i];
+            }
+#pragma unroll
+            for (int t = 0; t < PPL; t++) {
+                const int d = d0 + t * LPC;
+                if (d < R) {
+                    int pr = rank + d;
+                    if (pr >= R) pr -= R;
+                    if (pr * rs < n2)  // CTAs without rows take no part
+                        st_async16(cluster_map(a, pr), v, cluster_map(mb, pr));
+                }
+            }
+        }
+        // all of z_{s+1} (own rows included) has landed once the phase completes
+        mbar_wait_bounded(smem_u32(&zbar[bo]), (zph >> bo) & 1u, true, dead, err);
+        zph ^= 1u << bo;
+        if (__any_sync(0xffffffffu, dead)) break;
+        bc = bn;
+    }
+    // after a timeout: let this CTA's own bulk loads still in flight land (bounded)
+    if (tid == 0 && dead) {
+        for (int s = q_next - 1; s >= 0 && s > q_next - 1 - QST && s < S; s--) {
+            const int b = s % QST;
+            // the phase of buffer b that step s completes has parity (s / QST) & 1
+            mbar_wait_bounded(smem_u32(&qbar[b]), (unsigned)((s / QST) & 1), false, dead, err);
+        }
+    }
+    cl.sync();  // no CTA leaves while peers may still push into it
+    if (__syncthreads_or(dead)) __nanosleep(20000);  // pushes a timed-out peer issued may still be landing
+}
+
+template <class T2, int NBT, int RW>
+static bool inner_sweep_staged(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
+                               const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
+    constexpr int CPC = 16 / (int)sizeof(T2);
+    const int groups = (B + NBT - 1) / NBT;
+    auto kern = k_inner_sweep<T2, NBT, RW>;
+    HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    for (int R = 16; R >= 2; R /= 2) {
+        const int rs = (max_n2 + R - 1) / R;
+        const int warps = (rs + RW - 1) / RW;
+        if (warps > 8) return false;  // larger R would have been tried first
+        if (RW == 4 && rs <= 16) continue;  // the RW = 2 form serves these slabs
+        const size_t sm = (size_t)(2 * max_n2 * (NBT + CPC) + 2LL * rs * max_n2) * sizeof(T2);
+        if (sm > 220 * 1024) continue;
+        HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = R;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(32 * warps, 1, 1);
+        cfg.gridDim = dim3(R * groups, nlayer, 1);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl <= 0) {
+            cudaGetLastError();
+            continue;
+        }
+        HZ_CU(cudaLaunchKernelEx(&cfg, kern, d_layers, ids, P, V, H, X, B, err));
+        return true;
+    }
+    return false;
+}
+
 template <class T2>
 void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
                         const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl) {
     if (nlayer <= 0 || B <= 0) return;
-    bool ok;
-    if ((long long)((B + 7) / 8) * nlayer * 16 <= 608)
-        ok = inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
-    else
-        ok = inner_sweep_nb<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st) ||
-             inner_sweep_nb<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    // 8-column tiles while the clusters of all layers fit on the GPU at once, else 16
+    const bool narrow = (long long)((B + 7) / 8) * nlayer * 16 <= 608;
+    bool ok = narrow ? inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st)
+                     : inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    if (!ok) ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    if (!ok) {
+        if ((long long)((B + 7) / 8) * nlayer * 16 <= 608)
+            ok = inner_sweep_regq<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+        else
+            ok = inner_sweep_regq<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st) ||
+                 inner_sweep_regq<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    }
     if (!ok) throw HzError(HZ_ENOMEM, "inner sweep: interface blocks too large for shared memory");
     if (nl) (*nl)++;
 }

@@ -105,3 +105,22 @@ def test_gradient_twin():
         ctx.close()
         assert abs(J - J_ref) <= tol * abs(J_ref)
         assert _rel(g, g_ref) < 10 * tol
+
+
+def test_uneven_rowless_cluster_ranks_wide_tiles():
+    # Layers of 2nz' = 88..146 rows: with 16 CTAs per cluster the last CTA owns
+    # no rows.  48 sources make the layer-parallel sweeps use 16-column tiles
+    # and the single-layer sweeps 8-column tiles.  Repeated solves must agree.
+    pb = I.uneven_multifreq(n=192, n_pml=10, seed=4, part_seed=40)[1]
+    f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, 48)
+    C_pml = O.default_pml_C(pb.m)
+    box, ref = _oracle(pb, C_pml, f)
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_MIXED,
+                     pml_C=C_pml, layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
+    ctx.hz_factor()
+    us = [ctx.hz_solve(f)[0] for _ in range(3)]
+    ctx.close()
+    for u in us:
+        assert _rel(u, ref) < 1e-5
+        assert np.all(O.relative_residual(box, u, f) < 1e-8)
+    assert _rel(us[1], us[0]) < 1e-12 and _rel(us[2], us[0]) < 1e-12
