@@ -168,6 +168,26 @@ hz_status hz_gradient(hz_ctx *ctx, const double *f, int B, const double *d,
 hz_status hz_adjoint(hz_ctx *ctx, const double *u, const double *gu, int B, double *grad_m, double *grad_f,
                      hz_stats *st);
 
+/* Checkpoint of a solve (not in the paper; used to differentiate without
+ * keeping volume fields): the interface traces of a field,
+ *   tr[b][k][0][x] = u[b][row_a(k)][x],  tr[b][k][1][x] = u[b][row_b(k)][x],
+ * row_a(k) = last interior row of layer k, row_b(k) = first interior row of
+ * layer k+1 (k = 0..L-2), x over the full extended width n_x+2p.
+ *   u : [B][grid] complex; tr : [B][L-1][2][n_x+2p] complex, written.
+ * Errors: HZ_EINVAL (NULL, B < 1, L < 2), HZ_ECUDA. */
+hz_status hz_traces(hz_ctx *ctx, const double *u, int B, double *tr);
+
+/* Recompute a field from its source and its interface traces: every layer's
+ * field is its local solution with the interface forcing of Appendix C built
+ * from the traces (the reconstruction stage of Alg. matrix_free_solver, lines
+ * 10-18, with the traces given), so no GMRES runs.  With tr = hz_traces(u) of
+ * a converged u it returns u to the working precision of the operators
+ * (roundoff in FP64, ~1e-6 relative in HZ_MIXED).
+ *   f : [B][grid]; tr : [B][L-1][2][n_x+2p]; u : [B][grid], written.
+ * Errors: HZ_ESTATE (not factored), HZ_EINVAL (NULL, B < 1, L < 2, non-finite
+ * f or tr), HZ_ETIMEOUT, HZ_ECUDA. */
+hz_status hz_reconstruct(hz_ctx *ctx, const double *f, const double *tr, int B, double *u);
+
 /* ---- component entry points (each runs one step of the online path on the
  * device, used to test that step alone; inputs/outputs follow the conventions
  * above, batch outermost) ---- */

@@ -545,6 +545,50 @@ hz_status hz_residual(hz_ctx *c, const double *u, const double *f, int B, double
     });
 }
 
+hz_status hz_traces(hz_ctx *c, const double *u, int B, double *tr) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!u || !tr || B < 1) return fail(c, HZ_EINVAL, "u, tr must be non-NULL and B >= 1");
+    if (c->L < 2) return fail(c, HZ_EINVAL, "a single layer has no interface traces");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        const long long T = (long long)(c->L - 1) * 2 * c->NX * B;
+        double2 *buf = stage(c, N * B + T);
+        const double2 *ud = to_dev(c, u, N * B, buf);
+        double2 *td = c->opts.device_ptrs ? (double2 *)tr : buf + N * B;
+        hz::comp_traces(c, ud, B, td);
+        from_dev(c, tr, td, T);
+        if (c->opts.device_ptrs) HZ_CU(cudaStreamSynchronize(c->st));
+        return HZ_OK;
+    });
+}
+
+hz_status hz_reconstruct(hz_ctx *c, const double *f, const double *tr, int B, double *u) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_reconstruct before hz_factor");
+    if (!f || !tr || !u || B < 1) return fail(c, HZ_EINVAL, "f, tr, u must be non-NULL and B >= 1");
+    if (c->L < 2) return fail(c, HZ_EINVAL, "a single layer has no interface traces");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        const long long N = (long long)c->NX * c->NZ;
+        const long long T = (long long)(c->L - 1) * 2 * c->NX * B;
+        double2 *buf = stage(c, 2 * N * B + T);
+        const double2 *fd = to_dev(c, f, N * B, buf);
+        const double2 *td = c->opts.device_ptrs ? (const double2 *)tr : buf + N * B;
+        if (!c->opts.device_ptrs)
+            HZ_CU(cudaMemcpyAsync(buf + N * B, tr, sizeof(double2) * T, cudaMemcpyHostToDevice, c->st));
+        check_finite(c, (const double *)fd, 2 * N * B, "f");
+        check_finite(c, (const double *)td, 2 * T, "tr");
+        double2 *ud = c->opts.device_ptrs ? (double2 *)u : buf + N * B + T;
+        if (c->mixed())
+            hz::comp_reconstruct<float2>(c, fd, td, B, ud);
+        else
+            hz::comp_reconstruct<double2>(c, fd, td, B, ud);
+        from_dev(c, u, ud, N * B);
+        return HZ_OK;
+    });
+}
+
 hz_status hz_set_device_ptrs(hz_ctx *c, int device_ptrs) {
     if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
     c->opts.device_ptrs = device_ptrs ? 1 : 0;

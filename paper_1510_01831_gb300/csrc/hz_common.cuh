@@ -153,7 +153,13 @@ struct HzError {
 // ------------------------------------------------- kernel launchers ---
 // (defined in hz_kernels.cu; all launch on `st` and count launches in *nl)
 template <class T2>
-void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, cudaStream_t st, int *nl);
+void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt, cudaStream_t st,
+                 int *nl);
+// batched GEMM tile (complex outputs) and K step
+constexpr int GBM = 64, GBN = 32, GBK = 16;
+// split-K is used while a launch has fewer tiles than this; its workspace
+// holds at most 2x this many partial tiles
+constexpr int GEMM_SPLIT_TILES = 304;
 
 template <class T2>
 void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B,

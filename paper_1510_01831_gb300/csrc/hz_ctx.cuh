@@ -22,6 +22,7 @@ template <class T2> struct Ops {
 template <class T2> struct ProbList {
     GemmProb<T2> *d = nullptr;
     int n = 0, max_tiles = 0;
+    int kmax = 0;                 // longest K (both passes) of a problem
     double bytes = 0, flops = 0;  // algorithmic traffic and real flops of one launch
 };
 
@@ -124,6 +125,8 @@ struct hz_ctx {
     int *d_flag = nullptr;
     int *d_err = nullptr;  // device error word: 1 = a bounded wait in a kernel gave up
     int dev = 0;           // CUDA device current at hz_setup
+    void *gemm_ws = nullptr;  // split-K partial tiles of the batched GEMM (sized for double2)
+    int *gemm_cnt = nullptr;  // split-K arrival counters (zero between launches)
     // allocations
     std::map<void *, size_t> allocs;
     long long dev_bytes = 0;
@@ -146,6 +149,8 @@ template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev
 template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_dev, int mask, int B, double2 *out_dev);
 template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, int B, double2 *y_dev);
 template <class T2> void comp_residual(hz_ctx *c, const double2 *u_dev, const double2 *f_dev, int B, double *res_host);
+void comp_traces(hz_ctx *c, const double2 *u_dev, int B, double2 *tr_dev);
+template <class T2> void comp_reconstruct(hz_ctx *c, const double2 *f_dev, const double2 *tr_dev, int B, double2 *u_dev);
 template <class T2> Ops<T2> &ops(hz_ctx *c);
 template <class T2> Work<T2> &work(hz_ctx *c, int B);
 }  // namespace hz

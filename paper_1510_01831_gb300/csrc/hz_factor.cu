@@ -390,7 +390,7 @@ void factor_all(hz_ctx *c) {
                     mt = std::max(mt, ((nz + 63) / 64) * ((n2 + 31) / 32));
                 }
                 HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, st, nl);
+                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
             }
             for (int l = 0; l < L; l++) {
                 const LayerDesc &ld = c->layers[l];
@@ -424,7 +424,7 @@ void factor_all(hz_ctx *c) {
                 }
                 HZ_CU(cudaStreamSynchronize(st));  // pr is reused below
                 HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, st, nl);
+                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
                 HZ_CU(cudaStreamSynchronize(st));
             }
             if (j < C - 2) {  // V_j = W_j(:, nz:) K_{j+1}(1-rows, right part)
@@ -450,7 +450,7 @@ void factor_all(hz_ctx *c) {
                     mt = std::max(mt, ((n2 + 63) / 64) * ((n2 + 31) / 32));
                 }
                 HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, st, nl);
+                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
             }
             HZ_CU(cudaStreamSynchronize(st));  // host vectors reused next step
         }

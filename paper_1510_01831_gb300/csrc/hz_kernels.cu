@@ -11,10 +11,11 @@
 namespace hz {
 
 // ================================================================ GEMM ===
-constexpr int GBM = 64, GBN = 32, GBK = 16;
+
 
 template <class T2>
-__global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ probs) {
+__global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ probs, int S, T2 *ws, int *cnt,
+                                              int max_tiles) {
     __shared__ GemmProb<T2> P;
     extern __shared__ __align__(16) unsigned char gsm[];
     T2 (*As)[GBK][GBM + 1] = reinterpret_cast<T2 (*)[GBK][GBM + 1]>(gsm);
@@ -24,8 +25,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     __syncthreads();
     const int M = P.M, N = P.N;
     const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
-    const int tile = blockIdx.x;
+    const int tile = blockIdx.x / S, sp = blockIdx.x % S;
     if (tile >= tilesM * tilesN) return;
+    // split sp of S takes a GBK-aligned slice of the K range of both passes laid end to end
+    const int K1 = max(P.K, 0), Kt = K1 + max(P.K2, 0);
+    const int per = ((Kt + S - 1) / S + GBK - 1) / GBK * GBK;
+    const int kb = min(Kt, sp * per), ke = min(Kt, kb + per);
     const int m0 = (tile % tilesM) * GBM, n0 = (tile / tilesM) * GBN;
     T2 acc[4][2];
 #pragma unroll
@@ -40,11 +45,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     for (int pass = 0; pass < 2; pass++) {
         const T2 *A = pass ? P.A2 : P.A;
         const long long lda = pass ? P.lda2 : P.lda;
-        const int K = pass ? P.K2 : P.K;
         const int xseg = pass ? P.xseg2 : P.xseg;
         const long long ldx = pass ? P.ldx2 : P.ldx;
         const T2 *const *Xp = pass ? P.X2 : P.X;
-        if (K <= 0) continue;
+        // this split's part of the pass, in the pass's own K coordinates
+        const int off = pass ? K1 : 0, Kp = pass ? Kt - K1 : K1;
+        const int klo = max(kb - off, 0), K = min(ke - off, Kp);
+        if (K <= klo) continue;
         auto load = [&](int k0) {
 #pragma unroll
             for (int q = 0; q < 4; q++) {
@@ -62,8 +69,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
                 rx[q] = v;
             }
         };
-        load(0);
-        for (int k0 = 0; k0 < K; k0 += GBK) {
+        load(klo);
+        for (int k0 = klo; k0 < K; k0 += GBK) {
 #pragma unroll
             for (int q = 0; q < 4; q++) As[buf][a_kk][a_mm + 16 * q] = ra[q];
 #pragma unroll
@@ -86,6 +93,38 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         }
     }
     const float al = P.alpha;
+    if (S > 1) {
+        // split-K: every split stores its partial tile; the last split of the
+        // tile to finish adds the partials in split order (deterministic) and
+        // writes the output, then re-arms the tile's counter
+        const long long slot = (long long)blockIdx.y * max_tiles + tile;
+        T2 *mine = ws + (slot * S + sp) * (GBM * GBN);
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) mine[(ty + 16 * i) * GBN + tx + 16 * j] = acc[i][j];
+        __threadfence();
+        __syncthreads();
+        __shared__ int last;
+        if (tid == 0) last = atomicAdd(&cnt[slot], 1) == S - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                T2 v = czero<T2>();
+                for (int q = 0; q < S; q++) {
+                    const T2 *pq = ws + (slot * S + q) * (GBM * GBN) + (ty + 16 * i) * GBN + tx + 16 * j;
+                    const T2 w = __ldcg(pq);
+                    v.x += w.x;
+                    v.y += w.y;
+                }
+                acc[i][j] = v;
+            }
+        if (tid == 0) cnt[slot] = 0;
+    }
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const int m = m0 + ty + 16 * i;
@@ -105,21 +144,23 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
 }
 
 template <class T2>
-void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, cudaStream_t st, int *nl) {
+void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt,
+                 cudaStream_t st, int *nl) {
     if (nprob <= 0 || max_tiles <= 0) return;
-    dim3 grid(max_tiles, nprob);
+    if (split < 1 || (split > 1 && (!ws || !cnt))) throw HzError(HZ_EINVAL, "batched GEMM: bad split-K workspace");
+    dim3 grid(max_tiles * split, nprob);
     const size_t sm = sizeof(T2) * 2 * GBK * (GBM + 1 + GBN);
     static bool attr = false;
     if (!attr) {
         HZ_CU(cudaFuncSetAttribute(k_gemm<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    k_gemm<T2><<<grid, 256, sm, st>>>(d_probs);
+    k_gemm<T2><<<grid, 256, sm, st>>>(d_probs, split, ws, cnt, max_tiles);
     HZ_CU(cudaGetLastError());
     if (nl) (*nl)++;
 }
-template void launch_gemm<double2>(const GemmProb<double2> *, int, int, cudaStream_t, int *);
-template void launch_gemm<float2>(const GemmProb<float2> *, int, int, cudaStream_t, int *);
+template void launch_gemm<double2>(const GemmProb<double2> *, int, int, int, double2 *, int *, cudaStream_t, int *);
+template void launch_gemm<float2>(const GemmProb<float2> *, int, int, int, float2 *, int *, cudaStream_t, int *);
 
 // ========================================================= cell chain ===
 // Solve H^{l,c} x = g for every cell and RHS group.  H^{l,c} is block

@@ -119,6 +119,7 @@ __global__ void k_residual(const double2 *__restrict__ u, const double2 *__restr
     const long long g0 = blockIdx.x * chunk, g1 = min(N, g0 + chunk);
     double acc = 0.0;
     if (b < B) {
+#pragma unroll 4
         for (long long g = g0 + threadIdx.y; g < g1; g += blockDim.y) {
             const int iz = (int)(g / NX), ix = (int)(g % NX);
             double2 v;
@@ -349,6 +350,38 @@ __global__ void k_traces(const double2 *__restrict__ x, T2 *tr, int K, int NX, i
     }
 }
 
+// Interface traces of a field (the checkpoint of a solve): rows a = last
+// interior row of layer k and b = first interior row of layer k+1, full
+// extended width.  u: [B][N] (FP64), tr: [B][K][2][NX]
+__global__ void k_get_traces(const LayerDesc *__restrict__ layers, const double2 *__restrict__ u, double2 *tr, int K,
+                             int NX, long long N, int B, int p) {
+    const long long n = (long long)B * K * 2 * NX;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(e % NX);
+        long long q = e / NX;
+        const int ab = (int)(q % 2);
+        q /= 2;
+        const int k = (int)(q % K), b = (int)(q / K);
+        const int row = ab == 0 ? layers[k].s + p + layers[k].n - 1 : layers[k + 1].s + p;
+        tr[e] = u[(long long)b * N + (long long)row * NX + x];
+    }
+}
+
+// Given traces [B][K][2][NX] into the polarized layout [K][4][NX][B] with the
+// whole trace on the down-going components (their sum is what the
+// reconstruction uses)
+__global__ void k_put_traces(const double2 *__restrict__ tr, double2 *x, int K, int NX, int B) {
+    const long long n = (long long)K * 4 * NX * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % B);
+        long long q = e / B;
+        const int xi = (int)(q % NX);
+        q /= NX;
+        const int comp = (int)(q % 4), k = (int)(q / 4);
+        x[e] = comp < 2 ? tr[(((long long)b * K + k) * 2 + comp) * NX + xi] : make_double2(0.0, 0.0);
+    }
+}
+
 // reconstruction source of every cell: outer interface forcing on rows
 // (0,1,n,n+1) x owned columns from the traces, inner interface forcing on
 // columns (0,1,w,w+1) from the inner traces (Appendix C forcing, both levels).
@@ -439,6 +472,8 @@ __global__ void k_cast(const TA *__restrict__ a, TB *b, long long n) {
 
 // ---- FGMRES helpers (FP64) ----
 // partial[i][chunk][b] = sum over the chunk of conj(V_i) w
+// partial sums over point chunks of h[i][b] = <V_i, w> (conjugate-linear in V):
+// block (chunk, 32 RHS, vector i)
 __global__ void k_dots(const double2 *__restrict__ V, long long vstride, const double2 *__restrict__ w, long long n,
                        int B, int nchunk, double2 *part) {
     const int i = blockIdx.z;
@@ -448,8 +483,9 @@ __global__ void k_dots(const double2 *__restrict__ V, long long vstride, const d
     double2 acc = make_double2(0.0, 0.0);
     if (b < B) {
         const double2 *Vi = V + i * vstride;
+#pragma unroll 4
         for (long long x = x0 + threadIdx.y; x < x1; x += blockDim.y) {
-            double2 a = Vi[x * B + b], c = w[x * B + b];
+            const double2 a = Vi[x * B + b], c = w[x * B + b];
             acc.x += a.x * c.x + a.y * c.y;
             acc.y += a.x * c.y - a.y * c.x;
         }
@@ -464,14 +500,25 @@ __global__ void k_dots(const double2 *__restrict__ V, long long vstride, const d
     }
 }
 
-// h[i][b] (+)= sum over chunks
+// point chunks of the Arnoldi dot products (blocks = chunks x RHS groups x vectors)
+static int dots_chunks(long long n, int B) {
+    return (int)std::max<long long>(1, std::min<long long>(n / 64, std::max(64, 512 / ((B + 31) / 32))));
+}
+
+// h[i][b] (+)= sum over chunks: one warp per (i, b), lanes over chunks, fixed order
 __global__ void k_dots_final(const double2 *__restrict__ part, int nchunk, int B, int nvec, double2 *h, int accum) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nvec * B) return;
-    int i = e / B, b = e % B;
+    const int e = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x & 31;
+    if (e >= nvec * B) return;  // uniform over the warp
+    const int i = e / B, b = e % B;
+    const double2 *p = part + (long long)i * nchunk * B + b;
     double2 s = make_double2(0.0, 0.0);
-    for (int c = 0; c < nchunk; c++) s = s + part[((long long)i * nchunk + c) * B + b];
-    h[e] = accum ? h[e] + s : s;
+    for (int c = lane; c < nchunk; c += 32) s = s + p[(long long)c * B];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+    }
+    if (lane == 0) h[e] = accum ? h[e] + s : s;
 }
 
 // w -= sum_i V_i h[i]   (coefficients hc[i][b])
@@ -515,13 +562,14 @@ template <class T2> struct ListBuilder {
     hz_ctx *c;
     Ops<T2> &o;
     std::vector<GemmProb<T2>> v;
-    int max_tiles = 0;
+    int max_tiles = 0, kmax = 0;
     ListBuilder(hz_ctx *c_, Ops<T2> &o_) : c(c_), o(o_) {}
 
     double bytes = 0, flops = 0;
     void push(const GemmProb<T2> &g) {
         v.push_back(g);
-        max_tiles = std::max(max_tiles, ((g.M + 63) / 64) * ((g.N + 31) / 32));
+        max_tiles = std::max(max_tiles, ((g.M + GBM - 1) / GBM) * ((g.N + GBN - 1) / GBN));
+        kmax = std::max(kmax, std::max(g.K, 0) + std::max(g.K2, 0));
         const double es = sizeof(T2);
         const double K = (double)g.K + g.K2;
         bytes += es * ((double)g.M * K + K * g.N + (double)g.M * g.N * (g.beta ? 2 : 1));
@@ -609,6 +657,7 @@ template <class T2> struct ListBuilder {
         ProbList<T2> pl;
         pl.n = (int)v.size();
         pl.max_tiles = max_tiles;
+        pl.kmax = kmax;
         pl.bytes = bytes;
         pl.flops = flops;
         bytes = flops = 0;
@@ -617,15 +666,29 @@ template <class T2> struct ListBuilder {
             HZ_CU(cudaMemcpy(pl.d, v.data(), sizeof(GemmProb<T2>) * v.size(), cudaMemcpyHostToDevice));
         }
         v.clear();
-        max_tiles = 0;
+        max_tiles = kmax = 0;
         return pl;
     }
 };
 
+// K slices per tile: launches with fewer tiles than GEMM_SPLIT_TILES and a
+// long K are split so that the whole GPU works on them
+static int gemm_split(long long tiles, int kmax) {
+    if (tiles >= GEMM_SPLIT_TILES || kmax < 32 * GBK) return 1;
+    const long long s = (GEMM_SPLIT_TILES + tiles - 1) / tiles;
+    return (int)std::max(1LL, std::min<long long>({8, s, kmax / (16 * GBK)}));  // >= 256 of K per split
+}
+
 template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
     if (!pl.n) return;
+    const int split = gemm_split((long long)pl.n * pl.max_tiles, pl.kmax);
+    if (split > 1 && !c->gemm_ws) {
+        c->gemm_ws = c->dalloc(sizeof(double2) * 2 * GEMM_SPLIT_TILES * GBM * GBN);
+        c->gemm_cnt = (int *)c->dalloc(sizeof(int) * GEMM_SPLIT_TILES);
+        HZ_CU(cudaMemset(c->gemm_cnt, 0, sizeof(int) * GEMM_SPLIT_TILES));
+    }
     c->kt_begin(2, pl.bytes, pl.flops);
-    launch_gemm<T2>(pl.d, pl.n, pl.max_tiles, c->st, &c->nl);
+    launch_gemm<T2>(pl.d, pl.n, pl.max_tiles, split, (T2 *)c->gemm_ws, c->gemm_cnt, c->st, &c->nl);
     c->kt_end();
 }
 
@@ -881,13 +944,13 @@ template <class T2> Work<T2> &work(hz_ctx *c, int B) {
     W.w64 = (double2 *)al(ntr * B, sizeof(double2));
     W.rhs64 = (double2 *)al(ntr * B, sizeof(double2));
     W.x64 = (double2 *)al(ntr * B, sizeof(double2));
-    W.dots = (double *)al((long long)(m + 2) * 64 * B * 2, sizeof(double));
+    W.dots = (double *)al((long long)(m + 2) * dots_chunks(c->n_tr(), B) * B * 2, sizeof(double));
     W.hbuf = (double *)al((long long)(2 * m + 4) * B * 2, sizeof(double));
     HZ_CU(cudaMallocHost(&W.hhost, sizeof(double) * (2 * m + 4) * B * 2));
     W.gsrc = (double2 *)al(N * B, sizeof(double2));
     W.u = (double2 *)al(N * B, sizeof(double2));
     W.io = (double2 *)al(N * B, sizeof(double2));
-    W.rnorm = (double *)al((long long)1024 * B + 4 * B, sizeof(double));
+    W.rnorm = (double *)al((long long)4096 * B + 4 * B, sizeof(double));
     HZ_CU(cudaMallocHost(&W.rhost, sizeof(double) * 4 * B));
     build_lists(c, W);
     return W;
@@ -1005,9 +1068,10 @@ template <class T2> struct Fgmres {
         dim3 g3(nchunk, (B + 31) / 32, nvec), blk(32, 8);
         k_dots<<<g3, blk, 0, c->st>>>(V, vs, w, n, B, nchunk, (double2 *)W->dots);
         HZ_CU(cudaGetLastError());
-        k_dots_final<<<(nvec * B + 255) / 256, 256, 0, c->st>>>((double2 *)W->dots, nchunk, B, nvec, h, 0);
+        c->nl++;
+        k_dots_final<<<(nvec * B + 7) / 8, 256, 0, c->st>>>((double2 *)W->dots, nchunk, B, nvec, h, 0);
         HZ_CU(cudaGetLastError());
-        c->nl += 2;
+        c->nl++;
     }
     double2 *H() { return (double2 *)W->hbuf; }
     double2 *Hh() { return (double2 *)W->hhost; }
@@ -1022,7 +1086,7 @@ template <class T2> struct Fgmres {
         m = W->restart;
         n = c->n_tr();
         nB = n * B;
-        nchunk = (int)std::min<long long>(64, std::max<long long>(1, n / 256));
+        nchunk = dots_chunks(n, B);
         Hm.assign(B, std::vector<double2>((size_t)(m + 1) * m));
         g.assign(B, std::vector<double2>(m + 1));
         cs.assign(B, std::vector<double2>(m));
@@ -1260,7 +1324,9 @@ static double now_ms() {
 // symmetric-form source src ([N][B], FP64): Newton potentials of every layer
 // through cell solves and inner sweeps, sampled into the polarized
 // right-hand side.
-template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const double2 *src) {
+// Local solves of every cell on the symmetric-form source src ([N][B], FP64)
+// into W.vol, and the inner right-hand side of every layer (W.inner_f) from them.
+template <class T2> static void local_enqueue(hz_ctx *c, Work<T2> &W, const double2 *src) {
     cudaStream_t st = c->st;
     const int B = W.B, L = c->L, ncell = (int)c->cells.size();
     const int nb = (int)std::min<long long>(1024, (c->tot_vol * B / ncell + 255) / 256 + 1);
@@ -1273,6 +1339,16 @@ template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const dou
         HZ_CU(cudaGetLastError());
         c->nl++;
     }
+}
+
+// Stage 1 of a pass of Alg. matrix_free_solver (lines 2-7) on the
+// symmetric-form source src ([N][B], FP64): Newton potentials of every layer
+// through cell solves and inner sweeps, sampled into the polarized
+// right-hand side.
+template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const double2 *src) {
+    cudaStream_t st = c->st;
+    const int B = W.B, L = c->L, ncell = (int)c->cells.size();
+    local_enqueue<T2>(c, W, src);
     // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
     chain_layers(c, W, false, 0, L);
@@ -1307,11 +1383,14 @@ template <class T2> static void recon_enqueue(hz_ctx *c, Work<T2> &W) {
     c->nl++;
 }
 
+// point chunks of the residual (its FP64 arithmetic, not the chunking, bounds it)
+static int residual_chunks(int) { return 256; }
+
 // per-RHS ||alpha r||^2 partial sums -> host buffer (mode 0 writes r = fs - H u);
 // enqueued only: valid after the stream synchronises
 static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
                              int mode, double *part) {
-    const int nchunk = 256;
+    const int nchunk = residual_chunks(B);
     dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
     k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ, B, part,
                                      nchunk, mode);
@@ -1325,7 +1404,7 @@ static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, dou
 
 static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
                            int mode, double *part) {
-    const int nchunk = 256;
+    const int nchunk = residual_chunks(B);
     dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
     k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ, B, part,
                                      nchunk, mode);
@@ -1591,6 +1670,40 @@ template <class T2> void comp_polar(hz_ctx *c, int which, const double2 *x_dev, 
 }
 template void comp_polar<double2>(hz_ctx *, int, const double2 *, int, double2 *);
 template void comp_polar<float2>(hz_ctx *, int, const double2 *, int, double2 *);
+
+// checkpoint of a solve: the interface traces of u ([B][N] device) -> tr ([B][K][2][NX] device)
+void comp_traces(hz_ctx *c, const double2 *u_dev, int B, double2 *tr_dev) {
+    const int K = c->L - 1;
+    k_get_traces<<<grid1((long long)B * K * 2 * c->NX), 256, 0, c->st>>>(
+        c->d_layers, u_dev, tr_dev, K, c->NX, (long long)c->NX * c->NZ, B, c->p);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+}
+
+// recompute u from its source and its interface traces: local solves of f,
+// then the reconstruction stage of the solver with the traces given (the
+// Appendix C identity; no GMRES).  f, u: [B][N]; tr: [B][K][2][NX] (device)
+template <class T2> void comp_reconstruct(hz_ctx *c, const double2 *f_dev, const double2 *tr_dev, int B, double2 *u_dev) {
+    Work<T2> &W = work<T2>(c, B);
+    const long long N = (long long)c->NX * c->NZ;
+    transpose_in(c, f_dev, W.gsrc, N, B, true);
+    HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, c->st));
+    local_enqueue<T2>(c, W, W.gsrc);
+    k_put_traces<<<grid1(c->n_tr() * B), 256, 0, c->st>>>(tr_dev, W.x64, c->L - 1, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    recon_enqueue<T2>(c, W);
+    transpose_out(c, W.u, u_dev, N, B);
+    HZ_CU(cudaStreamSynchronize(c->st));
+    int e = 0;
+    HZ_CU(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
+        throw HzError(HZ_ETIMEOUT, "an inter-CTA exchange in the inner sweep timed out; results are invalid");
+    }
+}
+template void comp_reconstruct<double2>(hz_ctx *, const double2 *, const double2 *, int, double2 *);
+template void comp_reconstruct<float2>(hz_ctx *, const double2 *, const double2 *, int, double2 *);
 
 template <class T2> void comp_residual(hz_ctx *c, const double2 *u_dev, const double2 *f_dev, int B, double *res_host) {
     Work<T2> &W = work<T2>(c, B);

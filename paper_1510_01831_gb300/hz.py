@@ -26,7 +26,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
                 "HZ_ESINGULAR"]
 
 # every entry point declared in include/hz.h
-EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_cell_solve",
+EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve",
            "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
            "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
             L.hz_solve_group.argtypes = [P(vp), i, P(vp), i, P(vp), P(HzStats)]
             L.hz_gradient.argtypes = [vp, vp, i, vp, vp, i, P(d), vp, vp, P(HzStats)]
             L.hz_adjoint.argtypes = [vp, vp, vp, i, vp, vp, P(HzStats)]
+            L.hz_traces.argtypes = [vp, vp, i, vp]
+            L.hz_reconstruct.argtypes = [vp, vp, vp, i, vp]
             L.hz_cell_solve.argtypes = [vp, i, i, vp, i, vp]
             L.hz_layer_green.argtypes = [vp, i, vp, i, i, vp]
             L.hz_apply_M.argtypes = [vp, vp, i, vp]
@@ -103,7 +105,7 @@ def load() -> ctypes.CDLL:
             L.hz_destroy.restype = None
             L.hz_last_error.argtypes = [vp]
             L.hz_last_error.restype = ctypes.c_char_p
-            for name in ("hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_cell_solve", "hz_layer_green",
+            for name in ("hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve", "hz_layer_green",
                          "hz_apply_M", "hz_precond", "hz_residual"):
                 getattr(L, name).restype = ctypes.c_int
             _lib = L
@@ -244,6 +246,23 @@ class Context:
         else:
             _check(st, self._ctx)
         return grad_m, grad_f, s
+
+    def hz_traces(self, u):
+        """Interface traces [B][L-1][2][NX] of the fields u [B][NZ][NX] (a solve's checkpoint)."""
+        u = self._in(u)
+        B = u.shape[0]
+        tr = self._alloc((B, self.L - 1, 2, self.NX), like=u)
+        _check(load().hz_traces(self._ctx, _ptr(u, self.device), B, _ptr(tr, self.device)), self._ctx)
+        return tr
+
+    def hz_reconstruct(self, f, tr):
+        """Fields u [B][NZ][NX] from their sources f and interface traces tr."""
+        f, tr = self._in(f), self._in(tr)
+        B = f.shape[0]
+        u = self._alloc(tuple(f.shape), like=f)
+        _check(load().hz_reconstruct(self._ctx, _ptr(f, self.device), _ptr(tr, self.device), B,
+                                     _ptr(u, self.device)), self._ctx)
+        return u
 
     def hz_cell_solve(self, l, c, g):
         g = self._in(g)

@@ -68,3 +68,50 @@ def test_autograd_matches_finite_differences(case):
         mm_.reshape(-1)[i] -= eps
         fd = (J(mp) - J(mm_)) / (2 * eps)
         assert abs(fd - g.reshape(-1)[i]) <= 1e-5 * np.abs(g).max() + 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-5)])
+def test_traces_reconstruct_roundtrip(case, precision, tol):
+    # a field is recomputed from its source and its interface traces
+    pb, C_pml, box, fac = case
+    B = 3
+    f = I.random_sources(pb.shape_ext, pb.n_pml, B, 76)
+    prec = hz.HZ_FP64 if precision == "fp64" else hz.HZ_MIXED
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec, pml_C=C_pml)
+    ctx.hz_factor()
+    u, _ = ctx.hz_solve(f)
+    tr = ctx.hz_traces(u)
+    assert tr.shape == (B, pb.L - 1, 2, pb.n_x + 2 * pb.n_pml)
+    # the traces are rows of u: last interior row of layer k, first of layer k+1
+    rows = np.cumsum(ctx.rows)[:-1] + pb.n_pml  # first interior row of layers 1..L-1 (extended index)
+    assert np.array_equal(tr[:, :, 1, :], u[:, rows, :])
+    assert np.array_equal(tr[:, :, 0, :], u[:, rows - 1, :])
+    u2 = ctx.hz_reconstruct(f, tr)
+    # exact traces from the oracle give the oracle field
+    uo = fac.solve(f)
+    u3 = ctx.hz_reconstruct(f, np.ascontiguousarray(np.stack([uo[:, rows - 1, :], uo[:, rows, :]], axis=2)))
+    ctx.close()
+    assert _rel(u2, u) < tol
+    assert _rel(u3, uo) < tol
+
+
+def test_autograd_checkpoint_matches_stored_fields(case):
+    torch = pytest.importorskip("torch")
+    from paper_1510_01831_gb300 import torch_ops
+    pb, C_pml, box, fac = case
+    B = 3
+    f0 = torch.from_numpy(I.random_sources(pb.shape_ext, pb.n_pml, B, 77)).cuda()
+    w = torch.from_numpy(np.random.default_rng(78).random(pb.shape_ext)).cuda()
+    grads = []
+    for ck in (False, True):
+        m = torch.from_numpy(pb.m.copy()).cuda().requires_grad_(True)
+        f = f0.clone().requires_grad_(True)
+        op = torch_ops.HelmholtzOperator(m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, pml_C=C_pml,
+                                         checkpoint=ck)
+        u = op(m, f)
+        loss = (w * u.abs() ** 2).sum()
+        loss.backward()
+        grads.append((m.grad.cpu().numpy(), f.grad.cpu().numpy()))
+        op.close()
+    assert _rel(grads[1][0], grads[0][0]) < 1e-9
+    assert _rel(grads[1][1], grads[0][1]) < 1e-9
