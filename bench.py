@@ -176,7 +176,8 @@ def run_ours(args, rank, world):
         if pb.layer_rows is not None:
             kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
-                         device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8, **kw)
+                         device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
+                         tensor_cores=args.tensor_cores, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
     t_factor = time.time() - t0
@@ -344,6 +345,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tensor-cores", action="store_true", help="mixed precision: cell solves on the tensor cores")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -75,6 +75,11 @@ typedef struct {
     int device_ptrs;    /* 1: array arguments of solve/gradient/component calls are device pointers */
     void *stream;       /* cudaStream_t used by every call on the context (NULL = legacy default) */
     int time_kernels;   /* 1: time the hot kernels with CUDA events (hz_stats.kt_*) */
+    int tensor_cores;   /* HZ_MIXED only: 1 runs the cell solves (a1) on the tensor
+                           cores (tcgen05, 3xTF32 split, cells up to 128 columns
+                           wide, cell-solve error ~6e-6 against ~8e-7 on the
+                           FP32 SIMT pipes), 0 (default) keeps them on the SIMT
+                           pipes */
 } hz_opts;
 
 typedef struct {

@@ -133,6 +133,7 @@ void hz_default_opts(hz_opts *o) {
     o->refine_tol = 1e-8;
     o->max_refine = 6;
     o->pml_C = 0.0;
+    o->tensor_cores = 0;
 }
 
 hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega, double h, int n_pml, int L, int C,

@@ -86,6 +86,7 @@ struct CellDesc {
     long long E_off;     // E: (4 no) x (4 nz)
     long long S_off;     // S: (4 no) x (4 no)
     long long K_off;     // K (offline only): (2 nz) x (4 nz)
+    long long tc_off;    // split TF32 copy of the W blocks for the tensor-core cell solve (floats)
 };
 
 // One layer: its inner SIE over the C-1 cell interfaces.
@@ -161,6 +162,12 @@ constexpr int GBM = 64, GBN = 32, GBK = 16;
 // holds at most 2x this many partial tiles
 constexpr int GEMM_SPLIT_TILES = 304;
 
+// tensor-core cell solve (mixed precision, cells up to 128 columns)
+size_t cell_chain_tc_smem(int max_nx);
+long long cell_tc_floats(int nx, int nz);
+void build_wtc(const CellDesc *d_cells, int ncell, const double2 *W, float *wtc, cudaStream_t st, int *nl);
+void launch_cell_chain_tc(const CellDesc *d_cells, int ncell, const float *wtc, const float2 *cz, float2 *vol, int B,
+                          int max_nx, int *err, cudaStream_t st, int *nl);
 template <class T2>
 void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B,
                        int max_nx, cudaStream_t st, int *nl);

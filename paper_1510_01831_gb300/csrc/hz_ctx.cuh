@@ -126,6 +126,7 @@ struct hz_ctx {
     int *d_err = nullptr;  // device error word: 1 = a bounded wait in a kernel gave up
     int dev = 0;           // CUDA device current at hz_setup
     void *gemm_ws = nullptr;  // split-K partial tiles of the batched GEMM (sized for double2)
+    float *wtc = nullptr;     // split TF32 W blocks of the tensor-core cell solve (null: SIMT cell solve)
     int *gemm_cnt = nullptr;  // split-K arrival counters (zero between launches)
     // allocations
     std::map<void *, size_t> allocs;

@@ -476,6 +476,18 @@ void factor_all(hz_ctx *c) {
         auto &o = c->o32;
         o.cellW = alloc_n<float2>(c, c->tot_W);
         to_f32(cellW, o.cellW, c->tot_W, st, nl);
+        if (c->opts.tensor_cores && c->max_nx <= 128) {
+            // split TF32 copy of the cell blocks for the tensor-core cell solve
+            long long off = 0;
+            for (CellDesc &cd : c->cells) {
+                cd.tc_off = off;
+                off += cell_tc_floats(cd.nx, cd.nz);
+            }
+            HZ_CU(cudaMemcpyAsync(c->d_cells, c->cells.data(), sizeof(CellDesc) * c->cells.size(),
+                                  cudaMemcpyHostToDevice, st));
+            c->wtc = (float *)c->dalloc(sizeof(float) * std::max(off, 1LL));
+            build_wtc(c->d_cells, ncell, cellW, c->wtc, st, nl);
+        }
         o.cz = alloc_n<float2>(c, c->tot_vol);
         to_f32(czv, o.cz, c->tot_vol, st, nl);
         o.F = alloc_n<float2>(c, c->tot_F);

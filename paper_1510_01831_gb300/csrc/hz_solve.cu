@@ -1,3 +1,4 @@
+#include <type_traits>
 // Online stage: Alg. matrix_free_solver with the nested inner solver.
 //   1. Newton potentials: cell solves (local solves), inner sweeps, samples.
 //   2. FGMRES on the polarized traces (eq. integral_polarized) with P^GS
@@ -715,12 +716,24 @@ template <class T2> static void inner_chain_cost(hz_ctx *c, int l0, int nl, int 
     }
 }
 
-template <class T2> static void cell_chain(hz_ctx *c, T2 *vol, int N) {
+// cell solves of every cell (a1): tensor cores in mixed precision when the
+// split blocks were built, else the SIMT chain
+template <class T2> static void cell_chain_launch(hz_ctx *c, const CellDesc *d_cells, int ncell, T2 *vol, int N) {
     Ops<T2> &o = ops<T2>(c);
+    if constexpr (std::is_same<T2, float2>::value) {
+        if (c->wtc) {
+            launch_cell_chain_tc(d_cells, ncell, c->wtc, o.cz, vol, N, c->max_nx, c->d_err, c->st, &c->nl);
+            return;
+        }
+    }
+    launch_cell_chain<T2>(d_cells, ncell, o.cellW, o.cz, vol, N, c->max_nx, c->st, &c->nl);
+}
+
+template <class T2> static void cell_chain(hz_ctx *c, T2 *vol, int N) {
     double by = 0, fl = 0;
     if (c->opts.time_kernels) cell_chain_cost<T2>(c, N, by, fl);
     c->kt_begin(0, by, fl);
-    launch_cell_chain<T2>(c->d_cells, (int)c->cells.size(), o.cellW, o.cz, vol, N, c->max_nx, c->st, &c->nl);
+    cell_chain_launch<T2>(c, c->d_cells, (int)c->cells.size(), vol, N);
     c->kt_end();
 }
 
@@ -1608,7 +1621,7 @@ template <class T2> void comp_cell_solve(hz_ctx *c, int ci, const double2 *g_dev
     k_cast<double2, T2><<<grid1(npt * B), 256, 0, c->st>>>(W.io, W.vol + cd.vol_off * B, npt * B);
     HZ_CU(cudaGetLastError());
     c->nl++;
-    launch_cell_chain<T2>(c->d_cells + ci, 1, o.cellW, o.cz, W.vol, B, c->max_nx, c->st, &c->nl);
+    cell_chain_launch<T2>(c, c->d_cells + ci, 1, W.vol, B);
     k_cast<T2, double2><<<grid1(npt * B), 256, 0, c->st>>>(W.vol + cd.vol_off * B, W.io, npt * B);
     HZ_CU(cudaGetLastError());
     HZ_CU(cudaGetLastError());

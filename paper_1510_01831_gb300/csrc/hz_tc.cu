@@ -1,0 +1,444 @@
+// Tensor-core form of the cell chain (mixed precision, sm_103a tcgen05).
+//
+// The cell solve of Alg. inner_solver is the block-tridiagonal chain
+//   y_0 = W_0 g_0,  y_j = W_j (g_j - cz_{j-1} . y_{j-1}),
+//   x_{nz-1} = y_{nz-1},  x_j = y_j - W_j (cz_j . x_{j+1}),
+// i.e. one dense complex product D = W_j T per step, T being the nx x 32
+// panel of right-hand sides the previous step's epilogue produced.  Here every
+// product runs on the 5th-generation tensor cores as four real products
+// (Wr Tr, Wi Ti, Wr Ti, Wi Tr), each with the 3xTF32 split
+// X Y ~ Xh Yh + Xh Yl + Xl Yh (Xh = X rounded to TF32, Xl = X - Xh rounded to
+// TF32), which keeps the product accurate to about FP32 roundoff:
+//   - W_j is split offline (from the FP64 factors) into Wr_h, Wr_l, Wi_h,
+//     Wi_l, stored in the no-swizzle K-major canonical layout of the MMA
+//     operand, 16 columns per chunk, so a chunk is one contiguous bulk (TMA)
+//     copy; chunks stream through a 4-stage shared-memory ring (mbarriers
+//     "full" / "empty");
+//   - T is kept in shared memory as Tr_h, Tr_l, Ti_h, Ti_l in the same
+//     canonical layout (rows = right-hand sides, K = cell columns);
+//   - one thread issues the tcgen05.mma instructions (M = 128 rows of W,
+//     N = 32 right-hand sides, K = 8 per instruction) into FP32 accumulators
+//     in tensor memory (the Xh Yh terms and the small cross terms in separate
+//     accumulators) and commits them to mbarriers;
+//   - the 128 threads (thread = row of W, = TMEM lane) read the accumulators
+//     with tcgen05.ld, form the step's output (stored to global memory) and
+//     the next T, split it and write it back through a per-warp transpose.
+// One CTA per (cell, 32 right-hand sides); cells up to 128 columns wide.
+// Every wait is bounded (1 s): a timeout sets the error word and the whole
+// CTA leaves the steps together, drains its bulk copies and frees its tensor
+// memory before it returns.
+#include "hz_common.cuh"
+
+namespace hz {
+
+namespace {
+
+constexpr int TC_NT = 32;    // right-hand sides per CTA (MMA N)
+constexpr int TC_KC = 16;    // K columns per streamed chunk
+constexpr int TC_ST = 4;     // ring stages
+constexpr int TC_THREADS = 128;
+constexpr int TC_STAGE_BYTES = 4 * 16 * (TC_KC / 4) * 128;  // 4 arrays x 16 row groups x SBO
+
+__device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mb_init(unsigned mb, unsigned n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_expect(unsigned mb, unsigned tx) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mb_try(unsigned mb, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mb), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (1 s, or 1 ms once this thread has given up before)
+__device__ __forceinline__ bool mb_wait(unsigned mb, unsigned parity, bool &dead, int *err) {
+    const unsigned long long lim = dead ? 1000000ull : 1000000000ull;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; it++) {
+        if (mb_try(mb, parity)) return true;
+        if ((it & 63u) == 63u) {
+            const unsigned long long t = gns();
+            if (t0 == 0) {
+                t0 = t;
+            } else if (t - t0 > lim) {
+                if (!dead) atomicExch(err, 1);
+                dead = true;
+                return false;
+            }
+        }
+    }
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void *src, unsigned bytes, unsigned mb) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+__device__ __forceinline__ float tf32_rna(float x) {
+    unsigned u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+// shared-memory matrix descriptor: no swizzle, K-major canonical layout
+// (core matrices of 8 rows x 16 bytes; lbo = distance between K-adjacent core
+// matrices, sbo = distance between 8-row groups), descriptor version 1
+__device__ __forceinline__ unsigned long long sdesc(unsigned addr, unsigned lbo, unsigned sbo) {
+    return (unsigned long long)((addr & 0x3FFFFu) >> 4) | ((unsigned long long)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((unsigned long long)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void umma_tf32(unsigned dtmem, unsigned long long a, unsigned long long b, unsigned idesc,
+                                          unsigned accum) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned mb) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(unsigned taddr, float (&v)[8]) {
+    unsigned r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// byte offset of element (r, k) in a K-major canonical tile with K extent kext
+__host__ __device__ __forceinline__ unsigned canon(int r, int k, int kext) {
+    return (unsigned)((r >> 3) * (kext >> 2) * 128 + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+// Build the split W blocks of every cell (see the file header).  Per cell at
+// tc_off (floats): per block j: chunks c of KC_c = min(16, Kp - 16c) columns,
+// each [Wr_h, Wr_l, Wi_h, Wi_l][8 R8 rows x KC_c] canonical (rows >= nx and
+// columns >= nx are zero), Kp = 8 R8, R8 = ceil(nx / 8).
+__global__ void k_build_wtc(const CellDesc *__restrict__ cells, const double2 *__restrict__ W, float *wtc) {
+    const CellDesc cd = cells[blockIdx.y];
+    const int nx = cd.nx, R8 = (nx + 7) / 8, Kp = 8 * R8, rows = 8 * R8;
+    const long long per_block = 32LL * R8 * Kp;
+    const long long n = (long long)cd.nz * rows * Kp;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % Kp);
+        const int r = (int)((e / Kp) % rows);
+        const int j = (int)(e / ((long long)Kp * rows));
+        double2 w = make_double2(0.0, 0.0);
+        if (r < nx && k < nx) w = W[cd.w_off + ((long long)j * nx + r) * cd.ldw + k];
+        const float rh = tf32_rna((float)w.x), ih = tf32_rna((float)w.y);
+        const float rl = tf32_rna((float)(w.x - (double)rh)), il = tf32_rna((float)(w.y - (double)ih));
+        const int c = k / TC_KC, kc = k % TC_KC, KC = min(TC_KC, Kp - c * TC_KC);
+        float *chunk = wtc + cd.tc_off + j * per_block + (long long)c * 4 * rows * TC_KC;
+        const long long arr = (long long)rows * KC;  // floats per array in this chunk
+        const unsigned off = canon(r, kc, KC) / 4;
+        chunk[off] = rh;
+        chunk[arr + off] = rl;
+        chunk[2 * arr + off] = ih;
+        chunk[3 * arr + off] = il;
+    }
+}
+
+// Write 16 values per thread (thread = K index k = 32 warp + lane, values for
+// right-hand sides n0..n0+15) into a canonical T array [32 rows = n][Kp],
+// through a per-warp transpose so that every store is 16 bytes.
+__device__ __forceinline__ void put_T(float *Tq, int kext, int n0, const float (&v)[16], float *scr, int warp,
+                                      int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 16; i++) scr[lane * 33 + i] = v[i];
+    __syncwarp();
+    const int nl = lane & 15;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int kg = (lane >> 4) + 2 * q;  // 4-column group within the warp's 32 K values
+        float4 w;
+        w.x = scr[(4 * kg + 0) * 33 + nl];
+        w.y = scr[(4 * kg + 1) * 33 + nl];
+        w.z = scr[(4 * kg + 2) * 33 + nl];
+        w.w = scr[(4 * kg + 3) * 33 + nl];
+        const int k = 32 * warp + 4 * kg;
+        if (k < kext) *reinterpret_cast<float4 *>(reinterpret_cast<char *>(Tq) + canon(n0 + nl, k, kext)) = w;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_cell_chain_tc(const CellDesc *__restrict__ cells, const float *__restrict__ wtc, const float2 *__restrict__ cz,
+                    float2 *vol, int B, int *err) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long full[TC_ST], empty[TC_ST], done;
+    __shared__ unsigned tmem_slot;
+    const CellDesc cd = cells[blockIdx.y];
+    const int nx = cd.nx, nz = cd.nz;
+    const int n0 = blockIdx.x * TC_NT;
+    if (n0 >= B) return;  // uniform
+    const int R8 = (nx + 7) / 8, Kp = 8 * R8, rows = 8 * R8;
+    const int nchk = (Kp + TC_KC - 1) / TC_KC;
+    const int nsteps = 2 * nz - 1, total = nsteps * nchk;
+    const long long per_block = 32LL * R8 * Kp;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    unsigned char *ring = smraw;
+    float *T = reinterpret_cast<float *>(smraw + TC_ST * TC_STAGE_BYTES);  // Tr_h, Tr_l, Ti_h, Ti_l
+    const int tarr = TC_NT * Kp;                                          // floats per T array
+    float *scr = T + 4 * tarr + warp * 32 * 33;
+    const float *wc = wtc + cd.tc_off;
+    const float2 *czc = cz + cd.cz_off;
+    float2 *v = vol + cd.vol_off * (long long)B;
+    const long long rs = (long long)nx * B;
+    auto jb_of = [&](int s) { return s < nz ? s : 2 * nz - 2 - s; };
+    auto chunk_kc = [&](int c) { return min(TC_KC, Kp - c * TC_KC); };
+    auto load = [&](int q) {  // thread 0
+        const int s = q / nchk, c = q % nchk, st = q % TC_ST;
+        const unsigned bytes = (unsigned)(4 * rows * chunk_kc(c) * 4);
+        const float *src = wc + jb_of(s) * per_block + (long long)c * 4 * rows * TC_KC;
+        mb_expect(su32(&full[st]), bytes);
+        bulk_g2s(su32(ring + st * TC_STAGE_BYTES), src, bytes, su32(&full[st]));
+    };
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < TC_ST; i++) {
+            mb_init(su32(&full[i]), 1);
+            mb_init(su32(&empty[i]), 1);
+        }
+        mb_init(su32(&done), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int q = 0; q < TC_ST && q < total; q++) load(q);
+    }
+    // this thread's row of the panel (K index of T, row of W and of D)
+    const int m = tid;
+    const bool mrow = m < nx;
+    // t_0 = g_0
+    {
+        float tr[2][16], ti[2][16];
+#pragma unroll
+        for (int h = 0; h < 2; h++)
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                const int n = 16 * h + i;
+                float2 g = make_float2(0.f, 0.f);
+                if (mrow && n0 + n < B) g = v[(long long)m * B + n0 + n];
+                tr[h][i] = g.x;
+                ti[h][i] = g.y;
+            }
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            float a[16], b[16];
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                a[i] = tf32_rna(tr[h][i]);
+                b[i] = tf32_rna(tr[h][i] - a[i]);
+            }
+            put_T(T, Kp, 16 * h, a, scr, warp, lane);
+            put_T(T + tarr, Kp, 16 * h, b, scr, warp, lane);
+#pragma unroll
+            for (int i = 0; i < 16; i++) {
+                a[i] = tf32_rna(ti[h][i]);
+                b[i] = tf32_rna(ti[h][i] - a[i]);
+            }
+            put_T(T + 2 * tarr, Kp, 16 * h, a, scr, warp, lane);
+            put_T(T + 3 * tarr, Kp, 16 * h, b, scr, warp, lane);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tmem_slot;
+    // D accumulators (32 columns each): the main terms Xh Yh of P1 = Wr Tr, P2 = Wi Ti,
+    // P3 = Wr Ti, P4 = Wi Tr at columns 0, 32, 64, 96 and their cross terms Xh Yl + Xl Yh
+    // at 128, 160, 192, 224.  Keeping the small cross terms apart shortens the chain of
+    // additions into each main accumulator (the tensor core's accumulation truncates).
+    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_NT >> 3) << 17) | (8u << 24);
+    const unsigned sboT = (unsigned)(Kp / 4) * 128;
+    const unsigned tbase = su32(T);
+    bool dead = false;
+    int q_loaded = min(TC_ST, total);  // thread 0: chunks issued so far
+    int q_waited = 0;                   // thread 0: chunks whose data it has consumed
+    for (int s = 0; s < nsteps; s++) {
+        const bool fwd = s < nz;
+        const int jb = jb_of(s);
+        if (tid == 0 && !dead) {
+            for (int c = 0; c < nchk && !dead; c++) {
+                const int q = s * nchk + c, st = q % TC_ST;
+                if (!mb_wait(su32(&full[st]), (unsigned)((q / TC_ST) & 1), dead, err)) break;
+                q_waited = q + 1;
+                tc_fence_after();
+                const int KC = chunk_kc(c);
+                const unsigned sbo = (unsigned)(KC / 4) * 128;
+                const unsigned abase = su32(ring + st * TC_STAGE_BYTES);
+                const unsigned arr = (unsigned)(rows * KC * 4);  // bytes per W array in this chunk
+                // descriptors of this chunk: only the start address (bits 0-13) changes per K step
+                const unsigned long long dW = sdesc(abase, 128, sbo), dT = sdesc(tbase, 128, sboT);
+                for (int t = 0; t < KC / 8; t++) {
+                    const int k0 = c * TC_KC + 8 * t;
+                    const unsigned first = (c == 0 && t == 0) ? 0u : 1u;
+                    const unsigned long long aoff = (unsigned long long)((t * 256u) >> 4);
+                    const unsigned long long Wrh = dW + aoff + ((0u * arr) >> 4), Wrl = dW + aoff + ((1u * arr) >> 4);
+                    const unsigned long long Wih = dW + aoff + ((2u * arr) >> 4), Wil = dW + aoff + ((3u * arr) >> 4);
+                    const unsigned long long toff = (unsigned long long)((((unsigned)k0 / 4) * 128u) >> 4);
+                    const unsigned long long tq = (unsigned long long)(((unsigned)tarr * 4u) >> 4);
+                    const unsigned long long Trh = dT + toff, Trl = dT + toff + tq, Tih = dT + toff + 2 * tq,
+                                             Til = dT + toff + 3 * tq;
+                    umma_tf32(tmem + 0, Wrh, Trh, idesc, first);    // P1 main
+                    umma_tf32(tmem + 32, Wih, Tih, idesc, first);   // P2 main
+                    umma_tf32(tmem + 64, Wrh, Tih, idesc, first);   // P3 main
+                    umma_tf32(tmem + 96, Wih, Trh, idesc, first);   // P4 main
+                    umma_tf32(tmem + 128, Wrh, Trl, idesc, first);  // P1 cross
+                    umma_tf32(tmem + 128, Wrl, Trh, idesc, 1u);
+                    umma_tf32(tmem + 160, Wih, Til, idesc, first);  // P2 cross
+                    umma_tf32(tmem + 160, Wil, Tih, idesc, 1u);
+                    umma_tf32(tmem + 192, Wrh, Til, idesc, first);  // P3 cross
+                    umma_tf32(tmem + 192, Wrl, Tih, idesc, 1u);
+                    umma_tf32(tmem + 224, Wih, Trl, idesc, first);  // P4 cross
+                    umma_tf32(tmem + 224, Wil, Trh, idesc, 1u);
+                }
+                umma_commit(su32(&empty[st]));
+                // refill the stage of the previous chunk once its products are done
+                if (q >= 1 && q - 1 + TC_ST < total) {
+                    const int qp = q - 1, sp = qp % TC_ST;
+                    if (!mb_wait(su32(&empty[sp]), (unsigned)((qp / TC_ST) & 1), dead, err)) break;
+                    load(qp + TC_ST);
+                    q_loaded = qp + TC_ST + 1;
+                }
+            }
+            if (!dead) umma_commit(su32(&done));
+        }
+        // global vector for this step's epilogue: forward -> g of step s+1, backward -> y of step s
+        const int sg = fwd ? (s + 1 < nz ? s + 1 : -1) : s;
+        float2 gv[TC_NT];
+#pragma unroll
+        for (int n = 0; n < TC_NT; n++) gv[n] = make_float2(0.f, 0.f);
+        if (sg >= 0 && mrow) {
+            const float2 *src = v + jb_of(sg) * rs + (long long)m * B + n0;
+#pragma unroll
+            for (int n = 0; n < TC_NT; n++)
+                if (n0 + n < B) gv[n] = src[n];
+        }
+        const float2 c_out = (mrow && fwd && s + 1 < nz) ? czc[(long long)jb * nx + m] : make_float2(0.f, 0.f);
+        const float2 c_next = (mrow && jb > 0) ? czc[(long long)(jb - 1) * nx + m] : make_float2(0.f, 0.f);
+        if (!dead) mb_wait(su32(&done), (unsigned)(s & 1), dead, err);
+        __syncwarp();
+        const bool wdead = __any_sync(0xffffffffu, dead);
+        if (!wdead) {
+            tc_fence_after();
+            float2 *g = v + jb * rs + (long long)m * B + n0;
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                float nr[16], ni[16];
+#pragma unroll
+                for (int qq = 0; qq < 2; qq++) {
+                    float p[8][8];
+                    const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 16 * h + 8 * qq;
+#pragma unroll
+                    for (int a = 0; a < 8; a++) tmem_ld8(ta + 32 * a, p[a]);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 8; i++) {
+                        const int n = 16 * h + 8 * qq + i;
+                        float2 out = make_float2((p[0][i] + p[4][i]) - (p[1][i] + p[5][i]),
+                                                 (p[2][i] + p[6][i]) + (p[3][i] + p[7][i]));
+                        float2 tn;
+                        if (fwd) {
+                            if (s + 1 < nz)
+                                tn = gv[n] - c_out * out;  // g_{j+1} - c_j y_j
+                            else
+                                tn = c_next * out;  // first backward step: c_{nz-2} x_{nz-1}
+                        } else {
+                            out = gv[n] - out;  // x_j = y_j - W_j t
+                            tn = c_next * out;
+                        }
+                        const bool live = mrow && n0 + n < B;
+                        if (!live) {
+                            out = make_float2(0.f, 0.f);
+                            tn = make_float2(0.f, 0.f);
+                        } else {
+                            g[n] = out;
+                        }
+                        nr[8 * qq + i] = tn.x;
+                        ni[8 * qq + i] = tn.y;
+                    }
+                }
+                float a[16], b[16];
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    a[i] = tf32_rna(nr[i]);
+                    b[i] = tf32_rna(nr[i] - a[i]);
+                }
+                put_T(T, Kp, 16 * h, a, scr, warp, lane);
+                put_T(T + tarr, Kp, 16 * h, b, scr, warp, lane);
+#pragma unroll
+                for (int i = 0; i < 16; i++) {
+                    a[i] = tf32_rna(ni[i]);
+                    b[i] = tf32_rna(ni[i] - a[i]);
+                }
+                put_T(T + 2 * tarr, Kp, 16 * h, a, scr, warp, lane);
+                put_T(T + 3 * tarr, Kp, 16 * h, b, scr, warp, lane);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // T written by threads -> read by the MMAs
+        tc_fence_before();
+        if (__syncthreads_or(dead)) break;
+        tc_fence_after();
+    }
+    // after a timeout: let the bulk copies this CTA issued land before it leaves
+    if (tid == 0 && dead) {
+        for (int q = q_waited; q < q_loaded; q++)
+            mb_wait(su32(&full[q % TC_ST]), (unsigned)((q / TC_ST) & 1), dead, err);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (dead) __nanosleep(20000);  // products still in flight finish before the tensor memory is freed
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+}
+
+}  // namespace
+
+size_t cell_chain_tc_smem(int max_nx) {
+    const int Kp = 8 * ((max_nx + 7) / 8);
+    return (size_t)TC_ST * TC_STAGE_BYTES + (size_t)4 * TC_NT * Kp * 4 + (size_t)4 * 32 * 33 * 4;
+}
+
+long long cell_tc_floats(int nx, int nz) {
+    const int R8 = (nx + 7) / 8;
+    return (long long)nz * 32 * R8 * (8 * R8);
+}
+
+void build_wtc(const CellDesc *d_cells, int ncell, const double2 *W, float *wtc, cudaStream_t st, int *nl) {
+    if (ncell <= 0) return;
+    k_build_wtc<<<dim3(256, ncell), 256, 0, st>>>(d_cells, W, wtc);
+    HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+
+void launch_cell_chain_tc(const CellDesc *d_cells, int ncell, const float *wtc, const float2 *cz, float2 *vol, int B,
+                          int max_nx, int *err, cudaStream_t st, int *nl) {
+    if (ncell <= 0 || B <= 0) return;
+    if (max_nx > 128) throw HzError(HZ_EINVAL, "tensor-core cell solve: cells wider than 128 columns");
+    const size_t sm = cell_chain_tc_smem(max_nx);
+    HZ_CU(cudaFuncSetAttribute(k_cell_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid((B + TC_NT - 1) / TC_NT, ncell);
+    k_cell_chain_tc<<<grid, TC_THREADS, sm, st>>>(d_cells, wtc, cz, vol, B, err);
+    HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+
+}  // namespace hz
