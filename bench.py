@@ -45,6 +45,15 @@ WORKLOADS = {
     "multifreq512": dict(n=512, n_pml=20, B=256, ppws=(6.0, 8.0, 10.0), seed=4, part_seed=40),
 }
 METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
+# launches with the per-launch shapes of the 1024x1024 workload) divided by the
+# algorithmic bytes of the same launches; the live traffic estimate of a launch
+# is this ratio times its algorithmic bytes (traffic grows with the steps,
+# layers and cells a launch processes)
+DRAM_PER_ALGO = {
+    "inner_chain": (0.65, "profiles/k_inner_sweep_smooth256_shape1024.md"),
+    "cell_chain": (0.742, "profiles/k_cell_chain_smooth256_shape1024.md"),
+}
 UNIT = "RHS*Mdof/s"
 
 
@@ -177,7 +186,7 @@ def run_ours(args, rank, world):
             kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
-                         tensor_cores=args.tensor_cores, **kw)
+                         tensor_cores=args.tensor_cores, krylov=1 if args.krylov == "bicgstab" else 0, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
     t_factor = time.time() - t0
@@ -249,7 +258,12 @@ def run_ours(args, rank, world):
     else:
         roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(tfl / alu_peak, 4)}
-    roof.update({"kernel": names[top], "traffic": None, "peak_source": src + " (" +
+    traffic, traffic_src = None, None
+    if names[top] in DRAM_PER_ALGO and kt_n[top] > 0 and not args.tensor_cores:
+        ratio, traffic_src = DRAM_PER_ALGO[names[top]]
+        traffic = round(float(ratio * kt_b[top] / kt_n[top]))
+    roof.update({"kernel": names[top], "traffic": traffic, "traffic_source": traffic_src,
+                 "peak_source": src + " (" +
                  ("FP32 SIMT from 152 SMs x 128 lanes x max clock" if roof["bound"] == "alu" else "copy GB/s") + ")",
                  "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
                  "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
@@ -268,7 +282,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "c64+f64" if prec == hz.HZ_MIXED else "c128", "data": "synthetic",
         "config": {"workload": f"{args.workload}: " + describe(wl, pbs, B, args.precision),
                    "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
-                   "frequencies": len(pbs),
+                   "frequencies": len(pbs), "krylov": args.krylov,
                    "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
         "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
         "solve": solve[0] if len(solve) == 1 else solve,
@@ -346,6 +360,7 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tensor-cores", action="store_true", help="mixed precision: cell solves on the tensor cores")
+    ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -51,6 +51,7 @@ typedef enum {
 
 enum { HZ_FP64 = 0, HZ_MIXED = 1 };            /* hz_opts.precision */
 enum { HZ_PGS = 0, HZ_PJAC = 1, HZ_PNONE = 2 }; /* hz_opts.precond */
+enum { HZ_GMRES = 0, HZ_BICGSTAB = 1 };         /* hz_opts.krylov */
 
 typedef struct {
     int precision;      /* HZ_FP64: every online operator in FP64.
@@ -75,6 +76,10 @@ typedef struct {
     int device_ptrs;    /* 1: array arguments of solve/gradient/component calls are device pointers */
     void *stream;       /* cudaStream_t used by every call on the context (NULL = legacy default) */
     int time_kernels;   /* 1: time the hot kernels with CUDA events (hz_stats.kt_*) */
+    int krylov;         /* outer Krylov method on the polarized traces: HZ_GMRES
+                           (flexible GMRES, default) or HZ_BICGSTAB (Bi-CGstab,
+                           right preconditioned, two preconditioned operator
+                           applications per iteration; §5) */
     int tensor_cores;   /* HZ_MIXED only: 1 runs the cell solves (a1) on the tensor
                            cores (tcgen05, 3xTF32 split, cells up to 128 columns
                            wide, cell-solve error ~6e-6 against ~8e-7 on the

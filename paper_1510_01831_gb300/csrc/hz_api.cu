@@ -160,6 +160,10 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
         delete c;
         return fail(nullptr, HZ_EINVAL, "precond must be HZ_PGS, HZ_PJAC or HZ_PNONE");
     }
+    if (c->opts.krylov != HZ_GMRES && c->opts.krylov != HZ_BICGSTAB) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "krylov must be HZ_GMRES or HZ_BICGSTAB");
+    }
     c->n_x = n_x;
     c->n_z = n_z;
     c->p = n_pml;
@@ -268,6 +272,8 @@ hz_status hz_solve_group(hz_ctx **cs, int G, const double *const *f, int B, doub
     for (int i = 0; i < G; i++) {
         if (!cs[i]->factored) return fail(c0, HZ_ESTATE, "hz_solve_group before hz_factor on every member");
         if (cs[i]->mixed() != c0->mixed()) return fail(c0, HZ_EINVAL, "group members must share the precision");
+        if (cs[i]->opts.krylov != c0->opts.krylov)
+            return fail(c0, HZ_EINVAL, "group members must share the Krylov method");
         if (cs[i]->dev != dev0) return fail(c0, HZ_EINVAL, "group members must share the device");
         if (!f[i] || !u[i]) return fail(c0, HZ_EINVAL, "f[i], u[i] must be non-NULL");
         for (int j = 0; j < i; j++)

@@ -558,6 +558,22 @@ __global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__
         r[e] = a[e] - w[e];
 }
 
+// Bi-CGstab vector updates with per-RHS complex coefficients
+// p = r + beta[b] (p - omega[b] v)
+__global__ void k_bicg_p(double2 *p, const double2 *__restrict__ r, const double2 *__restrict__ v,
+                         const double2 *__restrict__ beta, const double2 *__restrict__ omega, long long n, int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
+        const int b = (int)(e % B);
+        p[e] = r[e] + beta[b] * (p[e] - omega[b] * v[e]);
+    }
+}
+// out = a + coef[b] x
+__global__ void k_zaxpy(double2 *out, const double2 *__restrict__ a, const double2 *__restrict__ x,
+                        const double2 *__restrict__ coef, long long n, int B) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x)
+        out[e] = a[e] + coef[e % B] * x[e];
+}
+
 // ------------------------------------------------- problem-list build ---
 template <class T2> struct ListBuilder {
     hz_ctx *c;
@@ -924,7 +940,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
 
 template <class T2> Work<T2> &work(hz_ctx *c, int B) {
     auto &slot = work_slot<T2>(c);
-    const int m = std::max(1, c->opts.restart);
+    // FGMRES keeps restart+1 basis vectors; Bi-CGstab uses 6 of them and 14 B host slots
+    const int m = std::max(c->opts.krylov == HZ_BICGSTAB ? 6 : 1, c->opts.restart);
     if (slot && slot->B == B && slot->restart == m) return *slot;
     if (slot) {
         free_work(c, *slot);
@@ -1285,6 +1302,214 @@ template <class T2> struct Fgmres {
     }
 };
 
+static void sync_all(const std::vector<hz_ctx *> &cs);
+// Bi-CGstab on the polarized system with right preconditioning (the paper's
+// second Krylov method, §5): M P y = b, x = P y.  Per iteration two
+// preconditioner and two operator applications; per-RHS scalars in FP64 on
+// the host, three synchronisations per iteration (shared by a group).
+// Vectors (FP64) live in the Krylov basis buffer: V0 = r^, V1 = r, V2 = p,
+// V3 = v, V4 = s, V5 = t; P p and P s in the working precision in Z0, Z1.
+template <class T2> struct Bicgstab {
+    hz_ctx *c = nullptr;
+    Work<T2> *W = nullptr;
+    double tol = 0;
+    int maxit = 0, kind = 0, B = 0, nchunk = 1, total = 0;
+    long long n = 0, nB = 0;
+    std::vector<double> bnorm, res;
+    std::vector<double2> rho, alpha, omega;
+    std::vector<int> act;
+    bool finished = false;
+
+    double2 *vec(int i) { return W->V + (long long)i * nB; }
+    T2 *zv(int i) { return W->Z + (long long)i * nB; }
+    double2 *H() { return (double2 *)W->hbuf; }
+    double2 *Hh() { return (double2 *)W->hhost; }
+    double2 *coef_d(int i) { return (double2 *)W->dots + (long long)i * B; }  // small coefficient arrays
+    void dot(const double2 *a, const double2 *b, double2 *h) {
+        dim3 g3(nchunk, (B + 31) / 32, 1), blk(32, 8);
+        k_dots<<<g3, blk, 0, c->st>>>(a, 0, b, n, B, nchunk, (double2 *)W->dots + 8LL * B);
+        HZ_CU(cudaGetLastError());
+        k_dots_final<<<(B + 7) / 8, 256, 0, c->st>>>((double2 *)W->dots + 8LL * B, nchunk, B, 1, h, 0);
+        HZ_CU(cudaGetLastError());
+        c->nl += 2;
+    }
+    void precond_to(const double2 *x, T2 *z) {  // z = P x
+        k_cast<double2, T2><<<grid1(nB), 256, 0, c->st>>>(x, W->pb, nB);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        if (kind != HZ_PNONE) precond_inplace(c, *W, kind == HZ_PJAC ? 1 : 0);
+        HZ_CU(cudaMemcpyAsync(z, W->pb, sizeof(T2) * nB, cudaMemcpyDeviceToDevice, c->st));
+    }
+    // coefficient array -> device slot, staged in pinned memory beyond the
+    // reduction results (each slot has its own staging, reused only after a sync)
+    void upload(const std::vector<double2> &v, int slot) {
+        double2 *hst = Hh() + 8LL * B + (long long)slot * B;
+        std::copy(v.begin(), v.end(), hst);
+        HZ_CU(cudaMemcpyAsync(coef_d(slot), hst, sizeof(double2) * B, cudaMemcpyHostToDevice, c->st));
+    }
+
+    void init(hz_ctx *c_, Work<T2> &W_, double tol_, int maxit_, int kind_) {
+        c = c_;
+        W = &W_;
+        tol = tol_;
+        maxit = maxit_;
+        kind = kind_;
+        B = W->B;
+        n = c->n_tr();
+        nB = n * B;
+        nchunk = dots_chunks(n, B);
+        bnorm.assign(B, 0.0);
+        res.assign(B, 1.0);
+        rho.assign(B, make_double2(1, 0));
+        alpha.assign(B, make_double2(1, 0));
+        omega.assign(B, make_double2(1, 0));
+        act.assign(B, 1);
+        total = 0;
+        finished = false;
+        cudaStream_t st = c->st;
+        HZ_CU(cudaMemsetAsync(W->x64, 0, sizeof(double2) * nB, st));
+        HZ_CU(cudaMemcpyAsync(vec(0), W->rhs64, sizeof(double2) * nB, cudaMemcpyDeviceToDevice, st));  // r^ = b
+        HZ_CU(cudaMemcpyAsync(vec(1), W->rhs64, sizeof(double2) * nB, cudaMemcpyDeviceToDevice, st));  // r = b
+        HZ_CU(cudaMemsetAsync(vec(2), 0, sizeof(double2) * nB, st));                                   // p = 0
+        HZ_CU(cudaMemsetAsync(vec(3), 0, sizeof(double2) * nB, st));                                   // v = 0
+        dot(vec(1), vec(1), H());  // ||b||^2 = <r^, r>
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * B, cudaMemcpyDeviceToHost, st));
+    }
+    void init_host() {
+        bool any = false;
+        for (int b = 0; b < B; b++) {
+            bnorm[b] = std::sqrt(std::max(Hh()[b].x, 0.0));
+            act[b] = bnorm[b] > 0;
+            res[b] = act[b] ? 1.0 : 0.0;
+            rho[b] = Hh()[b];  // <r^, r> with r^ = r = b
+            any = any || act[b];
+        }
+        finished = !any;
+    }
+    // A: p = r + beta (p - omega v), v = M P p, <r^, v>
+    void a_enqueue() {
+        std::vector<double2> beta(B, make_double2(0, 0)), om(B, make_double2(0, 0));
+        for (int b = 0; b < B; b++)
+            if (act[b]) {
+                beta[b] = total == 0 ? make_double2(0, 0) : cdiv(rho[b] * alpha[b], rho_prev[b] * omega[b]);
+                om[b] = omega[b];
+            }
+        upload(beta, 0);
+        upload(om, 1);
+        k_bicg_p<<<grid1(nB), 256, 0, c->st>>>(vec(2), vec(1), vec(3), coef_d(0), coef_d(1), n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        precond_to(vec(2), zv(0));
+        apply_M(c, *W, zv(0), vec(3));
+        dot(vec(0), vec(3), H());
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * B, cudaMemcpyDeviceToHost, c->st));
+    }
+    std::vector<double2> rho_prev = std::vector<double2>();
+    void a_host() {
+        for (int b = 0; b < B; b++) {
+            if (!act[b]) {
+                alpha[b] = make_double2(0, 0);
+                continue;
+            }
+            const double2 rv = Hh()[b];
+            if (std::hypot(rv.x, rv.y) == 0) {  // breakdown: keep the current iterate
+                act[b] = 0;
+                alpha[b] = make_double2(0, 0);
+                continue;
+            }
+            alpha[b] = cdiv(rho[b], rv);
+        }
+    }
+    // B: s = r - alpha v, t = M P s, <t, s>, <t, t>
+    void b_enqueue() {
+        std::vector<double2> na(B);
+        for (int b = 0; b < B; b++) na[b] = make_double2(-alpha[b].x, -alpha[b].y);
+        upload(na, 2);
+        k_zaxpy<<<grid1(nB), 256, 0, c->st>>>(vec(4), vec(1), vec(3), coef_d(2), n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        precond_to(vec(4), zv(1));
+        apply_M(c, *W, zv(1), vec(5));
+        dot(vec(5), vec(4), H());
+        dot(vec(5), vec(5), H() + B);
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * 2 * B, cudaMemcpyDeviceToHost, c->st));
+    }
+    void b_host() {
+        for (int b = 0; b < B; b++) {
+            if (!act[b]) {
+                omega[b] = make_double2(0, 0);
+                continue;
+            }
+            const double tt = Hh()[B + b].x;
+            omega[b] = tt > 0 ? make_double2(Hh()[b].x / tt, Hh()[b].y / tt) : make_double2(0, 0);
+        }
+    }
+    // C: x += alpha P p + omega P s, r = s - omega t, <r^, r>, <r, r>
+    void c_enqueue() {
+        std::vector<double2> al(B), om(B), no(B);
+        for (int b = 0; b < B; b++) {
+            al[b] = act[b] ? alpha[b] : make_double2(0, 0);
+            om[b] = act[b] ? omega[b] : make_double2(0, 0);
+            no[b] = act[b] ? make_double2(-omega[b].x, -omega[b].y) : make_double2(0, 0);
+        }
+        upload(al, 3);  // slots 3, 4: coefficients of P p (Z0) and P s (Z1)
+        upload(om, 4);
+        upload(no, 5);
+        k_update_x<T2><<<grid1(nB), 256, 0, c->st>>>(W->Z, nB, coef_d(3), 2, W->x64, n, B);
+        HZ_CU(cudaGetLastError());
+        k_zaxpy<<<grid1(nB), 256, 0, c->st>>>(vec(1), vec(4), vec(5), coef_d(5), n, B);
+        HZ_CU(cudaGetLastError());
+        c->nl += 2;
+        dot(vec(0), vec(1), H());
+        dot(vec(1), vec(1), H() + B);
+        HZ_CU(cudaMemcpyAsync(Hh(), H(), sizeof(double2) * 2 * B, cudaMemcpyDeviceToHost, c->st));
+    }
+    void c_host() {
+        total++;
+        bool any = false;
+        rho_prev = rho;
+        for (int b = 0; b < B; b++) {
+            if (!act[b]) continue;
+            res[b] = std::sqrt(std::max(Hh()[B + b].x, 0.0)) / bnorm[b];
+            rho[b] = Hh()[b];
+            if (res[b] <= tol || std::hypot(rho[b].x, rho[b].y) == 0 ||
+                std::hypot(omega[b].x, omega[b].y) == 0)
+                act[b] = 0;
+            any = any || act[b];
+        }
+        finished = !any || total >= maxit;
+    }
+    GmresOut out() const {
+        GmresOut o;
+        o.iters = total;
+        for (int b = 0; b < B; b++) o.resid = std::max(o.resid, res[b]);
+        return o;
+    }
+};
+
+// Lockstep Bi-CGstab over several contexts
+template <class T2> static void bicgstab_group(std::vector<Bicgstab<T2> *> &gs) {
+    std::vector<hz_ctx *> cs;
+    for (auto *g : gs) cs.push_back(g->c);
+    sync_all(cs);
+    for (auto *g : gs) g->init_host();
+    while (true) {
+        std::vector<Bicgstab<T2> *> live;
+        for (auto *g : gs)
+            if (!g->finished) live.push_back(g);
+        if (live.empty()) break;
+        for (auto *g : live) g->a_enqueue();
+        sync_all(cs);
+        for (auto *g : live) g->a_host();
+        for (auto *g : live) g->b_enqueue();
+        sync_all(cs);
+        for (auto *g : live) g->b_host();
+        for (auto *g : live) g->c_enqueue();
+        sync_all(cs);
+        for (auto *g : live) g->c_host();
+    }
+}
+
 static void sync_all(const std::vector<hz_ctx *> &cs) {
     for (hz_ctx *c : cs) HZ_CU(cudaStreamSynchronize(c->st));
 }
@@ -1513,18 +1738,31 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
         for (int i : idx) newton_enqueue<T2>(cs[i], *Ws[i], src[i]);
         sync_all(cl);
         double tb = now_ms();
-        std::vector<Fgmres<T2>> gm(idx.size());
-        std::vector<Fgmres<T2> *> gp;
+        const bool bicg = cs[0]->opts.krylov == HZ_BICGSTAB;
+        std::vector<Fgmres<T2>> gm(bicg ? 0 : idx.size());
+        std::vector<Bicgstab<T2>> bm(bicg ? idx.size() : 0);
+        std::vector<double> gtol(idx.size());
         for (size_t q = 0; q < idx.size(); q++) {
             hz_ctx *c = cs[idx[q]];
             const double tol = c->opts.tol, rtol = c->opts.refine_tol;
             double ptol = tol;
             // a pass on the residual only has to shrink it to the target, with a 10x margin
             if (pass > 0 && rtol > 0) ptol = std::min(0.1, std::max(tol, 0.1 * rtol / std::max(prev[idx[q]], 1e-300)));
-            gm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
-            gp.push_back(&gm[q]);
+            gtol[q] = ptol;
+            if (bicg)
+                bm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
+            else
+                gm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
         }
-        fgmres_group(gp);
+        if (bicg) {
+            std::vector<Bicgstab<T2> *> bp;
+            for (auto &g : bm) bp.push_back(&g);
+            bicgstab_group(bp);
+        } else {
+            std::vector<Fgmres<T2> *> gp;
+            for (auto &g : gm) gp.push_back(&g);
+            fgmres_group(gp);
+        }
         double tc = now_ms();
         for (int i : idx) recon_enqueue<T2>(cs[i], *Ws[i]);
         sync_all(cl);
@@ -1543,7 +1781,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
             tm[i].gmres += tc - tb;
             tm[i].recon += td - tc;
             tm[i].resid += te - td;
-            GmresOut go = gm[q].out();
+            GmresOut go = bicg ? bm[q].out() : gm[q].out();
             stats[i].iterations += go.iters;
             stats[i].gmres_resid = go.resid;
             stats[i].refinements = pass + 1;
@@ -1553,7 +1791,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
                 worst[i] = std::max(worst[i], rn[i][b]);
             }
             const double rtol = c->opts.refine_tol;
-            if (go.resid > gm[q].tol && !c->mixed()) status[i] = HZ_ENOTCONV;
+            if (go.resid > gtol[q] && !c->mixed()) status[i] = HZ_ENOTCONV;
             prev[i] = worst[i];
             if (rtol <= 0 || worst[i] <= rtol) {
                 live[i] = 0;

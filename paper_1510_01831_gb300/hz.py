@@ -22,6 +22,7 @@ from . import build as _build
 HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ESTATE, HZ_ENOTCONV, HZ_ETIMEOUT, HZ_ESINGULAR = range(8)
 HZ_FP64, HZ_MIXED = 0, 1
 HZ_PGS, HZ_PJAC, HZ_PNONE = 0, 1, 2
+HZ_GMRES, HZ_BICGSTAB = 0, 1
 STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_ENOTCONV", "HZ_ETIMEOUT",
                 "HZ_ESINGULAR"]
 
@@ -44,7 +45,7 @@ class HzOpts(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("pml_C", ctypes.c_double),
                 ("layer_rows", ctypes.POINTER(ctypes.c_int)), ("cell_cols", ctypes.POINTER(ctypes.c_int)),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
-                ("tensor_cores", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):
@@ -141,7 +142,7 @@ class Context:
 
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
-                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=False):
+                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=False, krylov=0):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -158,6 +159,7 @@ class Context:
         o.stream = ctypes.c_void_p(stream) if stream else None
         o.time_kernels = 1 if time_kernels else 0
         o.tensor_cores = 1 if tensor_cores else 0
+        o.krylov = int(krylov)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")

@@ -97,3 +97,13 @@ def test_null_context_calls_fail_cleanly():
     hs = (ctypes.c_void_p * G)(None, None)
     assert lib.hz_solve_group(hs, G, None, 1, None, None) == hz.HZ_EINVAL
     assert lib.hz_solve_group(hs, 0, None, 1, None, None) == hz.HZ_EINVAL
+
+
+def test_setup_rejects_unknown_krylov():
+    lib = hz.load()
+    m = np.ones((12, 12))
+    o = hz.hz_default_opts()
+    o.krylov = 7
+    h_ = ctypes.c_void_p()
+    assert lib.hz_setup(ctypes.byref(h_), m.ctypes.data, 8, 8, 10.0, 0.1, 2, 2, 2, ctypes.byref(o)) == hz.HZ_EINVAL
+    assert b"krylov" in lib.hz_last_error(None)

@@ -230,3 +230,47 @@ def test_gradient_matches_oracle():
     ctx.close()
     assert abs(J - J_ref) <= 1e-8 * abs(J_ref)
     assert _rel(g, g_ref) < 1e-7
+
+
+# ------------------------------------------------------ Bi-CGstab (§5) ---
+@pytest.mark.parametrize("precision,tol", [(hz.HZ_FP64, 1e-8), (hz.HZ_MIXED, 1e-5)])
+def test_bicgstab_solve(precision, tol):
+    """The paper's second Krylov method: same solution as the oracle, and with
+    P^GS fewer iterations than GMRES (each does two preconditioned applications)."""
+    pb = _problem()
+    C_pml = O.default_pml_C(pb.m)
+    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 4, 141)
+    ref = box.factor().solve(f)
+    its = {}
+    for kr in (hz.HZ_GMRES, hz.HZ_BICGSTAB):
+        ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=precision,
+                         pml_C=C_pml, krylov=kr)
+        ctx.hz_factor()
+        u, st = ctx.hz_solve(f)
+        ctx.close()
+        assert _rel(u, ref) < tol
+        assert st.resid < 1e-8
+        its[kr] = st.iterations
+    assert 0 < its[hz.HZ_BICGSTAB] < its[hz.HZ_GMRES]
+
+
+def test_bicgstab_group_and_mixed_methods_rejected():
+    pb = _problem()
+    C_pml = O.default_pml_C(pb.m)
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 2, 142)
+    ref = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml).factor().solve(f)
+    a = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_MIXED, pml_C=C_pml,
+                   krylov=hz.HZ_BICGSTAB)
+    b = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_MIXED, pml_C=C_pml,
+                   krylov=hz.HZ_BICGSTAB)
+    g = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_MIXED, pml_C=C_pml)
+    for ctx in (a, b, g):
+        ctx.hz_factor()
+    us, sts = hz.hz_solve_group([a, b], [f, f])
+    for u in us:
+        assert _rel(u, ref) < 1e-5
+    with pytest.raises(hz.HzError):
+        hz.hz_solve_group([a, g], [f, f])
+    for ctx in (a, b, g):
+        ctx.close()
