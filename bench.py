@@ -186,7 +186,8 @@ def run_ours(args, rank, world):
             kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
-                         tensor_cores=args.tensor_cores, krylov=1 if args.krylov == "bicgstab" else 0, **kw)
+                         tensor_cores=args.tensor_cores, krylov=1 if args.krylov == "bicgstab" else 0,
+                         autotune=args.autotune, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
     t_factor = time.time() - t0
@@ -282,7 +283,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None, "dtype": "c64+f64" if prec == hz.HZ_MIXED else "c128", "data": "synthetic",
         "config": {"workload": f"{args.workload}: " + describe(wl, pbs, B, args.precision),
                    "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
-                   "frequencies": len(pbs), "krylov": args.krylov,
+                   "frequencies": len(pbs), "krylov": args.krylov, "autotune": args.autotune,
                    "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
         "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
         "solve": solve[0] if len(solve) == 1 else solve,
@@ -361,6 +362,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tensor-cores", action="store_true", help="mixed precision: cell solves on the tensor cores")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
+    ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -80,6 +80,11 @@ typedef struct {
                            (flexible GMRES, default) or HZ_BICGSTAB (Bi-CGstab,
                            right preconditioned, two preconditioned operator
                            applications per iteration; §5) */
+    int autotune;       /* 1: time the launch configurations of the inner sweep at
+                           the first use of each launch shape and keep the
+                           fastest (environment HZ_TUNE_CACHE: JSON file that
+                           keeps the choices across processes); 0 (default): fixed
+                           rule */
     int tensor_cores;   /* HZ_MIXED only: 1 runs the cell solves (a1) on the tensor
                            cores (tcgen05, 3xTF32 split, cells up to 128 columns
                            wide, cell-solve error ~6e-6 against ~8e-7 on the

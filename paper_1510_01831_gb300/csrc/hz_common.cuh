@@ -174,7 +174,8 @@ void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2
 
 template <class T2>
 void launch_inner_sweep(const LayerDesc *d_layers, const int *d_layer_ids, int nlayer, const T2 *P, const T2 *V,
-                        const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl);
+                        const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl,
+                        bool tune = false);
 
 // offline (FP64)
 void launch_cell_coeffs(const CellDesc *d_cells, int ncell, const double *m, int NX, double omega, double h,

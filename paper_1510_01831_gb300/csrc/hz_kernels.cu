@@ -5,6 +5,13 @@
 //     compressed-block LU sweeps of Section 4.2.2
 //   * pivoted Gauss-Jordan inversion (offline, FP64)
 #include <cooperative_groups.h>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
 
 #include "hz_common.cuh"
 
@@ -1000,16 +1007,17 @@ __global__ void __launch_bounds__(256) k_inner_sweep(const LayerDesc *__restrict
 
 template <class T2, int NBT, int RW>
 static bool inner_sweep_staged(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
-                               const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
+                               const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int Rfix = 0) {
     constexpr int CPC = 16 / (int)sizeof(T2);
     const int groups = (B + NBT - 1) / NBT;
     auto kern = k_inner_sweep<T2, NBT, RW>;
     HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    for (int R = 16; R >= 2; R /= 2) {
+    for (int R = Rfix ? Rfix : 16; R >= 2; R /= 2) {
+        if (Rfix && R != Rfix) break;
         const int rs = (max_n2 + R - 1) / R;
         const int warps = (rs + RW - 1) / RW;
         if (warps > 8) return false;  // larger R would have been tried first
-        if (RW == 4 && rs <= 16) continue;  // the RW = 2 form serves these slabs
+        if (!Rfix && RW == 4 && rs <= 16) continue;  // the RW = 2 form serves these slabs
         const size_t sm = (size_t)(2 * max_n2 * (NBT + CPC) + 2LL * rs * max_n2) * sizeof(T2);
         if (sm > 220 * 1024) continue;
         HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
@@ -1036,17 +1044,149 @@ static bool inner_sweep_staged(const LayerDesc *d_layers, const int *ids, int nl
     return false;
 }
 
+// ---- launch-shape tuner of the staged sweep ----
+// The candidates differ in right-hand sides per cluster (NBT), rows per warp
+// (RW) and cluster size (R).  With tuning on, the first launch of each shape
+// (precision, layers in flight, right-hand sides, largest 2nz') times every
+// feasible candidate on the real data (the sweep is idempotent: x depends only
+// on h, P and V) and keeps the fastest for the process; HZ_TUNE_CACHE names a
+// JSON file that carries the choices across processes.
+struct SweepCand {
+    int nbt, rw, R;
+};
+static const SweepCand kSweepCands[] = {{8, 2, 16}, {16, 2, 16}, {8, 4, 16}, {8, 2, 8}, {16, 2, 8}, {8, 4, 8}};
+constexpr int kNumSweepCands = (int)(sizeof(kSweepCands) / sizeof(kSweepCands[0]));
+
+template <class T2>
+static bool sweep_cand(int i, const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
+                       const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
+    const SweepCand &k = kSweepCands[i];
+    if (k.nbt == 8 && k.rw == 2)
+        return inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 16 && k.rw == 2)
+        return inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 8 && k.rw == 4)
+        return inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    return false;
+}
+
+struct TuneTable {
+    std::mutex mu;
+    std::map<std::string, int> best;
+    bool loaded = false;
+    static std::string path() {
+        const char *p = std::getenv("HZ_TUNE_CACHE");
+        return p ? std::string(p) : std::string();
+    }
+    void load_locked() {  // {"key": value, ...}; anything unreadable is ignored
+        loaded = true;
+        const std::string p = path();
+        if (p.empty()) return;
+        std::ifstream f(p);
+        if (!f) return;
+        std::stringstream ss;
+        ss << f.rdbuf();
+        const std::string t = ss.str();
+        size_t i = 0;
+        while ((i = t.find('"', i)) != std::string::npos) {
+            const size_t j = t.find('"', i + 1);
+            if (j == std::string::npos) break;
+            const std::string key = t.substr(i + 1, j - i - 1);
+            const size_t c = t.find(':', j);
+            if (c == std::string::npos) break;
+            best[key] = std::atoi(t.c_str() + c + 1);
+            i = t.find_first_of(",}", c);
+            if (i == std::string::npos) break;
+        }
+    }
+    void save_locked() {
+        const std::string p = path();
+        if (p.empty()) return;
+        std::ofstream f(p);
+        if (!f) return;
+        f << "{";
+        bool first = true;
+        for (auto &kv : best) {
+            f << (first ? "" : ",") << "\n  \"" << kv.first << "\": " << kv.second;
+            first = false;
+        }
+        f << "\n}\n";
+    }
+};
+static TuneTable &tune_table() {
+    static TuneTable t;
+    return t;
+}
+
+template <class T2>
+static int tune_sweep(const std::string &key, const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P,
+                      const T2 *V, const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st) {
+    cudaEvent_t e0, e1;
+    HZ_CU(cudaEventCreate(&e0));
+    HZ_CU(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.f;
+    for (int i = 0; i < kNumSweepCands; i++) {
+        float ms = 1e30f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; rep++) {
+            HZ_CU(cudaEventRecord(e0, st));
+            try {
+                ok = sweep_cand<T2>(i, d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+            } catch (const CudaError &) {
+                cudaGetLastError();
+                ok = false;
+            }
+            HZ_CU(cudaEventRecord(e1, st));
+            HZ_CU(cudaEventSynchronize(e1));
+            float t = 0.f;
+            HZ_CU(cudaEventElapsedTime(&t, e0, e1));
+            if (ok) ms = std::min(ms, t);
+        }
+        if (ok && (best < 0 || ms < best_ms)) {
+            best = i;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TuneTable &tt = tune_table();
+    std::lock_guard<std::mutex> lk(tt.mu);
+    tt.best[key] = best;
+    tt.save_locked();
+    return best;
+}
+
 template <class T2>
 void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, const T2 *P, const T2 *V,
-                        const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl) {
+                        const T2 *H, T2 *X, int B, int max_n2, int *err, cudaStream_t st, int *nl, bool tune) {
     if (nlayer <= 0 || B <= 0) return;
-    // 8-column tiles while the clusters of all layers fit on the GPU at once, else 16
+    bool ok = false;
+    if (tune) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        char key[160];
+        snprintf(key, sizeof key, "sweep es=%d layers=%d rhs=%d n2=%d dev=%d", (int)sizeof(T2), nlayer, B, max_n2, dev);
+        int choice = -2;
+        {
+            TuneTable &tt = tune_table();
+            std::lock_guard<std::mutex> lk(tt.mu);
+            if (!tt.loaded) tt.load_locked();
+            auto it = tt.best.find(key);
+            if (it != tt.best.end()) choice = it->second;
+        }
+        if (choice == -2) choice = tune_sweep<T2>(key, d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+        if (choice >= 0 && choice < kNumSweepCands)
+            ok = sweep_cand<T2>(choice, d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    }
+    // default rule: 8-column tiles while the clusters of all layers fit on the GPU at once, else 16
     const bool narrow = (long long)((B + 7) / 8) * nlayer * 16 <= 608;
-    bool ok = narrow ? inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st)
-                     : inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    if (!ok)
+        ok = narrow ? inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st)
+                    : inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) {
-        if ((long long)((B + 7) / 8) * nlayer * 16 <= 608)
+        if (narrow)
             ok = inner_sweep_regq<T2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
         else
             ok = inner_sweep_regq<T2, 16>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st) ||
@@ -1056,9 +1196,9 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
     if (nl) (*nl)++;
 }
 template void launch_inner_sweep<double2>(const LayerDesc *, const int *, int, const double2 *, const double2 *,
-                                          const double2 *, double2 *, int, int, int *, cudaStream_t, int *);
+                                          const double2 *, double2 *, int, int, int *, cudaStream_t, int *, bool);
 template void launch_inner_sweep<float2>(const LayerDesc *, const int *, int, const float2 *, const float2 *,
-                                         const float2 *, float2 *, int, int, int *, cudaStream_t, int *);
+                                         const float2 *, float2 *, int, int, int *, cudaStream_t, int *, bool);
 
 // ============================================== offline: coefficients ===
 // PML stretching alpha = 1/(1 + i sigma/omega), sigma(d) = (C/delta)(d/delta)^2

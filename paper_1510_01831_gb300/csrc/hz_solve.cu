@@ -1009,7 +1009,8 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     if (c->opts.time_kernels) inner_chain_cost<T2>(c, l0, nl, N, by, fl);
     c->kt_begin(1, by, fl);
     launch_inner_sweep<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.P, o.V, wide ? W.innerH2 : W.innerH,
-                           wide ? W.inner2 : W.inner, N, 2 * c->max_nz, c->d_err, c->st, &c->nl);
+                           wide ? W.inner2 : W.inner, N, 2 * c->max_nz, c->d_err, c->st, &c->nl,
+                           c->opts.autotune != 0);
     c->kt_end();
 }
 

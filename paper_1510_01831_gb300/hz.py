@@ -45,7 +45,7 @@ class HzOpts(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("pml_C", ctypes.c_double),
                 ("layer_rows", ctypes.POINTER(ctypes.c_int)), ("cell_cols", ctypes.POINTER(ctypes.c_int)),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):
@@ -142,7 +142,7 @@ class Context:
 
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
-                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=False, krylov=0):
+                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=False, krylov=0, autotune=False):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -160,6 +160,7 @@ class Context:
         o.time_kernels = 1 if time_kernels else 0
         o.tensor_cores = 1 if tensor_cores else 0
         o.krylov = int(krylov)
+        o.autotune = 1 if autotune else 0
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")

@@ -70,3 +70,26 @@ def test_group_device_pointers_and_errors():
     assert _rel(u.cpu().numpy(), ref) < 1e-8
     a.close()
     b.close()
+
+
+def test_autotuned_sweeps_match_oracle_and_fill_cache(tmp_path, monkeypatch):
+    # the tuner times the sweep launch configurations at first use and records
+    # its choice per launch shape in the JSON cache
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("HZ_TUNE_CACHE", str(cache))
+    pb = I.smooth_random(96, n_pml=8, L=3, C=4, seed=91, ppw=8, corr_pts=8)
+    C_pml = O.default_pml_C(pb.m)
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 20, 92)
+    ref = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml).factor().solve(f)
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_MIXED,
+                     pml_C=C_pml, autotune=True)
+    ctx.hz_factor()
+    u, st = ctx.hz_solve(f)
+    u2, _ = ctx.hz_solve(f)
+    ctx.close()
+    assert _rel(u, ref) < 1e-5 and _rel(u2, ref) < 1e-5
+    assert st.resid < 1e-8
+    import json
+    table = json.loads(cache.read_text())
+    assert any(k.startswith("sweep es=8") for k in table)
+    assert all(0 <= v < 6 for v in table.values())
