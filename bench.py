@@ -43,6 +43,8 @@ WORKLOADS = {
     # three frequencies (6, 8, 10 ppw) of one 512x512 smooth random medium, uneven layers and cells
     # (24-64 points), 256 sources each, solved as one group (one context and stream per frequency)
     "multifreq512": dict(n=512, n_pml=20, B=256, ppws=(6.0, 8.0, 10.0), seed=4, part_seed=40),
+    # layered medium with faults, 2000 wide x 4000 deep + 30 PML, L=40 x C=20, 16 sources, 8 ppw at c=1.5
+    "layered2000x4000": dict(n=2000, n_z=4000, n_pml=30, L=40, C=20, B=16, ppw=8.0, seed=3, layered=True),
 }
 METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
@@ -152,11 +154,17 @@ def describe(wl, pbs, B, precision):
                 f"{len(pbs)} frequencies ({'/'.join(f'{v:g}' for v in wl['ppws'])} ppw) solved as one group, "
                 f"uneven layers/cells 24-64 pts (L={pb.L} x C={pb.C}), {B} point sources row 1 per frequency, "
                 f"{precision}")
-    return (f"smooth random c in [1.5,4.5] corr 20h, {pb.n_x}x{pb.n_z}+{pb.n_pml} PML, {wl['ppw']:g} ppw, "
+    medium = ("layered medium with two dip-slip faults, c in [1.5,5.5]" if wl.get("layered")
+              else "smooth random c in [1.5,4.5] corr 20h")
+    return (f"{medium}, {pb.n_x}x{pb.n_z}+{pb.n_pml} PML, {wl['ppw']:g} ppw, "
             f"L={pb.L} x C={pb.C}, {B} point sources row 1, {precision}")
 
 
 def make_problem(wl):
+    if wl.get("layered"):
+        pb = I.layered_faulted(n_x=wl["n"], n_z=wl["n_z"], n_pml=wl["n_pml"], L=wl["L"], C=wl["C"], seed=wl["seed"],
+                               ppw=wl["ppw"])
+        return pb, I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, wl["B"])
     pb = I.smooth_random(wl["n"], n_pml=wl["n_pml"], L=wl["L"], C=wl["C"], seed=wl["seed"], ppw=wl["ppw"],
                          n_z=wl.get("n_z"))
     f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, wl["B"])
