@@ -310,15 +310,20 @@ __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__
                 // columns 2cg, 2cg+1 (+32 per extra pair): 16-byte loads of adjacent
                 // columns and of W(k), W(k+1)
                 const T2 *xr = tc + 2 * cg;
+                const T2 *wp[TM];
+#pragma unroll
+                for (int i = 0; i < TM; i++) wp[i] = wr + i * ldw;
                 int k = 0;
+#pragma unroll 2
                 for (; k + 1 < nx; k += 2) {
                     Pair<T2> w[TM];
 #pragma unroll
-                    for (int i = 0; i < TM; i++) w[i] = ld_pair(wr + i * ldw + k);
+                    for (int i = 0; i < TM; i++) w[i] = ld_pair(wp[i] + k);
+                    const T2 *xk = xr + k * NT;
 #pragma unroll
                     for (int tp = 0; tp < TN / 2; tp++) {
-                        const Pair<T2> x0 = ld_pair(xr + k * NT + 32 * tp);
-                        const Pair<T2> x1 = ld_pair(xr + (k + 1) * NT + 32 * tp);
+                        const Pair<T2> x0 = ld_pair(xk + 32 * tp);
+                        const Pair<T2> x1 = ld_pair(xk + NT + 32 * tp);
 #pragma unroll
                         for (int i = 0; i < TM; i++) {
                             cmac(acc[i][2 * tp], w[i].a, x0.a);
@@ -1179,11 +1184,13 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
         if (choice >= 0 && choice < kNumSweepCands)
             ok = sweep_cand<T2>(choice, d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     }
-    // default rule: 8-column tiles while the clusters of all layers fit on the GPU at once, else 16
+    // default rule (what the tuner picks on the 1024 x 1024 shapes): 8-column tiles;
+    // a single layer in flight takes 8-CTA clusters with 4 rows per warp, several
+    // layers 16-CTA clusters with 2 rows per warp
     const bool narrow = (long long)((B + 7) / 8) * nlayer * 16 <= 608;
-    if (!ok)
-        ok = narrow ? inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st)
-                    : inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
+    if (!ok && nlayer == 1)
+        ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 8);
+    if (!ok) ok = inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) {
         if (narrow)
