@@ -195,7 +195,7 @@ def run_ours(args, rank, world):
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
                          tensor_cores=args.tensor_cores, krylov=1 if args.krylov == "bicgstab" else 0,
-                         autotune=args.autotune, **kw)
+                         autotune=args.autotune, tol=args.tol, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
     t_factor = time.time() - t0
@@ -371,6 +371,7 @@ def main():
     ap.add_argument("--tensor-cores", action="store_true", help="mixed precision: cell solves on the tensor cores")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
+    ap.add_argument("--tol", type=float, default=0.0, help="GMRES tolerance of the first pass (0: library default)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -63,7 +63,8 @@ typedef struct {
     int restart;        /* GMRES restart length (default 30) */
     int max_it;         /* GMRES iteration cap per solve (default 200) */
     double tol;         /* GMRES relative residual on the polarized system
-                           (default 1e-10 FP64, 1e-6 mixed) */
+                           (default 1e-10 FP64, 3e-5 mixed: refinement
+                           passes carry the volume residual to refine_tol) */
     double refine_tol;  /* target ||H u - f|| / ||f|| on the volume; refinement
                            passes repeat the solve on the residual until it is
                            met (0: no refinement; default 1e-8) */

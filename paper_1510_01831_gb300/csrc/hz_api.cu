@@ -129,7 +129,7 @@ void hz_default_opts(hz_opts *o) {
     o->precond = HZ_PGS;
     o->restart = 30;
     o->max_it = 200;
-    o->tol = 0.0;  // 0: precision default (1e-10 FP64, 1e-6 mixed)
+    o->tol = 0.0;  // 0: precision default (1e-10 FP64, 3e-5 mixed)
     o->refine_tol = 1e-8;
     o->max_refine = 6;
     o->pml_C = 0.0;
@@ -151,7 +151,9 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     if (opts) c->opts = *opts;
     if (c->opts.restart < 1) c->opts.restart = 30;
     if (c->opts.max_it < 1) c->opts.max_it = 200;
-    if (c->opts.tol <= 0) c->opts.tol = c->opts.precision == HZ_MIXED ? 1e-6 : 1e-10;
+    // mixed: the first pass only has to bring the volume residual near the FP32
+    // operators' accuracy, the refinement passes carry it to refine_tol
+    if (c->opts.tol <= 0) c->opts.tol = c->opts.precision == HZ_MIXED ? 3e-5 : 1e-10;
     if (c->opts.precision != HZ_FP64 && c->opts.precision != HZ_MIXED) {
         delete c;
         return fail(nullptr, HZ_EINVAL, "precision must be HZ_FP64 or HZ_MIXED");
