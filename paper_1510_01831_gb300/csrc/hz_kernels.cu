@@ -44,10 +44,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     for (int i = 0; i < 4; i++)
 #pragma unroll
         for (int j = 0; j < 2; j++) acc[i][j] = czero<T2>();
-    // load slots of this thread: A elements (mm, kk) for q = 0..3, X elements (kk, nn) for q = 0..1
-    const int a_kk = tid % GBK, a_mm = tid / GBK;  // + 16 q rows
-    const int x_nn = tid % GBN, x_kk = tid / GBN;  // + 8 q rows
-    T2 ra[4], rx[2];
+    // load slots of this thread: A elements (mm, kk) for q < AQ, X elements (kk, nn) for q < XQ
+    constexpr int AR = 256 / GBK, AQ = GBM / AR;  // A rows per pass, passes
+    constexpr int XR = 256 / GBN, XQ = GBK / XR;  // X rows per pass, passes
+    const int a_kk = tid % GBK, a_mm = tid / GBK;  // + AR q rows
+    const int x_nn = tid % GBN, x_kk = tid / GBN;  // + XR q rows
+    T2 ra[AQ], rx[XQ];
     int buf = 0;
     for (int pass = 0; pass < 2; pass++) {
         const T2 *A = pass ? P.A2 : P.A;
@@ -61,13 +63,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         if (K <= klo) continue;
         auto load = [&](int k0) {
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int gm = m0 + a_mm + 16 * q, gk = k0 + a_kk;
+            for (int q = 0; q < AQ; q++) {
+                const int gm = m0 + a_mm + AR * q, gk = k0 + a_kk;
                 ra[q] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
             }
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
-                const int gk = k0 + x_kk + 8 * q, gn = n0 + x_nn;
+            for (int q = 0; q < XQ; q++) {
+                const int gk = k0 + x_kk + XR * q, gn = n0 + x_nn;
                 T2 v = czero<T2>();
                 if (gk < K && gn < N) {
                     const int sg = gk / xseg;
@@ -79,9 +81,9 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         load(klo);
         for (int k0 = klo; k0 < K; k0 += GBK) {
 #pragma unroll
-            for (int q = 0; q < 4; q++) As[buf][a_kk][a_mm + 16 * q] = ra[q];
+            for (int q = 0; q < AQ; q++) As[buf][a_kk][a_mm + AR * q] = ra[q];
 #pragma unroll
-            for (int q = 0; q < 2; q++) Xs[buf][x_kk + 8 * q][x_nn] = rx[q];
+            for (int q = 0; q < XQ; q++) Xs[buf][x_kk + XR * q][x_nn] = rx[q];
             __syncthreads();
             if (k0 + GBK < K) load(k0 + GBK);  // in flight during the products below
 #pragma unroll

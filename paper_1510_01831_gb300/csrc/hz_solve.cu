@@ -691,9 +691,9 @@ template <class T2> struct ListBuilder {
 // K slices per tile: launches with fewer tiles than GEMM_SPLIT_TILES and a
 // long K are split so that the whole GPU works on them
 static int gemm_split(long long tiles, int kmax) {
-    if (tiles >= GEMM_SPLIT_TILES || kmax < 32 * GBK) return 1;
+    if (tiles >= GEMM_SPLIT_TILES || kmax < 512) return 1;
     const long long s = (GEMM_SPLIT_TILES + tiles - 1) / tiles;
-    return (int)std::max(1LL, std::min<long long>({8, s, kmax / (16 * GBK)}));  // >= 256 of K per split
+    return (int)std::max(1LL, std::min<long long>({8, s, kmax / 256}));  // >= 256 of K per split
 }
 
 template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
