@@ -86,11 +86,11 @@ typedef struct {
                            fastest (environment HZ_TUNE_CACHE: JSON file that
                            keeps the choices across processes); 0 (default): fixed
                            rule */
-    int tensor_cores;   /* HZ_MIXED only: 1 runs the cell solves (a1) on the tensor
-                           cores (tcgen05, 3xTF32 split, cells up to 128 columns
-                           wide, cell-solve error ~6e-6 against ~8e-7 on the
-                           FP32 SIMT pipes), 0 (default) keeps them on the SIMT
-                           pipes */
+    int tensor_cores;   /* HZ_MIXED only: 1 (default) runs the cell solves (a1) on
+                           the tensor cores (tcgen05, 3xTF32 split, cells up to
+                           128 columns wide, cell-solve error ~3e-6 against
+                           ~8e-7 on the FP32 SIMT pipes), 0 keeps them on the
+                           SIMT pipes */
 } hz_opts;
 
 typedef struct {

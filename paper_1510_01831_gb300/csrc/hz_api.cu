@@ -13,9 +13,14 @@ namespace {
 
 thread_local std::string g_err;  // errors without a context (hz_setup failures)
 
-__global__ void k_finite(const double *a, long long n, int *flag) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        if (!isfinite(a[i])) atomicExch(flag, 1);
+// flag = 1 if any of n doubles is NaN or Inf (16-byte loads, n even)
+__global__ void k_finite(const double2 *a, long long n2, int *flag) {
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+        const double2 v = a[i];
+        bad |= !isfinite(v.x) || !isfinite(v.y);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
 }
 
 // d [B][n_rec], u [B][N]: r = R u - d; adjoint source g[b][rec] = conj(r)
@@ -97,7 +102,9 @@ double2 *stage(hz_ctx *c, long long n) {
 void check_finite(hz_ctx *c, const double *a, long long n, const char *what) {
     if (!c->d_flag) c->d_flag = (int *)c->dalloc(sizeof(int));
     HZ_CU(cudaMemsetAsync(c->d_flag, 0, sizeof(int), c->st));
-    k_finite<<<256, 256, 0, c->st>>>(a, n, c->d_flag);
+    // callers pass complex arrays (n even, 16-byte aligned)
+    k_finite<<<(int)std::min<long long>(4096, (n / 2 + 255) / 256 + 1), 256, 0, c->st>>>((const double2 *)a, n / 2,
+                                                                                         c->d_flag);
     HZ_CU(cudaGetLastError());
     c->nl++;
     int f = 0;
@@ -133,7 +140,7 @@ void hz_default_opts(hz_opts *o) {
     o->refine_tol = 1e-8;
     o->max_refine = 6;
     o->pml_C = 0.0;
-    o->tensor_cores = 0;
+    o->tensor_cores = 1;
 }
 
 hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega, double h, int n_pml, int L, int C,

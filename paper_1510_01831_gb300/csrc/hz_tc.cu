@@ -16,10 +16,11 @@
 //     "full" / "empty");
 //   - T is kept in shared memory as Tr_h, Tr_l, Ti_h, Ti_l in the same
 //     canonical layout (rows = right-hand sides, K = cell columns);
-//   - one thread issues the tcgen05.mma instructions (M = 128 rows of W,
+//   - a producer warp streams the W chunks through the ring ahead of use;
+//     one thread issues the tcgen05.mma instructions (M = 128 rows of W,
 //     N = 32 right-hand sides, K = 8 per instruction) into FP32 accumulators
-//     in tensor memory (the Xh Yh terms and the small cross terms in separate
-//     accumulators) and commits them to mbarriers;
+//     in tensor memory (the Xh Yh terms of even and odd K chunks and the small
+//     cross terms in separate accumulators) and commits them to mbarriers;
 //   - the 128 threads (thread = row of W, = TMEM lane) read the accumulators
 //     with tcgen05.ld, form the step's output (stored to global memory) and
 //     the next T, split it and write it back through a per-warp transpose.
@@ -36,7 +37,7 @@ namespace {
 constexpr int TC_NT = 32;    // right-hand sides per CTA (MMA N)
 constexpr int TC_KC = 16;    // K columns per streamed chunk
 constexpr int TC_ST = 4;     // ring stages
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 160;  // warps 0-3: MMA issue and epilogue (TMEM lanes 0-127); warp 4: producer
 constexpr int TC_STAGE_BYTES = 4 * 16 * (TC_KC / 4) * 128;  // 4 arrays x 16 row groups x SBO
 
 __device__ __forceinline__ unsigned su32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -179,6 +180,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long full[TC_ST], empty[TC_ST], done;
     __shared__ unsigned tmem_slot;
+    __shared__ volatile int s_dead;
+    __shared__ int s_loaded;  // chunks the producer issued
     const CellDesc cd = cells[blockIdx.y];
     const int nx = cd.nx, nz = cd.nz;
     const int n0 = blockIdx.x * TC_NT;
@@ -191,14 +194,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *ring = smraw;
     float *T = reinterpret_cast<float *>(smraw + TC_ST * TC_STAGE_BYTES);  // Tr_h, Tr_l, Ti_h, Ti_l
     const int tarr = TC_NT * Kp;                                          // floats per T array
-    float *scr = T + 4 * tarr + warp * 32 * 33;
+    float *scr = T + 4 * tarr + (warp & 3) * 32 * 33;
     const float *wc = wtc + cd.tc_off;
     const float2 *czc = cz + cd.cz_off;
     float2 *v = vol + cd.vol_off * (long long)B;
     const long long rs = (long long)nx * B;
     auto jb_of = [&](int s) { return s < nz ? s : 2 * nz - 2 - s; };
     auto chunk_kc = [&](int c) { return min(TC_KC, Kp - c * TC_KC); };
-    auto load = [&](int q) {  // thread 0
+    auto load = [&](int q) {  // producer lane
         const int s = q / nchk, c = q % nchk, st = q % TC_ST;
         const unsigned bytes = (unsigned)(4 * rows * chunk_kc(c) * 4);
         const float *src = wc + jb_of(s) * per_block + (long long)c * 4 * rows * TC_KC;
@@ -207,7 +210,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     };
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
-                     "r"(256)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -217,14 +220,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mb_init(su32(&empty[i]), 1);
         }
         mb_init(su32(&done), 1);
+        s_dead = 0;
+        s_loaded = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        for (int q = 0; q < TC_ST && q < total; q++) load(q);
     }
-    // this thread's row of the panel (K index of T, row of W and of D)
+    // this thread's row of the panel (K index of T, row of W and of D); warps 0-3
     const int m = tid;
-    const bool mrow = m < nx;
-    // t_0 = g_0
-    {
+    const bool mrow = warp < 4 && m < nx;
+    if (warp < 4) {  // t_0 = g_0
         float tr[2][16], ti[2][16];
 #pragma unroll
         for (int h = 0; h < 2; h++)
@@ -260,154 +263,178 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const unsigned tmem = tmem_slot;
-    // D accumulators (32 columns each): the main terms Xh Yh of P1 = Wr Tr, P2 = Wi Ti,
-    // P3 = Wr Ti, P4 = Wi Tr at columns 0, 32, 64, 96 and their cross terms Xh Yl + Xl Yh
-    // at 128, 160, 192, 224.  Keeping the small cross terms apart shortens the chain of
-    // additions into each main accumulator (the tensor core's accumulation truncates).
-    const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_NT >> 3) << 17) | (8u << 24);
-    const unsigned sboT = (unsigned)(Kp / 4) * 128;
-    const unsigned tbase = su32(T);
     bool dead = false;
-    int q_loaded = min(TC_ST, total);  // thread 0: chunks issued so far
-    int q_waited = 0;                   // thread 0: chunks whose data it has consumed
-    for (int s = 0; s < nsteps; s++) {
-        const bool fwd = s < nz;
-        const int jb = jb_of(s);
-        if (tid == 0 && !dead) {
-            for (int c = 0; c < nchk && !dead; c++) {
-                const int q = s * nchk + c, st = q % TC_ST;
-                if (!mb_wait(su32(&full[st]), (unsigned)((q / TC_ST) & 1), dead, err)) break;
-                q_waited = q + 1;
-                tc_fence_after();
-                const int KC = chunk_kc(c);
-                const unsigned sbo = (unsigned)(KC / 4) * 128;
-                const unsigned abase = su32(ring + st * TC_STAGE_BYTES);
-                const unsigned arr = (unsigned)(rows * KC * 4);  // bytes per W array in this chunk
-                // descriptors of this chunk: only the start address (bits 0-13) changes per K step
-                const unsigned long long dW = sdesc(abase, 128, sbo), dT = sdesc(tbase, 128, sboT);
-                for (int t = 0; t < KC / 8; t++) {
-                    const int k0 = c * TC_KC + 8 * t;
-                    const unsigned first = (c == 0 && t == 0) ? 0u : 1u;
-                    const unsigned long long aoff = (unsigned long long)((t * 256u) >> 4);
-                    const unsigned long long Wrh = dW + aoff + ((0u * arr) >> 4), Wrl = dW + aoff + ((1u * arr) >> 4);
-                    const unsigned long long Wih = dW + aoff + ((2u * arr) >> 4), Wil = dW + aoff + ((3u * arr) >> 4);
-                    const unsigned long long toff = (unsigned long long)((((unsigned)k0 / 4) * 128u) >> 4);
-                    const unsigned long long tq = (unsigned long long)(((unsigned)tarr * 4u) >> 4);
-                    const unsigned long long Trh = dT + toff, Trl = dT + toff + tq, Tih = dT + toff + 2 * tq,
-                                             Til = dT + toff + 3 * tq;
-                    umma_tf32(tmem + 0, Wrh, Trh, idesc, first);    // P1 main
-                    umma_tf32(tmem + 32, Wih, Tih, idesc, first);   // P2 main
-                    umma_tf32(tmem + 64, Wrh, Tih, idesc, first);   // P3 main
-                    umma_tf32(tmem + 96, Wih, Trh, idesc, first);   // P4 main
-                    umma_tf32(tmem + 128, Wrh, Trl, idesc, first);  // P1 cross
-                    umma_tf32(tmem + 128, Wrl, Trh, idesc, 1u);
-                    umma_tf32(tmem + 160, Wih, Til, idesc, first);  // P2 cross
-                    umma_tf32(tmem + 160, Wil, Tih, idesc, 1u);
-                    umma_tf32(tmem + 192, Wrh, Til, idesc, first);  // P3 cross
-                    umma_tf32(tmem + 192, Wrl, Tih, idesc, 1u);
-                    umma_tf32(tmem + 224, Wih, Trl, idesc, first);  // P4 cross
-                    umma_tf32(tmem + 224, Wil, Trh, idesc, 1u);
+    int q_waited = 0;  // thread 0: chunks whose data it has consumed
+    if (warp == 4) {
+        // producer: streams the W chunks of every step through the ring, TC_ST ahead
+        if (lane == 0) {
+            for (int q = 0; q < total; q++) {
+                const int st = q % TC_ST;
+                if (q >= TC_ST && !mb_wait(su32(&empty[st]), (unsigned)(((q / TC_ST) - 1) & 1), dead, err)) {
+                    s_dead = 1;
+                    break;
                 }
-                umma_commit(su32(&empty[st]));
-                // refill the stage of the previous chunk once its products are done
-                if (q >= 1 && q - 1 + TC_ST < total) {
-                    const int qp = q - 1, sp = qp % TC_ST;
-                    if (!mb_wait(su32(&empty[sp]), (unsigned)((qp / TC_ST) & 1), dead, err)) break;
-                    load(qp + TC_ST);
-                    q_loaded = qp + TC_ST + 1;
-                }
+                if (s_dead) break;
+                load(q);
+                s_loaded = q + 1;
             }
-            if (!dead) umma_commit(su32(&done));
         }
-        // global vector for this step's epilogue: forward -> g of step s+1, backward -> y of step s
-        const int sg = fwd ? (s + 1 < nz ? s + 1 : -1) : s;
-        float2 gv[TC_NT];
-#pragma unroll
-        for (int n = 0; n < TC_NT; n++) gv[n] = make_float2(0.f, 0.f);
-        if (sg >= 0 && mrow) {
-            const float2 *src = v + jb_of(sg) * rs + (long long)m * B + n0;
-#pragma unroll
-            for (int n = 0; n < TC_NT; n++)
-                if (n0 + n < B) gv[n] = src[n];
-        }
-        const float2 c_out = (mrow && fwd && s + 1 < nz) ? czc[(long long)jb * nx + m] : make_float2(0.f, 0.f);
-        const float2 c_next = (mrow && jb > 0) ? czc[(long long)(jb - 1) * nx + m] : make_float2(0.f, 0.f);
-        if (!dead) mb_wait(su32(&done), (unsigned)(s & 1), dead, err);
-        __syncwarp();
-        const bool wdead = __any_sync(0xffffffffu, dead);
-        if (!wdead) {
-            tc_fence_after();
-            float2 *g = v + jb * rs + (long long)m * B + n0;
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                float nr[16], ni[16];
-#pragma unroll
-                for (int qq = 0; qq < 2; qq++) {
-                    float p[8][8];
-                    const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 16 * h + 8 * qq;
-#pragma unroll
-                    for (int a = 0; a < 8; a++) tmem_ld8(ta + 32 * a, p[a]);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int i = 0; i < 8; i++) {
-                        const int n = 16 * h + 8 * qq + i;
-                        float2 out = make_float2((p[0][i] + p[4][i]) - (p[1][i] + p[5][i]),
-                                                 (p[2][i] + p[6][i]) + (p[3][i] + p[7][i]));
-                        float2 tn;
-                        if (fwd) {
-                            if (s + 1 < nz)
-                                tn = gv[n] - c_out * out;  // g_{j+1} - c_j y_j
-                            else
-                                tn = c_next * out;  // first backward step: c_{nz-2} x_{nz-1}
-                        } else {
-                            out = gv[n] - out;  // x_j = y_j - W_j t
-                            tn = c_next * out;
-                        }
-                        const bool live = mrow && n0 + n < B;
-                        if (!live) {
-                            out = make_float2(0.f, 0.f);
-                            tn = make_float2(0.f, 0.f);
-                        } else {
-                            g[n] = out;
-                        }
-                        nr[8 * qq + i] = tn.x;
-                        ni[8 * qq + i] = tn.y;
+        __syncwarp();  // the warp reaches the block barrier below converged
+    } else {
+        // D accumulators (32 columns each): main terms Xh Yh of P1 = Wr Tr, P2 = Wi Ti,
+        // P3 = Wr Ti, P4 = Wi Tr for even K chunks at columns 0..127 and odd chunks at
+        // 128..255, cross terms Xh Yl + Xl Yh at 256..383.  Short chains of additions
+        // into each accumulator keep the tensor core's truncating accumulation small.
+        const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_NT >> 3) << 17) | (8u << 24);
+        const unsigned sboT = (unsigned)(Kp / 4) * 128;
+        const unsigned tbase = su32(T);
+        for (int s = 0; s < nsteps; s++) {
+            const bool fwd = s < nz;
+            const int jb = jb_of(s);
+            if (tid == 0 && !dead) {
+                for (int c = 0; c < nchk && !dead; c++) {
+                    const int q = s * nchk + c, st = q % TC_ST;
+                    if (!mb_wait(su32(&full[st]), (unsigned)((q / TC_ST) & 1), dead, err)) break;
+                    q_waited = q + 1;
+                    tc_fence_after();
+                    const int KC = chunk_kc(c);
+                    const unsigned sbo = (unsigned)(KC / 4) * 128;
+                    const unsigned abase = su32(ring + st * TC_STAGE_BYTES);
+                    const unsigned arr = (unsigned)(rows * KC * 4);  // bytes per W array in this chunk
+                    const unsigned long long dW = sdesc(abase, 128, sbo), dT = sdesc(tbase, 128, sboT);
+                    const unsigned mainc = (c & 1) ? 128u : 0u;
+                    for (int t = 0; t < KC / 8; t++) {
+                        const int k0 = c * TC_KC + 8 * t;
+                        const unsigned fm = (c < 2 && t == 0) ? 0u : 1u;  // first product into a main accumulator
+                        const unsigned fx = (c == 0 && t == 0) ? 0u : 1u;  // first product into a cross accumulator
+                        const unsigned long long aoff = (unsigned long long)((t * 256u) >> 4);
+                        const unsigned long long Wrh = dW + aoff, Wrl = dW + aoff + ((1u * arr) >> 4);
+                        const unsigned long long Wih = dW + aoff + ((2u * arr) >> 4), Wil = dW + aoff + ((3u * arr) >> 4);
+                        const unsigned long long toff = (unsigned long long)((((unsigned)k0 / 4) * 128u) >> 4);
+                        const unsigned long long tq = (unsigned long long)(((unsigned)tarr * 4u) >> 4);
+                        const unsigned long long Trh = dT + toff, Trl = dT + toff + tq, Tih = dT + toff + 2 * tq,
+                                                 Til = dT + toff + 3 * tq;
+                        umma_tf32(tmem + mainc + 0, Wrh, Trh, idesc, fm);    // P1 main
+                        umma_tf32(tmem + mainc + 32, Wih, Tih, idesc, fm);   // P2 main
+                        umma_tf32(tmem + mainc + 64, Wrh, Tih, idesc, fm);   // P3 main
+                        umma_tf32(tmem + mainc + 96, Wih, Trh, idesc, fm);   // P4 main
+                        umma_tf32(tmem + 256, Wrh, Trl, idesc, fx);          // P1 cross
+                        umma_tf32(tmem + 256, Wrl, Trh, idesc, 1u);
+                        umma_tf32(tmem + 288, Wih, Til, idesc, fx);          // P2 cross
+                        umma_tf32(tmem + 288, Wil, Tih, idesc, 1u);
+                        umma_tf32(tmem + 320, Wrh, Til, idesc, fx);          // P3 cross
+                        umma_tf32(tmem + 320, Wrl, Tih, idesc, 1u);
+                        umma_tf32(tmem + 352, Wih, Trl, idesc, fx);          // P4 cross
+                        umma_tf32(tmem + 352, Wil, Trh, idesc, 1u);
                     }
+                    umma_commit(su32(&empty[st]));  // the producer may refill this stage once these are done
                 }
-                float a[16], b[16];
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    a[i] = tf32_rna(nr[i]);
-                    b[i] = tf32_rna(nr[i] - a[i]);
-                }
-                put_T(T, Kp, 16 * h, a, scr, warp, lane);
-                put_T(T + tarr, Kp, 16 * h, b, scr, warp, lane);
-#pragma unroll
-                for (int i = 0; i < 16; i++) {
-                    a[i] = tf32_rna(ni[i]);
-                    b[i] = tf32_rna(ni[i] - a[i]);
-                }
-                put_T(T + 2 * tarr, Kp, 16 * h, a, scr, warp, lane);
-                put_T(T + 3 * tarr, Kp, 16 * h, b, scr, warp, lane);
+                if (!dead) umma_commit(su32(&done));
             }
+            // global vector for this step's epilogue: forward -> g of step s+1, backward -> y of step s
+            const int sg = fwd ? (s + 1 < nz ? s + 1 : -1) : s;
+            float2 gv[TC_NT];
+#pragma unroll
+            for (int n = 0; n < TC_NT; n++) gv[n] = make_float2(0.f, 0.f);
+            if (sg >= 0 && mrow) {
+                const float2 *src = v + jb_of(sg) * rs + (long long)m * B + n0;
+#pragma unroll
+                for (int n = 0; n < TC_NT; n++)
+                    if (n0 + n < B) gv[n] = src[n];
+            }
+            const float2 c_out = (mrow && fwd && s + 1 < nz) ? czc[(long long)jb * nx + m] : make_float2(0.f, 0.f);
+            const float2 c_next = (mrow && jb > 0) ? czc[(long long)(jb - 1) * nx + m] : make_float2(0.f, 0.f);
+            if (!dead) mb_wait(su32(&done), (unsigned)(s & 1), dead, err);
+            __syncwarp();
+            const bool wdead = __any_sync(0xffffffffu, dead);
+            if (!wdead) {
+                tc_fence_after();
+                float2 *g = v + jb * rs + (long long)m * B + n0;
+#pragma unroll
+                for (int h = 0; h < 2; h++) {
+                    float nr[16], ni[16];
+#pragma unroll
+                    for (int qq = 0; qq < 2; qq++) {
+                        float p[12][8];
+                        const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 16 * h + 8 * qq;
+#pragma unroll
+                        for (int a = 0; a < 12; a++) tmem_ld8(ta + 32 * a, p[a]);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                        if (nchk < 2) {  // no odd chunks: those accumulators were never written
+#pragma unroll
+                            for (int a = 4; a < 8; a++)
+#pragma unroll
+                                for (int i = 0; i < 8; i++) p[a][i] = 0.f;
+                        }
+#pragma unroll
+                        for (int i = 0; i < 8; i++) {
+                            const int n = 16 * h + 8 * qq + i;
+                            const float s1 = (p[0][i] + p[4][i]) + p[8][i], s2 = (p[1][i] + p[5][i]) + p[9][i];
+                            const float s3 = (p[2][i] + p[6][i]) + p[10][i], s4 = (p[3][i] + p[7][i]) + p[11][i];
+                            float2 out = make_float2(s1 - s2, s3 + s4);
+                            float2 tn;
+                            if (fwd) {
+                                if (s + 1 < nz)
+                                    tn = gv[n] - c_out * out;  // g_{j+1} - c_j y_j
+                                else
+                                    tn = c_next * out;  // first backward step: c_{nz-2} x_{nz-1}
+                            } else {
+                                out = gv[n] - out;  // x_j = y_j - W_j t
+                                tn = c_next * out;
+                            }
+                            const bool live = mrow && n0 + n < B;
+                            if (!live) {
+                                out = make_float2(0.f, 0.f);
+                                tn = make_float2(0.f, 0.f);
+                            } else {
+                                g[n] = out;
+                            }
+                            nr[8 * qq + i] = tn.x;
+                            ni[8 * qq + i] = tn.y;
+                        }
+                    }
+                    float a[16], b[16];
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        a[i] = tf32_rna(nr[i]);
+                        b[i] = tf32_rna(nr[i] - a[i]);
+                    }
+                    put_T(T, Kp, 16 * h, a, scr, warp, lane);
+                    put_T(T + tarr, Kp, 16 * h, b, scr, warp, lane);
+#pragma unroll
+                    for (int i = 0; i < 16; i++) {
+                        a[i] = tf32_rna(ni[i]);
+                        b[i] = tf32_rna(ni[i] - a[i]);
+                    }
+                    put_T(T + 2 * tarr, Kp, 16 * h, a, scr, warp, lane);
+                    put_T(T + 3 * tarr, Kp, 16 * h, b, scr, warp, lane);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // T written by threads -> read by the MMAs
+            tc_fence_before();
+            if (dead) s_dead = 1;
+            asm volatile("bar.sync 1, 128;" ::: "memory");  // warps 0-3 only: the producer runs on
+            if (s_dead) {
+                dead = true;
+                break;
+            }
+            tc_fence_after();
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // T written by threads -> read by the MMAs
-        tc_fence_before();
-        if (__syncthreads_or(dead)) break;
-        tc_fence_after();
-    }
-    // after a timeout: let the bulk copies this CTA issued land before it leaves
-    if (tid == 0 && dead) {
-        for (int q = q_waited; q < q_loaded; q++)
-            mb_wait(su32(&full[q % TC_ST]), (unsigned)((q / TC_ST) & 1), dead, err);
+        if (dead) s_dead = 1;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (dead) __nanosleep(20000);  // products still in flight finish before the tensor memory is freed
+    // after a timeout: let the bulk copies issued for this CTA land before it leaves
+    if (tid == 0 && s_dead) {
+        for (int q = q_waited; q < s_loaded; q++)
+            mb_wait(su32(&full[q % TC_ST]), (unsigned)((q / TC_ST) & 1), dead, err);
+    }
+    __syncthreads();
+    if (s_dead) __nanosleep(20000);  // products still in flight finish before the tensor memory is freed
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 }  // namespace

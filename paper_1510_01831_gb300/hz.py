@@ -142,7 +142,7 @@ class Context:
 
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
-                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=False, krylov=0, autotune=False):
+                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
