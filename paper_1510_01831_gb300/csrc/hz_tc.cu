@@ -174,17 +174,23 @@ __device__ __forceinline__ void put_T(float *Tq, int kext, int n0, const float (
     }
 }
 
+// NT right-hand sides per CTA (MMA N): 32 (12 accumulators, the main terms of even
+// and odd K chunks apart, 4 ring stages) or 64 (8 accumulators, 3 ring stages;
+// the W stream then serves twice the right-hand sides)
+template <int NT>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_cell_chain_tc(const CellDesc *__restrict__ cells, const float *__restrict__ wtc, const float2 *__restrict__ cz,
                     float2 *vol, int B, int *err) {
+    constexpr int ST = NT == 64 ? 3 : TC_ST;         // ring stages
+    constexpr int NACC = NT == 64 ? 8 : 12;          // accumulators of NT columns (NACC * NT <= 512)
     extern __shared__ __align__(1024) unsigned char smraw[];
-    __shared__ __align__(8) unsigned long long full[TC_ST], empty[TC_ST], done;
+    __shared__ __align__(8) unsigned long long full[ST], empty[ST], done;
     __shared__ unsigned tmem_slot;
     __shared__ volatile int s_dead;
     __shared__ int s_loaded;  // chunks the producer issued
     const CellDesc cd = cells[blockIdx.y];
     const int nx = cd.nx, nz = cd.nz;
-    const int n0 = blockIdx.x * TC_NT;
+    const int n0 = blockIdx.x * NT;
     if (n0 >= B) return;  // uniform
     const int R8 = (nx + 7) / 8, Kp = 8 * R8, rows = 8 * R8;
     const int nchk = (Kp + TC_KC - 1) / TC_KC;
@@ -192,8 +198,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const long long per_block = 32LL * R8 * Kp;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     unsigned char *ring = smraw;
-    float *T = reinterpret_cast<float *>(smraw + TC_ST * TC_STAGE_BYTES);  // Tr_h, Tr_l, Ti_h, Ti_l
-    const int tarr = TC_NT * Kp;                                          // floats per T array
+    float *T = reinterpret_cast<float *>(smraw + ST * TC_STAGE_BYTES);  // Tr_h, Tr_l, Ti_h, Ti_l
+    const int tarr = NT * Kp;                                          // floats per T array
     float *scr = T + 4 * tarr + (warp & 3) * 32 * 33;
     const float *wc = wtc + cd.tc_off;
     const float2 *czc = cz + cd.cz_off;
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     auto jb_of = [&](int s) { return s < nz ? s : 2 * nz - 2 - s; };
     auto chunk_kc = [&](int c) { return min(TC_KC, Kp - c * TC_KC); };
     auto load = [&](int q) {  // producer lane
-        const int s = q / nchk, c = q % nchk, st = q % TC_ST;
+        const int s = q / nchk, c = q % nchk, st = q % ST;
         const unsigned bytes = (unsigned)(4 * rows * chunk_kc(c) * 4);
         const float *src = wc + jb_of(s) * per_block + (long long)c * 4 * rows * TC_KC;
         mb_expect(su32(&full[st]), bytes);
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < TC_ST; i++) {
+        for (int i = 0; i < ST; i++) {
             mb_init(su32(&full[i]), 1);
             mb_init(su32(&empty[i]), 1);
         }
@@ -228,9 +234,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int m = tid;
     const bool mrow = warp < 4 && m < nx;
     if (warp < 4) {  // t_0 = g_0
-        float tr[2][16], ti[2][16];
+        float tr[NT / 16][16], ti[NT / 16][16];
 #pragma unroll
-        for (int h = 0; h < 2; h++)
+        for (int h = 0; h < NT / 16; h++)
 #pragma unroll
             for (int i = 0; i < 16; i++) {
                 const int n = 16 * h + i;
@@ -240,7 +246,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 ti[h][i] = g.y;
             }
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
+        for (int h = 0; h < NT / 16; h++) {
             float a[16], b[16];
 #pragma unroll
             for (int i = 0; i < 16; i++) {
@@ -266,11 +272,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool dead = false;
     int q_waited = 0;  // thread 0: chunks whose data it has consumed
     if (warp == 4) {
-        // producer: streams the W chunks of every step through the ring, TC_ST ahead
+        // producer: streams the W chunks of every step through the ring, ST ahead
         if (lane == 0) {
             for (int q = 0; q < total; q++) {
-                const int st = q % TC_ST;
-                if (q >= TC_ST && !mb_wait(su32(&empty[st]), (unsigned)(((q / TC_ST) - 1) & 1), dead, err)) {
+                const int st = q % ST;
+                if (q >= ST && !mb_wait(su32(&empty[st]), (unsigned)(((q / ST) - 1) & 1), dead, err)) {
                     s_dead = 1;
                     break;
                 }
@@ -281,11 +287,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         __syncwarp();  // the warp reaches the block barrier below converged
     } else {
-        // D accumulators (32 columns each): main terms Xh Yh of P1 = Wr Tr, P2 = Wi Ti,
-        // P3 = Wr Ti, P4 = Wi Tr for even K chunks at columns 0..127 and odd chunks at
-        // 128..255, cross terms Xh Yl + Xl Yh at 256..383.  Short chains of additions
-        // into each accumulator keep the tensor core's truncating accumulation small.
-        const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(TC_NT >> 3) << 17) | (8u << 24);
+        // D accumulators (NT columns each): main terms Xh Yh of P1 = Wr Tr, P2 = Wi Ti,
+        // P3 = Wr Ti, P4 = Wi Tr at columns 0..4NT-1 (NT = 32: even K chunks there, odd
+        // chunks at 128..255), cross terms Xh Yl + Xl Yh at 256..256+4NT-1.  Short chains
+        // of additions into each accumulator keep the tensor core's truncating
+        // accumulation small.
+        const unsigned idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((unsigned)(NT >> 3) << 17) | (8u << 24);
         const unsigned sboT = (unsigned)(Kp / 4) * 128;
         const unsigned tbase = su32(T);
         for (int s = 0; s < nsteps; s++) {
@@ -293,8 +300,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int jb = jb_of(s);
             if (tid == 0 && !dead) {
                 for (int c = 0; c < nchk && !dead; c++) {
-                    const int q = s * nchk + c, st = q % TC_ST;
-                    if (!mb_wait(su32(&full[st]), (unsigned)((q / TC_ST) & 1), dead, err)) break;
+                    const int q = s * nchk + c, st = q % ST;
+                    if (!mb_wait(su32(&full[st]), (unsigned)((q / ST) & 1), dead, err)) break;
                     q_waited = q + 1;
                     tc_fence_after();
                     const int KC = chunk_kc(c);
@@ -302,10 +309,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const unsigned abase = su32(ring + st * TC_STAGE_BYTES);
                     const unsigned arr = (unsigned)(rows * KC * 4);  // bytes per W array in this chunk
                     const unsigned long long dW = sdesc(abase, 128, sbo), dT = sdesc(tbase, 128, sboT);
-                    const unsigned mainc = (c & 1) ? 128u : 0u;
+                    const unsigned mainc = (NT == 32 && (c & 1)) ? 128u : 0u;
                     for (int t = 0; t < KC / 8; t++) {
                         const int k0 = c * TC_KC + 8 * t;
-                        const unsigned fm = (c < 2 && t == 0) ? 0u : 1u;  // first product into a main accumulator
+                        // first product into a main accumulator (NT = 32: even and odd chunks apart)
+                        const unsigned fm = ((NT == 32 ? c < 2 : c == 0) && t == 0) ? 0u : 1u;
                         const unsigned fx = (c == 0 && t == 0) ? 0u : 1u;  // first product into a cross accumulator
                         const unsigned long long aoff = (unsigned long long)((t * 256u) >> 4);
                         const unsigned long long Wrh = dW + aoff, Wrl = dW + aoff + ((1u * arr) >> 4);
@@ -314,34 +322,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         const unsigned long long tq = (unsigned long long)(((unsigned)tarr * 4u) >> 4);
                         const unsigned long long Trh = dT + toff, Trl = dT + toff + tq, Tih = dT + toff + 2 * tq,
                                                  Til = dT + toff + 3 * tq;
-                        umma_tf32(tmem + mainc + 0, Wrh, Trh, idesc, fm);    // P1 main
-                        umma_tf32(tmem + mainc + 32, Wih, Tih, idesc, fm);   // P2 main
-                        umma_tf32(tmem + mainc + 64, Wrh, Tih, idesc, fm);   // P3 main
-                        umma_tf32(tmem + mainc + 96, Wih, Trh, idesc, fm);   // P4 main
-                        umma_tf32(tmem + 256, Wrh, Trl, idesc, fx);          // P1 cross
-                        umma_tf32(tmem + 256, Wrl, Trh, idesc, 1u);
-                        umma_tf32(tmem + 288, Wih, Til, idesc, fx);          // P2 cross
-                        umma_tf32(tmem + 288, Wil, Tih, idesc, 1u);
-                        umma_tf32(tmem + 320, Wrh, Til, idesc, fx);          // P3 cross
-                        umma_tf32(tmem + 320, Wrl, Tih, idesc, 1u);
-                        umma_tf32(tmem + 352, Wih, Trl, idesc, fx);          // P4 cross
-                        umma_tf32(tmem + 352, Wil, Trh, idesc, 1u);
+                        umma_tf32(tmem + mainc + 0 * NT, Wrh, Trh, idesc, fm);  // P1 main
+                        umma_tf32(tmem + mainc + 1 * NT, Wih, Tih, idesc, fm);  // P2 main
+                        umma_tf32(tmem + mainc + 2 * NT, Wrh, Tih, idesc, fm);  // P3 main
+                        umma_tf32(tmem + mainc + 3 * NT, Wih, Trh, idesc, fm);  // P4 main
+                        umma_tf32(tmem + 256 + 0 * NT, Wrh, Trl, idesc, fx);    // P1 cross
+                        umma_tf32(tmem + 256 + 0 * NT, Wrl, Trh, idesc, 1u);
+                        umma_tf32(tmem + 256 + 1 * NT, Wih, Til, idesc, fx);    // P2 cross
+                        umma_tf32(tmem + 256 + 1 * NT, Wil, Tih, idesc, 1u);
+                        umma_tf32(tmem + 256 + 2 * NT, Wrh, Til, idesc, fx);    // P3 cross
+                        umma_tf32(tmem + 256 + 2 * NT, Wrl, Tih, idesc, 1u);
+                        umma_tf32(tmem + 256 + 3 * NT, Wih, Trl, idesc, fx);    // P4 cross
+                        umma_tf32(tmem + 256 + 3 * NT, Wil, Trh, idesc, 1u);
                     }
                     umma_commit(su32(&empty[st]));  // the producer may refill this stage once these are done
                 }
                 if (!dead) umma_commit(su32(&done));
             }
-            // global vector for this step's epilogue: forward -> g of step s+1, backward -> y of step s
+            // global vector of this step's epilogue (forward: g of step s+1; backward: y of
+            // step s), row m, loaded one 8-column quarter ahead of its use
             const int sg = fwd ? (s + 1 < nz ? s + 1 : -1) : s;
-            float2 gv[TC_NT];
+            const float2 *gsrc = (sg >= 0 && mrow) ? v + jb_of(sg) * rs + (long long)m * B + n0 : nullptr;
+            auto gload = [&](int q8, float2 (&gq)[8]) {
 #pragma unroll
-            for (int n = 0; n < TC_NT; n++) gv[n] = make_float2(0.f, 0.f);
-            if (sg >= 0 && mrow) {
-                const float2 *src = v + jb_of(sg) * rs + (long long)m * B + n0;
-#pragma unroll
-                for (int n = 0; n < TC_NT; n++)
-                    if (n0 + n < B) gv[n] = src[n];
-            }
+                for (int i = 0; i < 8; i++) {
+                    const int n = 8 * q8 + i;
+                    gq[i] = (gsrc && n0 + n < B) ? gsrc[n] : make_float2(0.f, 0.f);
+                }
+            };
+            float2 gcur[8], gnext[8];
+            gload(0, gcur);
             const float2 c_out = (mrow && fwd && s + 1 < nz) ? czc[(long long)jb * nx + m] : make_float2(0.f, 0.f);
             const float2 c_next = (mrow && jb > 0) ? czc[(long long)(jb - 1) * nx + m] : make_float2(0.f, 0.f);
             if (!dead) mb_wait(su32(&done), (unsigned)(s & 1), dead, err);
@@ -351,16 +361,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 tc_fence_after();
                 float2 *g = v + jb * rs + (long long)m * B + n0;
 #pragma unroll
-                for (int h = 0; h < 2; h++) {
+                for (int h = 0; h < NT / 16; h++) {
                     float nr[16], ni[16];
 #pragma unroll
                     for (int qq = 0; qq < 2; qq++) {
-                        float p[12][8];
-                        const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 16 * h + 8 * qq;
+                        const int q8 = 2 * h + qq;
+                        if (q8 + 1 < NT / 8) gload(q8 + 1, gnext);
+                        float p[NACC][8];
+                        const unsigned ta = tmem + ((unsigned)(32 * warp) << 16) + 8 * q8;
 #pragma unroll
-                        for (int a = 0; a < 12; a++) tmem_ld8(ta + 32 * a, p[a]);
+                        for (int a = 0; a < NACC; a++) tmem_ld8(ta + NT * a, p[a]);
                         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                        if (nchk < 2) {  // no odd chunks: those accumulators were never written
+                        if (NT == 32 && nchk < 2) {  // no odd chunks: those accumulators were never written
 #pragma unroll
                             for (int a = 4; a < 8; a++)
 #pragma unroll
@@ -368,18 +380,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                         }
 #pragma unroll
                         for (int i = 0; i < 8; i++) {
-                            const int n = 16 * h + 8 * qq + i;
-                            const float s1 = (p[0][i] + p[4][i]) + p[8][i], s2 = (p[1][i] + p[5][i]) + p[9][i];
-                            const float s3 = (p[2][i] + p[6][i]) + p[10][i], s4 = (p[3][i] + p[7][i]) + p[11][i];
+                            const int n = 8 * q8 + i;
+                            float s1, s2, s3, s4;  // P1..P4: main (+ odd-chunk main) + cross
+                            if (NT == 32) {
+                                s1 = (p[0][i] + p[4][i]) + p[8][i];
+                                s2 = (p[1][i] + p[5][i]) + p[9][i];
+                                s3 = (p[2][i] + p[6][i]) + p[10][i];
+                                s4 = (p[3][i] + p[7][i]) + p[11][i];
+                            } else {
+                                s1 = p[0][i] + p[4][i];
+                                s2 = p[1][i] + p[5][i];
+                                s3 = p[2][i] + p[6][i];
+                                s4 = p[3][i] + p[7][i];
+                            }
                             float2 out = make_float2(s1 - s2, s3 + s4);
                             float2 tn;
                             if (fwd) {
                                 if (s + 1 < nz)
-                                    tn = gv[n] - c_out * out;  // g_{j+1} - c_j y_j
+                                    tn = gcur[i] - c_out * out;  // g_{j+1} - c_j y_j
                                 else
                                     tn = c_next * out;  // first backward step: c_{nz-2} x_{nz-1}
                             } else {
-                                out = gv[n] - out;  // x_j = y_j - W_j t
+                                out = gcur[i] - out;  // x_j = y_j - W_j t
                                 tn = c_next * out;
                             }
                             const bool live = mrow && n0 + n < B;
@@ -392,6 +414,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                             nr[8 * qq + i] = tn.x;
                             ni[8 * qq + i] = tn.y;
                         }
+#pragma unroll
+                        for (int i = 0; i < 8; i++) gcur[i] = gnext[i];
                     }
                     float a[16], b[16];
 #pragma unroll
@@ -428,7 +452,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // after a timeout: let the bulk copies issued for this CTA land before it leaves
     if (tid == 0 && s_dead) {
         for (int q = q_waited; q < s_loaded; q++)
-            mb_wait(su32(&full[q % TC_ST]), (unsigned)((q / TC_ST) & 1), dead, err);
+            mb_wait(su32(&full[q % ST]), (unsigned)((q / ST) & 1), dead, err);
     }
     __syncthreads();
     if (s_dead) __nanosleep(20000);  // products still in flight finish before the tensor memory is freed
@@ -439,10 +463,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
 }  // namespace
 
-size_t cell_chain_tc_smem(int max_nx) {
+static size_t tc_smem(int nt, int max_nx) {
     const int Kp = 8 * ((max_nx + 7) / 8);
-    return (size_t)TC_ST * TC_STAGE_BYTES + (size_t)4 * TC_NT * Kp * 4 + (size_t)4 * 32 * 33 * 4;
+    const int st = nt == 64 ? 3 : TC_ST;
+    return (size_t)st * TC_STAGE_BYTES + (size_t)4 * nt * Kp * 4 + (size_t)4 * 32 * 33 * 4;
 }
+size_t cell_chain_tc_smem(int max_nx) { return tc_smem(32, max_nx); }
 
 long long cell_tc_floats(int nx, int nz) {
     const int R8 = (nx + 7) / 8;
@@ -460,10 +486,16 @@ void launch_cell_chain_tc(const CellDesc *d_cells, int ncell, const float *wtc, 
                           int max_nx, int *err, cudaStream_t st, int *nl) {
     if (ncell <= 0 || B <= 0) return;
     if (max_nx > 128) throw HzError(HZ_EINVAL, "tensor-core cell solve: cells wider than 128 columns");
-    const size_t sm = cell_chain_tc_smem(max_nx);
-    HZ_CU(cudaFuncSetAttribute(k_cell_chain_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    dim3 grid((B + TC_NT - 1) / TC_NT, ncell);
-    k_cell_chain_tc<<<grid, TC_THREADS, sm, st>>>(d_cells, wtc, cz, vol, B, err);
+    // 64 right-hand sides per CTA when the batch has more than 32 and the panel fits
+    const bool wide = B > 32 && tc_smem(64, max_nx) <= 220 * 1024;
+    const size_t sm = tc_smem(wide ? 64 : 32, max_nx);
+    if (wide) {
+        HZ_CU(cudaFuncSetAttribute(k_cell_chain_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cell_chain_tc<64><<<dim3((B + 63) / 64, ncell), TC_THREADS, sm, st>>>(d_cells, wtc, cz, vol, B, err);
+    } else {
+        HZ_CU(cudaFuncSetAttribute(k_cell_chain_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_cell_chain_tc<32><<<dim3((B + 31) / 32, ncell), TC_THREADS, sm, st>>>(d_cells, wtc, cz, vol, B, err);
+    }
     HZ_CU(cudaGetLastError());
     if (nl) (*nl)++;
 }

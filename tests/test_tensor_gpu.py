@@ -29,7 +29,11 @@ def _ctx(pb, C_pml, tc):
     return ctx
 
 
-@pytest.mark.parametrize("n,p,L,C,B", [(100, 6, 4, 2, 5), (128, 20, 2, 2, 40)])
+# B > 32 takes the 64-column form of the kernel where its panel fits in shared memory
+# (cells up to 104 columns), else the 32-column form (115 columns): B = 40 and 70 leave
+# ragged tails
+@pytest.mark.parametrize("n,p,L,C,B", [(100, 6, 4, 2, 5), (128, 20, 2, 2, 40), (100, 20, 2, 2, 70),
+                                       (150, 20, 2, 2, 70)])
 def test_cell_solve_tensor_vs_simt_and_oracle(n, p, L, C, B):
     pb = I.smooth_random(n, n_pml=p, L=L, C=C, seed=31, ppw=8, corr_pts=10)
     C_pml = O.default_pml_C(pb.m)
