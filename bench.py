@@ -194,7 +194,7 @@ def run_ours(args, rank, world):
             kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
-                         tensor_cores=not args.no_tensor_cores, krylov=1 if args.krylov == "bicgstab" else 0,
+                         tensor_cores=0 if args.no_tensor_cores else (2 if args.tc_gemm else 1), krylov=1 if args.krylov == "bicgstab" else 0,
                          autotune=args.autotune, tol=args.tol, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tensor-cores", action="store_true", help="mixed precision: cell solves on the SIMT pipes")
+    ap.add_argument("--tc-gemm", action="store_true",
+                    help="mixed precision: batched F/E/S/W products with long K on the tensor cores too")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
     ap.add_argument("--tol", type=float, default=0.0, help="GMRES tolerance of the first pass (0: library default)")

@@ -89,8 +89,12 @@ typedef struct {
     int tensor_cores;   /* HZ_MIXED only: 1 (default) runs the cell solves (a1) on
                            the tensor cores (tcgen05, 3xTF32 split, cells up to
                            128 columns wide, cell-solve error ~3e-6 against
-                           ~8e-7 on the FP32 SIMT pipes), 0 keeps them on the
-                           SIMT pipes */
+                           ~8e-7 on the FP32 SIMT pipes); 2 also runs the
+                           batched F / E / S / W products (a2-a5) with long K
+                           on them (3xTF32, error ~2e-7 against ~5e-7 on the
+                           SIMT pipes, at the cost of TF32 split copies of the
+                           operators, twice their FP32 size in device memory);
+                           0 keeps everything on the SIMT pipes */
 } hz_opts;
 
 typedef struct {

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libhz.so")
-SOURCES = ["hz_kernels.cu", "hz_tc.cu", "hz_factor.cu", "hz_solve.cu", "hz_api.cu", "hz_noalloc.cu"]
+SOURCES = ["hz_kernels.cu", "hz_tc.cu", "hz_tcgemm.cu", "hz_factor.cu", "hz_solve.cu", "hz_api.cu", "hz_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

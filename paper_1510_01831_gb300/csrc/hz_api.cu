@@ -173,6 +173,10 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
         delete c;
         return fail(nullptr, HZ_EINVAL, "krylov must be HZ_GMRES or HZ_BICGSTAB");
     }
+    if (c->opts.tensor_cores < 0 || c->opts.tensor_cores > 2) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "tensor_cores must be 0, 1 or 2");
+    }
     c->n_x = n_x;
     c->n_z = n_z;
     c->p = n_pml;

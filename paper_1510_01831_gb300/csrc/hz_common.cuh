@@ -120,6 +120,9 @@ template <class T2> struct GemmProb {
     int K2, xseg2;
     long long ldx2;
     const T2 *X2[4];
+    // tensor-core GEMM only: TF32 split copies of A and A2 (per 128-row tile and
+    // 16-column chunk, canonical MMA layout; null elsewhere)
+    const float *Atc, *A2tc;
 };
 
 // ------------------------------------------------------------ errors ---
@@ -161,6 +164,16 @@ constexpr int GBM = 64, GBN = 32, GBK = 16;
 // split-K is used while a launch has fewer tiles than this; its workspace
 // holds at most 2x this many partial tiles
 constexpr int GEMM_SPLIT_TILES = 304;
+
+// tensor-core batched GEMM (mixed precision): 128 x 64 output tiles, K chunks of
+// 16; split-K while a launch has fewer tiles than GEMM_TC_SPLIT_TILES, with a
+// workspace of at most GEMM_TC_WS_TILES partial tiles (defined in hz_tcgemm.cu)
+constexpr int GT_M = 128, GT_N = 64, GT_KC = 16;
+constexpr int GEMM_TC_SPLIT_TILES = 152, GEMM_TC_WS_TILES = 1024;
+// launches with fewer (tiles x K chunks) than this take the SIMT kernel
+constexpr long long GEMM_TC_MIN_WORK = 600;
+void launch_gemm_tc(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int split, float2 *ws, int *cnt,
+                    int *err, cudaStream_t st, int *nl);
 
 // tensor-core cell solve (mixed precision, cells up to 128 columns)
 size_t cell_chain_tc_smem(int max_nx);

@@ -3,6 +3,7 @@
 #pragma once
 #include <map>
 #include <memory>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hz.h"
@@ -23,6 +24,9 @@ template <class T2> struct ProbList {
     GemmProb<T2> *d = nullptr;
     int n = 0, max_tiles = 0;
     int kmax = 0;                 // longest K (both passes) of a problem
+    int tc_max_tiles = 0;         // tensor-core GEMM: most 128 x 64 tiles of a problem,
+    int tc_kchunks = 0;           // most K chunks of 16 (both passes), and
+    long long tc_tiles = 0;       // tiles of the whole list
     double bytes = 0, flops = 0;  // algorithmic traffic and real flops of one launch
 };
 
@@ -67,6 +71,14 @@ template <class T2> struct Work {
     std::vector<double> hbytes, hflops;  // per layer (B wide)
 };
 
+}  // namespace hz
+
+struct hz_ctx;
+namespace hz {
+// tensor-core GEMM (hz_tcgemm.cu): the split copy of operator block A (M x K,
+// leading dimension lda), built on first use
+const float *tc_split_operator(hz_ctx *c, const float2 *A, long long lda, int M, int K);
+long long atc_floats(int M, int K);
 }  // namespace hz
 
 struct hz_ctx {
@@ -128,6 +140,13 @@ struct hz_ctx {
     void *gemm_ws = nullptr;  // split-K partial tiles of the batched GEMM (sized for double2)
     float *wtc = nullptr;     // split TF32 W blocks of the tensor-core cell solve (null: SIMT cell solve)
     int *gemm_cnt = nullptr;  // split-K arrival counters (zero between launches)
+    float2 *tcg_ws = nullptr; // split-K partial tiles of the tensor-core GEMM (GEMM_TC_WS_TILES)
+    int *tcg_cnt = nullptr;   // its arrival counters
+    // TF32 split copies of the operator blocks the tensor-core GEMM reads, keyed by
+    // (block address, leading dimension, rows, columns), in device slabs
+    std::map<std::tuple<const void *, long long, int, int>, float *> tca;
+    std::vector<void *> tca_slabs;
+    size_t tca_used = 0, tca_cap = 0;
     // allocations
     std::map<void *, size_t> allocs;
     long long dev_bytes = 0;

@@ -579,14 +579,28 @@ template <class T2> struct ListBuilder {
     hz_ctx *c;
     Ops<T2> &o;
     std::vector<GemmProb<T2>> v;
-    int max_tiles = 0, kmax = 0;
+    int max_tiles = 0, kmax = 0, tc_max_tiles = 0, tc_kchunks = 0;
+    long long tc_tiles = 0;
     ListBuilder(hz_ctx *c_, Ops<T2> &o_) : c(c_), o(o_) {}
 
     double bytes = 0, flops = 0;
-    void push(const GemmProb<T2> &g) {
+    // the tensor-core GEMM reads the operators through their TF32 split copies
+    void tc_operands(GemmProb<float2> &g) {
+        g.Atc = g.A2tc = nullptr;
+        if (c->opts.tensor_cores < 2) return;
+        g.Atc = tc_split_operator(c, g.A, g.lda, g.M, g.K);
+        if (g.K2 > 0) g.A2tc = tc_split_operator(c, g.A2, g.lda2, g.M, g.K2);
+    }
+    void tc_operands(GemmProb<double2> &) {}
+    void push(GemmProb<T2> g) {
+        tc_operands(g);
         v.push_back(g);
         max_tiles = std::max(max_tiles, ((g.M + GBM - 1) / GBM) * ((g.N + GBN - 1) / GBN));
         kmax = std::max(kmax, std::max(g.K, 0) + std::max(g.K2, 0));
+        const int tct = ((g.M + GT_M - 1) / GT_M) * ((g.N + GT_N - 1) / GT_N);
+        tc_max_tiles = std::max(tc_max_tiles, tct);
+        tc_tiles += tct;
+        tc_kchunks = std::max(tc_kchunks, (std::max(g.K, 0) + GT_KC - 1) / GT_KC + (std::max(g.K2, 0) + GT_KC - 1) / GT_KC);
         const double es = sizeof(T2);
         const double K = (double)g.K + g.K2;
         bytes += es * ((double)g.M * K + K * g.N + (double)g.M * g.N * (g.beta ? 2 : 1));
@@ -675,6 +689,9 @@ template <class T2> struct ListBuilder {
         pl.n = (int)v.size();
         pl.max_tiles = max_tiles;
         pl.kmax = kmax;
+        pl.tc_max_tiles = tc_max_tiles;
+        pl.tc_kchunks = tc_kchunks;
+        pl.tc_tiles = tc_tiles;
         pl.bytes = bytes;
         pl.flops = flops;
         bytes = flops = 0;
@@ -683,7 +700,8 @@ template <class T2> struct ListBuilder {
             HZ_CU(cudaMemcpy(pl.d, v.data(), sizeof(GemmProb<T2>) * v.size(), cudaMemcpyHostToDevice));
         }
         v.clear();
-        max_tiles = kmax = 0;
+        max_tiles = kmax = tc_max_tiles = tc_kchunks = 0;
+        tc_tiles = 0;
         return pl;
     }
 };
@@ -696,8 +714,38 @@ static int gemm_split(long long tiles, int kmax) {
     return (int)std::max(1LL, std::min<long long>({8, s, kmax / 256}));  // >= 256 of K per split
 }
 
+// K slices per tile of the tensor-core GEMM: launches with few tiles take as many
+// slices as fit one CTA per SM in a single wave, at least 2 chunks of K per slice,
+// at most 8, within the workspace
+static int gemm_tc_split(const ProbList<float2> &pl) {
+    if (pl.tc_tiles * 2 > GEMM_TC_SPLIT_TILES || pl.tc_kchunks < 4) return 1;
+    const long long slots = (long long)pl.n * pl.tc_max_tiles;
+    const long long s = std::min<long long>({GEMM_TC_SPLIT_TILES / pl.tc_tiles, (long long)pl.tc_kchunks / 2, 8,
+                                             GEMM_TC_WS_TILES / std::max(1LL, slots)});
+    return (int)std::max(1LL, s);
+}
+
+static bool run_tc(hz_ctx *c, const ProbList<float2> &pl) {
+    if (c->opts.tensor_cores < 2) return false;
+    // small launches (a sweep step's F products: ~30 tiles x 9 chunks) stay on the SIMT
+    // kernel, whose fixed cost per launch is lower
+    if (pl.tc_tiles * pl.tc_kchunks < GEMM_TC_MIN_WORK) return false;
+    const int split = gemm_tc_split(pl);
+    if (split > 1 && !c->tcg_ws) {
+        c->tcg_ws = (float2 *)c->dalloc(sizeof(float2) * (size_t)GEMM_TC_WS_TILES * GT_M * GT_N);
+        c->tcg_cnt = (int *)c->dalloc(sizeof(int) * GEMM_TC_WS_TILES);
+        HZ_CU(cudaMemset(c->tcg_cnt, 0, sizeof(int) * GEMM_TC_WS_TILES));
+    }
+    c->kt_begin(2, pl.bytes, pl.flops);
+    launch_gemm_tc(pl.d, pl.n, pl.tc_max_tiles, split, c->tcg_ws, c->tcg_cnt, c->d_err, c->st, &c->nl);
+    c->kt_end();
+    return true;
+}
+static bool run_tc(hz_ctx *, const ProbList<double2> &) { return false; }
+
 template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
     if (!pl.n) return;
+    if (run_tc(c, pl)) return;
     const int split = gemm_split((long long)pl.n * pl.max_tiles, pl.kmax);
     if (split > 1 && !c->gemm_ws) {
         c->gemm_ws = c->dalloc(sizeof(double2) * 2 * GEMM_SPLIT_TILES * GBM * GBN);
@@ -998,6 +1046,7 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     ProbList<T2> sub = all;
     sub.d = all.d + W.hoff[l0];
     sub.n = W.hoff[l0 + nl] - W.hoff[l0];
+    sub.tc_tiles = (long long)sub.n * all.tc_max_tiles;
     sub.bytes = sub.flops = 0;
     for (int l = l0; l < l0 + nl; l++) {
         sub.bytes += W.hbytes[l] * (wide ? 2 : 1);

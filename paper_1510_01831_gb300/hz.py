@@ -158,7 +158,7 @@ class Context:
         o.device_ptrs = 1 if device_ptrs else 0
         o.stream = ctypes.c_void_p(stream) if stream else None
         o.time_kernels = 1 if time_kernels else 0
-        o.tensor_cores = 1 if tensor_cores else 0
+        o.tensor_cores = int(tensor_cores)  # False / True / 2 (cell solves and batched products)
         o.krylov = int(krylov)
         o.autotune = 1 if autotune else 0
         m = np.ascontiguousarray(m, dtype=np.float64)
