@@ -256,9 +256,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 if (!dead) umma_commit(su32(&done));
             }
-            // the rest of warp 0 waits here, not on the mbarrier below: a lane spinning on an
-            // mbarrier while the rest of its warp is suspended on another one stalls
-            if (warp == 0) __syncwarp();
             // global vector of this step's epilogue (forward: g of step s+1; backward: y of
             // step s), row m, loaded one 8-column quarter ahead of its use
             const int sg = fwd ? (s + 1 < nz ? s + 1 : -1) : s;
