@@ -195,7 +195,7 @@ def run_ours(args, rank, world):
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
                          tensor_cores=0 if args.no_tensor_cores else (2 if args.tc_gemm else 1), krylov=1 if args.krylov == "bicgstab" else 0,
-                         autotune=args.autotune, tol=args.tol, **kw)
+                         autotune=args.autotune, tol=args.tol, rhs_lanes=args.rhs_lanes, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
     t_factor = time.time() - t0
@@ -292,6 +292,8 @@ def run_ours(args, rank, world):
         "config": {"workload": f"{args.workload}: " + describe(wl, pbs, B, args.precision),
                    "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
                    "frequencies": len(pbs), "krylov": args.krylov, "autotune": args.autotune,
+                   "rhs_lanes": args.rhs_lanes, "tensor_cores": "off" if args.no_tensor_cores else
+                   ("cell solves + batched products" if args.tc_gemm else "cell solves"),
                    "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
         "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
         "solve": solve[0] if len(solve) == 1 else solve,
@@ -369,6 +371,8 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tensor-cores", action="store_true", help="mixed precision: cell solves on the SIMT pipes")
+    ap.add_argument("--rhs-lanes", type=int, default=1,
+                    help="solve the right-hand sides as this many groups in lockstep on separate streams")
     ap.add_argument("--tc-gemm", action="store_true",
                     help="mixed precision: batched F/E/S/W products with long K on the tensor cores too")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")

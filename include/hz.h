@@ -95,6 +95,12 @@ typedef struct {
                            SIMT pipes, at the cost of TF32 split copies of the
                            operators, twice their FP32 size in device memory);
                            0 keeps everything on the SIMT pipes */
+    int rhs_lanes;      /* hz_solve with B a multiple of rhs_lanes (> 1) splits the
+                           right-hand sides into rhs_lanes equal groups solved in
+                           lockstep, each on its own stream with its own
+                           workspaces but the context's factorization, so that
+                           the latency-bound sweep chains of the groups overlap on
+                           the GPU (1, the default: one group) */
 } hz_opts;
 
 typedef struct {

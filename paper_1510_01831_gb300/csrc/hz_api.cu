@@ -141,6 +141,7 @@ void hz_default_opts(hz_opts *o) {
     o->max_refine = 6;
     o->pml_C = 0.0;
     o->tensor_cores = 1;
+    o->rhs_lanes = 1;
 }
 
 hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega, double h, int n_pml, int L, int C,
@@ -172,6 +173,10 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     if (c->opts.krylov != HZ_GMRES && c->opts.krylov != HZ_BICGSTAB) {
         delete c;
         return fail(nullptr, HZ_EINVAL, "krylov must be HZ_GMRES or HZ_BICGSTAB");
+    }
+    if (c->opts.rhs_lanes < 1 || c->opts.rhs_lanes > 8) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "rhs_lanes must be 1..8");
     }
     if (c->opts.tensor_cores < 0 || c->opts.tensor_cores > 2) {
         delete c;
@@ -615,10 +620,23 @@ hz_status hz_set_device_ptrs(hz_ctx *c, int device_ptrs) {
     return HZ_OK;
 }
 
-long long hz_device_bytes(const hz_ctx *c) { return c ? c->dev_bytes : 0; }
+long long hz_device_bytes(const hz_ctx *c) {
+    if (!c) return 0;
+    long long b = c->dev_bytes;
+    for (const hz_ctx *s : c->lanes) b += s->dev_bytes;
+    return b;
+}
+
+static void destroy_one(hz_ctx *c);
 
 void hz_destroy(hz_ctx *c) {
     if (!c) return;
+    for (hz_ctx *s : c->lanes) destroy_one(s);  // lanes own only their streams and workspaces
+    c->lanes.clear();
+    destroy_one(c);
+}
+
+static void destroy_one(hz_ctx *c) {
     for (auto &kv : c->allocs) cudaFree(kv.first);
     c->kt_open.clear();
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -632,6 +650,7 @@ void hz_destroy(hz_ctx *c) {
         if (c->w32->hhost) cudaFreeHost(c->w32->hhost);
         if (c->w32->rhost) cudaFreeHost(c->w32->rhost);
     }
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }
 

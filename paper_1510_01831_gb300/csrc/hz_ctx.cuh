@@ -147,6 +147,13 @@ struct hz_ctx {
     std::map<std::tuple<const void *, long long, int, int>, float *> tca;
     std::vector<void *> tca_slabs;
     size_t tca_used = 0, tca_cap = 0;
+    bool tca_pending = false;  // split copies enqueued since the last stream synchronisation
+    // right-hand-side lanes (opts.rhs_lanes): contexts that share this one's
+    // decomposition, operators and split copies but own a stream, workspaces,
+    // error word and timers
+    std::vector<hz_ctx *> lanes;
+    hz_ctx *parent = nullptr;  // set on a lane
+    bool own_stream = false;
     // allocations
     std::map<void *, size_t> allocs;
     long long dev_bytes = 0;

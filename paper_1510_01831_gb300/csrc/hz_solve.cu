@@ -685,6 +685,10 @@ template <class T2> struct ListBuilder {
         }
     }
     ProbList<T2> finish() {
+        if (c->tca_pending) {  // split copies built on this stream are complete before any stream reads them
+            HZ_CU(cudaStreamSynchronize(c->st));
+            c->tca_pending = false;
+        }
         ProbList<T2> pl;
         pl.n = (int)v.size();
         pl.max_tiles = max_tiles;
@@ -1883,14 +1887,81 @@ template int solve_group_impl<double2>(const std::vector<hz_ctx *> &, const std:
 template int solve_group_impl<float2>(const std::vector<hz_ctx *> &, const std::vector<const double2 *> &, int,
                                       const std::vector<double2 *> &, std::vector<hz_stats> &, bool);
 
+// A lane of context c: shares c's decomposition, operators and split copies
+// (device pointers it does not own) and owns a non-blocking stream, its error
+// word and, on first use, its workspaces.
+static hz_ctx *make_lane(hz_ctx *c) {
+    hz_ctx *s = new hz_ctx();
+    s->n_x = c->n_x, s->n_z = c->n_z, s->p = c->p, s->L = c->L, s->C = c->C;
+    s->omega = c->omega, s->h = c->h, s->pml_C = c->pml_C, s->NX = c->NX, s->NZ = c->NZ;
+    s->opts = c->opts;
+    s->rows = c->rows, s->cols = c->cols;
+    s->factored = true;
+    s->cells = c->cells, s->layers = c->layers;
+    s->d_cells = c->d_cells, s->d_layers = c->d_layers, s->d_layer_ids = c->d_layer_ids;
+    s->tot_vol = c->tot_vol, s->tot_W = c->tot_W, s->tot_F = c->tot_F, s->tot_E = c->tot_E, s->tot_S = c->tot_S;
+    s->tot_K = c->tot_K, s->tot_inner = c->tot_inner, s->tot_Wi = c->tot_Wi, s->tot_P = c->tot_P;
+    s->tot_V = c->tot_V, s->max_nx = c->max_nx, s->max_nz = c->max_nz, s->max_no = c->max_no;
+    s->d_m = c->d_m, s->d_ax = c->d_ax, s->d_axh = c->d_axh, s->d_az = c->d_az, s->d_azh = c->d_azh;
+    s->d_gdiag = c->d_gdiag, s->d_gcx = c->d_gcx, s->d_gcz = c->d_gcz, s->d_gD = c->d_gD;
+    s->d_ginvD = c->d_ginvD, s->d_ggam = c->d_ggam, s->d_lbeta = c->d_lbeta, s->tot_z = c->tot_z;
+    s->d_gcell = c->d_gcell;
+    s->o64 = c->o64, s->o32 = c->o32;
+    s->wtc = c->wtc;
+    s->dev = c->dev;
+    s->parent = c;
+    HZ_CU(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
+    s->own_stream = true;
+    s->d_err = (int *)s->dalloc(sizeof(int));
+    HZ_CU(cudaMemset(s->d_err, 0, sizeof(int)));
+    return s;
+}
+
 // Full solve of one context: f (device, batch-outer [B][N]) -> u (device), stats.
+// With opts.rhs_lanes = S > 1 and B a multiple of S, the right-hand sides are
+// solved as S groups in lockstep, group 0 on the context, the others on lanes.
 template <class T2>
 int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st_out, bool scale_src) {
+    const int S = (c->opts.rhs_lanes > 1 && B % c->opts.rhs_lanes == 0) ? c->opts.rhs_lanes : 1;
+    std::vector<hz_ctx *> cs{c};
+    std::vector<const double2 *> fs{f_dev};
+    std::vector<double2 *> us{u_dev};
+    if (S > 1) {
+        while ((int)c->lanes.size() < S - 1) c->lanes.push_back(make_lane(c));
+        const long long N = (long long)c->NX * c->NZ, Bs = B / S;
+        HZ_CU(cudaStreamSynchronize(c->st));  // the staged inputs are complete before the lanes read them
+        for (int g = 1; g < S; g++) {
+            hz_ctx *s = c->lanes[g - 1];
+            s->opts.time_kernels = c->opts.time_kernels;
+            s->nl = 0;
+            s->kt_reset();
+            cs.push_back(s);
+            fs.push_back(f_dev + g * Bs * N);
+            us.push_back(u_dev + g * Bs * N);
+        }
+    }
     std::vector<hz_stats> sts;
-    int r = solve_group_impl<T2>({c}, {f_dev}, B, {u_dev}, sts, scale_src);
+    int r = solve_group_impl<T2>(cs, fs, B / S, us, sts, scale_src);
+    for (int g = 1; g < S; g++) {  // fold the lanes' launches and kernel timings into the context
+        hz_ctx *s = cs[g];
+        s->kt_collect();
+        c->nl += s->nl;
+        for (int i = 0; i < 3; i++) {
+            c->kt_launches[i] += s->kt_launches[i];
+            c->kt_ms[i] += s->kt_ms[i];
+            c->kt_bytes[i] += s->kt_bytes[i];
+            c->kt_flops[i] += s->kt_flops[i];
+        }
+    }
     if (st_out) {
         int keep = st_out->gpu_launches;
         *st_out = sts[0];
+        for (int g = 1; g < S; g++) {  // the worst group
+            st_out->iterations = std::max(st_out->iterations, sts[g].iterations);
+            st_out->refinements = std::max(st_out->refinements, sts[g].refinements);
+            st_out->resid = std::max(st_out->resid, sts[g].resid);
+            st_out->gmres_resid = std::max(st_out->gmres_resid, sts[g].gmres_resid);
+        }
         st_out->gpu_launches = keep;
     }
     return r;

@@ -453,8 +453,9 @@ long long atc_floats(int M, int K) {
 // Split copy of an operator block for the tensor-core GEMM, built on first use
 // and shared by every problem list of the context (keyed by the block's
 // address, leading dimension and extent); kept in device slabs of 256 MB.
-const float *tc_split_operator(hz_ctx *c, const float2 *A, long long lda, int M, int K) {
+const float *tc_split_operator(hz_ctx *c0, const float2 *A, long long lda, int M, int K) {
     if (!A || M <= 0 || K <= 0) return nullptr;
+    hz_ctx *c = c0->parent ? c0->parent : c0;  // lanes share their parent's copies
     const auto key = std::make_tuple((const void *)A, lda, M, K);
     auto it = c->tca.find(key);
     if (it != c->tca.end()) return it->second;
@@ -470,8 +471,9 @@ const float *tc_split_operator(hz_ctx *c, const float2 *A, long long lda, int M,
     float *dst = reinterpret_cast<float *>(static_cast<char *>(c->tca_slabs.back()) + c->tca_used);
     c->tca_used += need;
     const long long blocks = std::min<long long>(4096, (nf / 4 + 255) / 256);
-    k_build_atc<<<(int)std::max(1LL, blocks), 256, 0, c->st>>>(A, lda, M, K, dst);
+    k_build_atc<<<(int)std::max(1LL, blocks), 256, 0, c0->st>>>(A, lda, M, K, dst);
     HZ_CU(cudaGetLastError());
+    c0->tca_pending = true;  // the list builder synchronises before the copy is shared
     c->tca[key] = dst;
     return dst;
 }

@@ -45,7 +45,8 @@ class HzOpts(ctypes.Structure):
                 ("max_refine", ctypes.c_int), ("pml_C", ctypes.c_double),
                 ("layer_rows", ctypes.POINTER(ctypes.c_int)), ("cell_cols", ctypes.POINTER(ctypes.c_int)),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
-                ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("rhs_lanes", ctypes.c_int)]
 
 
 class HzStats(ctypes.Structure):
@@ -142,7 +143,8 @@ class Context:
 
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
-                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False):
+                 cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False,
+                 rhs_lanes=1):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -161,6 +163,7 @@ class Context:
         o.tensor_cores = int(tensor_cores)  # False / True / 2 (cell solves and batched products)
         o.krylov = int(krylov)
         o.autotune = 1 if autotune else 0
+        o.rhs_lanes = int(rhs_lanes)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")

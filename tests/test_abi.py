@@ -117,3 +117,14 @@ def test_setup_rejects_unknown_tensor_core_mode():
     h_ = ctypes.c_void_p()
     assert lib.hz_setup(ctypes.byref(h_), m.ctypes.data, 8, 8, 10.0, 0.1, 2, 2, 2, ctypes.byref(o)) == hz.HZ_EINVAL
     assert b"tensor_cores" in lib.hz_last_error(None)
+
+
+def test_setup_rejects_bad_lane_count():
+    lib = hz.load()
+    m = np.ones((12, 12))
+    o = hz.hz_default_opts()
+    assert o.rhs_lanes == 1
+    o.rhs_lanes = 0
+    h_ = ctypes.c_void_p()
+    assert lib.hz_setup(ctypes.byref(h_), m.ctypes.data, 8, 8, 10.0, 0.1, 2, 2, 2, ctypes.byref(o)) == hz.HZ_EINVAL
+    assert b"rhs_lanes" in lib.hz_last_error(None)
