@@ -182,6 +182,23 @@ hz_status hz_gradient(hz_ctx *ctx, const double *f, int B, const double *d,
                       const int *rec_idx, int n_rec, double *J, double *grad_m,
                       double *u_out, hz_stats *st);
 
+/* Local model update (paper, Conclusion: a medium updated locally inside an
+ * inversion loop needs only a local modification of the method): replace the
+ * medium by m_new and re-factor only the layers with a cell whose box reads a
+ * changed value (the cell operators, their Green's blocks F / E / S and the
+ * layer's inner block LU; the other layers' operators stay as they are),
+ * plus the global residual coefficients.  The result is the factorization
+ * hz_factor computes for m_new (same kernels on the same data); the PML
+ * strength stays the one fixed at hz_setup.
+ *   m_new      : [n_z+2p][n_x+2p] squared slowness, host pointer always,
+ *                finite and positive;
+ *   n_layers   : NULL or out: how many layers were re-factored (0 when m_new
+ *                equals the current medium).
+ * Errors: HZ_EINVAL (NULL, non-finite or non-positive m_new), HZ_ESTATE (before
+ * hz_factor), HZ_ENOMEM, HZ_ECUDA; on an error after validation the context
+ * must be destroyed. */
+hz_status hz_update_model(hz_ctx *ctx, const double *m_new, int *n_layers);
+
 /* Adjoint of hz_solve for an arbitrary real loss L(u) (not in the paper; the
  * differentiation pattern of the solver): with gu = dL/dRe(u) + i dL/dIm(u)
  * (PyTorch's gradient convention for complex tensors),

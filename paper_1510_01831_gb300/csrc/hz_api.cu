@@ -226,6 +226,7 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     hz_status s = guarded(c, [&]() -> hz_status {
         c->d_m = (double *)c->dalloc(sizeof(double) * N);
         HZ_CU(cudaMemcpy(c->d_m, m, sizeof(double) * N, cudaMemcpyHostToDevice));
+        c->h_m.assign(m, m + N);
         hz::build_decomposition(c);
         hz::init_global_alpha(c);
         return HZ_OK;
@@ -246,6 +247,58 @@ hz_status hz_factor(hz_ctx *c) {
     return guarded(c, [&]() -> hz_status {
         hz::factor_all(c);
         c->factored = true;
+        return HZ_OK;
+    });
+}
+
+hz_status hz_update_model(hz_ctx *c, const double *m_new, int *n_layers) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    if (!m_new) return fail(c, HZ_EINVAL, "m_new must be non-NULL");
+    if (!c->factored) return fail(c, HZ_ESTATE, "hz_update_model before hz_factor");
+    const int NX = c->NX, NZ = c->NZ;
+    const long long N = (long long)NX * NZ;
+    for (long long i = 0; i < N; i++)
+        if (!std::isfinite(m_new[i]) || m_new[i] <= 0) return fail(c, HZ_EINVAL, "m_new must be finite and positive");
+    c->nl = 0;
+    return guarded(c, [&]() -> hz_status {
+        // changed points, as a 2D prefix count: a cell is touched when its read box holds one
+        std::vector<long long> cnt((size_t)(NZ + 1) * (NX + 1), 0);
+        long long changed = 0;
+        for (int z = 0; z < NZ; z++)
+            for (int x = 0; x < NX; x++) {
+                const int d = m_new[(long long)z * NX + x] != c->h_m[(long long)z * NX + x];
+                changed += d;
+                cnt[(size_t)(z + 1) * (NX + 1) + x + 1] = d + cnt[(size_t)z * (NX + 1) + x + 1] +
+                                                          cnt[(size_t)(z + 1) * (NX + 1) + x] - cnt[(size_t)z * (NX + 1) + x];
+            }
+        auto box = [&](int z0, int z1, int x0, int x1) {  // changed points in rows [z0, z1], columns [x0, x1]
+            return cnt[(size_t)(z1 + 1) * (NX + 1) + x1 + 1] - cnt[(size_t)z0 * (NX + 1) + x1 + 1] -
+                   cnt[(size_t)(z1 + 1) * (NX + 1) + x0] + cnt[(size_t)z0 * (NX + 1) + x0];
+        };
+        std::vector<int> lays;
+        if (changed) {
+            const int p = c->p;
+            for (int l = 0; l < c->L; l++) {
+                bool touched = false;
+                for (int cc = 0; cc < c->C && !touched; cc++) {
+                    // the grid points the cell's coefficients read (its box, with the
+                    // neighbour sides clamped to the interior as in the coefficient kernel)
+                    const hz::CellDesc &cd = c->cells[c->layers[l].cell0 + cc];
+                    const int z0 = cd.top ? cd.s + p : cd.s, z1 = cd.bot ? cd.s + cd.n + p - 1 : cd.s + cd.nz - 1;
+                    const int x0 = cd.left ? cd.t + p : cd.t, x1 = cd.right ? cd.t + cd.w + p - 1 : cd.t + cd.nx - 1;
+                    touched = box(z0, z1, x0, x1) > 0;
+                }
+                if (touched) lays.push_back(l);
+            }
+            HZ_CU(cudaMemcpy(c->d_m, m_new, sizeof(double) * N, cudaMemcpyHostToDevice));
+            c->h_m.assign(m_new, m_new + N);
+            hz::launch_cell_coeffs(c->d_gcell, 1, c->d_m, NX, c->omega, c->h, c->pml_C, c->p, c->d_gdiag, c->d_gcx,
+                                   c->d_gcz, c->st, &c->nl);
+            hz::factor_layers(c, lays, false);
+            if (c->mixed() && c->opts.tensor_cores == 2) hz::tc_refresh_operators(c);
+            HZ_CU(cudaStreamSynchronize(c->st));
+        }
+        if (n_layers) *n_layers = (int)lays.size();
         return HZ_OK;
     });
 }

@@ -78,6 +78,7 @@ namespace hz {
 // tensor-core GEMM (hz_tcgemm.cu): the split copy of operator block A (M x K,
 // leading dimension lda), built on first use
 const float *tc_split_operator(hz_ctx *c, const float2 *A, long long lda, int M, int K);
+void tc_refresh_operators(hz_ctx *c);  // rebuild every split copy from the current operators
 long long atc_floats(int M, int K);
 }  // namespace hz
 
@@ -102,6 +103,7 @@ struct hz_ctx {
     long long tot_inner = 0, tot_Wi = 0, tot_P = 0, tot_V = 0;
     int max_nx = 0, max_nz = 0, max_no = 0;
     // global medium and PML profiles (FP64)
+    std::vector<double> h_m;  // host copy of the medium (local model updates compare against it)
     double *d_m = nullptr;
     double2 *d_ax = nullptr, *d_axh = nullptr, *d_az = nullptr, *d_azh = nullptr;
     // row-scaled global operator: diagonal, +x and +z couplings, and alpha_x alpha_z (FP64)
@@ -167,6 +169,7 @@ struct hz_ctx {
 namespace hz {
 void build_decomposition(hz_ctx *c);
 void factor_all(hz_ctx *c);
+void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first);
 void init_global_alpha(hz_ctx *c);
 template <class T2> int solve_impl(hz_ctx *c, const double2 *f_dev, int B, double2 *u_dev, hz_stats *st, bool scale_src);
 template <class T2>

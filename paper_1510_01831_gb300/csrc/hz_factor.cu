@@ -282,37 +282,63 @@ static void check_info(int *d_info, cudaStream_t st, const char *what) {
 template <class T2> static T2 *alloc_n(hz_ctx *c, long long n) { return (T2 *)c->dalloc(sizeof(T2) * std::max(n, 1LL)); }
 
 // ---------------------------------------------------------- factor ---
-void factor_all(hz_ctx *c) {
+// Factorization of the layers in `lays` (all layers on the first call, from
+// hz_factor; the layers whose cells read a changed medium on a local update,
+// from hz_update_model).  Every stage below works on those layers' cells only
+// and writes the operators in place at their global offsets, so a local update
+// leaves the other layers' operators exactly as they were.
+void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
     cudaStream_t st = c->st;
     int *nl = &c->nl;
-    const int p = c->p, L = c->L;
-    const int ncell = (int)c->cells.size();
+    const int p = c->p, C = c->C;
+    const int nlay = (int)lays.size();
+    if (nlay == 0) return;
+    std::vector<CellDesc> sub;
+    std::vector<LayerDesc> lsub;
+    for (int l : lays) {
+        lsub.push_back(c->layers[l]);
+        for (int cc = 0; cc < C; cc++) sub.push_back(c->cells[c->layers[l].cell0 + cc]);
+    }
+    const int nsub = (int)sub.size();
+    CellDesc *d_sub = (CellDesc *)c->dalloc(sizeof(CellDesc) * nsub);
+    HZ_CU(cudaMemcpyAsync(d_sub, sub.data(), sizeof(CellDesc) * nsub, cudaMemcpyHostToDevice, st));
+    LayerDesc *d_lsub = (LayerDesc *)c->dalloc(sizeof(LayerDesc) * nlay);
+    HZ_CU(cudaMemcpyAsync(d_lsub, lsub.data(), sizeof(LayerDesc) * nlay, cudaMemcpyHostToDevice, st));
     int *d_info = (int *)c->dalloc(sizeof(int));
     HZ_CU(cudaMemsetAsync(d_info, 0, sizeof(int), st));
+    const bool mixed = c->mixed();
+    // FP64 operators: the context's own in FP64 mode, full-size temporaries in mixed mode
+    auto fp64_buf = [&](double2 *&keep, long long n, bool zero) {
+        if (!mixed && !first) return keep;
+        double2 *q = alloc_n<double2>(c, n);
+        if (zero) HZ_CU(cudaMemsetAsync(q, 0, sizeof(double2) * std::max(n, 1LL), st));
+        if (!mixed) keep = q;
+        return q;
+    };
 
     // 1. cell operators (row-scaled form) and block-tridiagonal inverses
     double2 *diag = alloc_n<double2>(c, c->tot_vol), *cxv = alloc_n<double2>(c, c->tot_vol);
-    double2 *czv = alloc_n<double2>(c, c->tot_vol);
-    launch_cell_coeffs(c->d_cells, ncell, c->d_m, c->NX, c->omega, c->h, c->pml_C, p, diag, cxv, czv, st, nl);
-    double2 *cellW = alloc_n<double2>(c, c->tot_W);
-    HZ_CU(cudaMemsetAsync(cellW, 0, sizeof(double2) * c->tot_W, st));  // row padding stays zero
-    launch_cell_factor(c->d_cells, ncell, diag, cxv, czv, cellW, c->max_nx, d_info, st, nl);
+    double2 *czv = fp64_buf(c->o64.cz, c->tot_vol, false);
+    launch_cell_coeffs(d_sub, nsub, c->d_m, c->NX, c->omega, c->h, c->pml_C, p, diag, cxv, czv, st, nl);
+    double2 *cellW = fp64_buf(c->o64.cellW, c->tot_W, true);  // row padding stays zero
+    launch_cell_factor(d_sub, nsub, diag, cxv, czv, cellW, c->max_nx, d_info, st, nl);
     check_info(d_info, st, "cell factorization");
     c->dfree(diag);
     c->dfree(cxv);
 
     // 2. Green's blocks from unit-source cell solves, in groups of cells
-    double2 *K = alloc_n<double2>(c, c->tot_K), *F = alloc_n<double2>(c, c->tot_F);
-    double2 *E = alloc_n<double2>(c, c->tot_E), *S = alloc_n<double2>(c, c->tot_S);
+    double2 *K = alloc_n<double2>(c, c->tot_K);
+    double2 *F = fp64_buf(c->o64.F, c->tot_F, false), *E = fp64_buf(c->o64.E, c->tot_E, false);
+    double2 *S = fp64_buf(c->o64.S, c->tot_S, false);
     {
         const long long budget = 3LL << 30;  // bytes of solution buffer per group
         int i0 = 0;
-        while (i0 < ncell) {
+        while (i0 < nsub) {
             int Bg = 0;
             long long pts = 0;
             int i1 = i0;
-            while (i1 < ncell) {
-                const CellDesc &cd = c->cells[i1];
+            while (i1 < nsub) {
+                const CellDesc &cd = sub[i1];
                 int nb = 4 * cd.nz + 4 * cd.no;
                 int Bn = std::max(Bg, nb);
                 long long ptsn = pts + (long long)cd.nx * cd.nz;
@@ -321,7 +347,7 @@ void factor_all(hz_ctx *c) {
                 pts = ptsn;
                 i1++;
             }
-            std::vector<CellDesc> grp(c->cells.begin() + i0, c->cells.begin() + i1);
+            std::vector<CellDesc> grp(sub.begin() + i0, sub.begin() + i1);
             long long off = 0;
             for (auto &cd : grp) {
                 cd.vol_off = off;
@@ -349,29 +375,28 @@ void factor_all(hz_ctx *c) {
 
     // 3. inner block LU per layer: S_j = A_j - [Z_j V_{j-1}; 0], W_j = S_j^{-1},
     //    V_j = W_j(:, nz:2nz) K_{j+1}(1-rows, x_{j+1} part)
-    double2 *Wi = alloc_n<double2>(c, c->tot_Wi), *Zi = alloc_n<double2>(c, c->tot_P);
-    double2 *Pm = alloc_n<double2>(c, c->tot_P), *Vi = alloc_n<double2>(c, c->tot_V);
-    const int C = c->C;
+    double2 *Wi = fp64_buf(c->o64.W, c->tot_Wi, false), *Zi = alloc_n<double2>(c, c->tot_P);
+    double2 *Pm = fp64_buf(c->o64.P, c->tot_P, false), *Vi = fp64_buf(c->o64.V, c->tot_V, false);
     if (C > 1) {
-        GemmProb<double2> *d_pr = (GemmProb<double2> *)c->dalloc(sizeof(GemmProb<double2>) * L);
-        double2 **d_mats = (double2 **)c->dalloc(sizeof(double2 *) * L);
-        int *d_ns = (int *)c->dalloc(sizeof(int) * L);
-        std::vector<GemmProb<double2>> pr(L);
-        std::vector<double2 *> mats(L);
-        std::vector<int> ns(L);
+        GemmProb<double2> *d_pr = (GemmProb<double2> *)c->dalloc(sizeof(GemmProb<double2>) * nlay);
+        double2 **d_mats = (double2 **)c->dalloc(sizeof(double2 *) * nlay);
+        int *d_ns = (int *)c->dalloc(sizeof(int) * nlay);
+        std::vector<GemmProb<double2>> pr(nlay);
+        std::vector<double2 *> mats(nlay);
+        std::vector<int> ns(nlay);
         int maxn2 = 0;
-        for (int l = 0; l < L; l++) maxn2 = std::max(maxn2, 2 * c->layers[l].nz);
+        for (const LayerDesc &ld : lsub) maxn2 = std::max(maxn2, 2 * ld.nz);
         for (int j = 0; j < C - 1; j++) {
-            k_inner_diag<<<dim3(64, L), 256, 0, st>>>(c->d_layers, c->d_cells, K, Wi, j);
+            k_inner_diag<<<dim3(64, nlay), 256, 0, st>>>(d_lsub, c->d_cells, K, Wi, j);
             HZ_CU(cudaGetLastError());
             (*nl)++;
-            k_inner_z<<<dim3(64, L), 256, 0, st>>>(c->d_layers, c->d_cells, K, Zi, j);
+            k_inner_z<<<dim3(64, nlay), 256, 0, st>>>(d_lsub, c->d_cells, K, Zi, j);
             HZ_CU(cudaGetLastError());
             (*nl)++;
             if (j > 0) {  // S_j(a-rows) -= Z_j V_{j-1}
                 int mt = 0;
-                for (int l = 0; l < L; l++) {
-                    const LayerDesc &ld = c->layers[l];
+                for (int q = 0; q < nlay; q++) {
+                    const LayerDesc &ld = lsub[q];
                     const int nz = ld.nz, n2 = 2 * nz;
                     GemmProb<double2> g{};
                     g.A = Zi + ld.P_off + (long long)j * n2 * n2;
@@ -386,25 +411,25 @@ void factor_all(hz_ctx *c) {
                     g.ldy = n2;
                     g.beta = 1;
                     g.alpha = -1.f;
-                    pr[l] = g;
+                    pr[q] = g;
                     mt = std::max(mt, ((nz + 63) / 64) * ((n2 + 31) / 32));
                 }
-                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
+                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * nlay, cudaMemcpyHostToDevice, st));
+                launch_gemm<double2>(d_pr, nlay, mt, 1, nullptr, nullptr, st, nl);
             }
-            for (int l = 0; l < L; l++) {
-                const LayerDesc &ld = c->layers[l];
+            for (int q = 0; q < nlay; q++) {
+                const LayerDesc &ld = lsub[q];
                 const long long n2 = 2LL * ld.nz;
-                mats[l] = Wi + ld.W_off + j * n2 * n2;
-                ns[l] = (int)n2;
+                mats[q] = Wi + ld.W_off + j * n2 * n2;
+                ns[q] = (int)n2;
             }
-            HZ_CU(cudaMemcpyAsync(d_mats, mats.data(), sizeof(double2 *) * L, cudaMemcpyHostToDevice, st));
-            HZ_CU(cudaMemcpyAsync(d_ns, ns.data(), sizeof(int) * L, cudaMemcpyHostToDevice, st));
-            launch_gj_inverse(d_mats, d_ns, L, maxn2, d_info, st, nl);
+            HZ_CU(cudaMemcpyAsync(d_mats, mats.data(), sizeof(double2 *) * nlay, cudaMemcpyHostToDevice, st));
+            HZ_CU(cudaMemcpyAsync(d_ns, ns.data(), sizeof(int) * nlay, cudaMemcpyHostToDevice, st));
+            launch_gj_inverse(d_mats, d_ns, nlay, maxn2, d_info, st, nl);
             if (j > 0) {  // P_j = W_j(:, 0:nz) Z_j: the forward sweep becomes y_j = W_j g_j + P_j y_{j-1}
                 int mt = 0;
-                for (int l = 0; l < L; l++) {
-                    const LayerDesc &ld = c->layers[l];
+                for (int q = 0; q < nlay; q++) {
+                    const LayerDesc &ld = lsub[q];
                     const int nz = ld.nz, n2 = 2 * nz;
                     GemmProb<double2> g{};
                     g.A = Wi + ld.W_off + (long long)j * n2 * n2;
@@ -419,18 +444,18 @@ void factor_all(hz_ctx *c) {
                     g.ldy = n2;
                     g.beta = 0;
                     g.alpha = 1.f;
-                    pr[l] = g;
+                    pr[q] = g;
                     mt = std::max(mt, ((n2 + 63) / 64) * ((n2 + 31) / 32));
                 }
                 HZ_CU(cudaStreamSynchronize(st));  // pr is reused below
-                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
+                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * nlay, cudaMemcpyHostToDevice, st));
+                launch_gemm<double2>(d_pr, nlay, mt, 1, nullptr, nullptr, st, nl);
                 HZ_CU(cudaStreamSynchronize(st));
             }
             if (j < C - 2) {  // V_j = W_j(:, nz:) K_{j+1}(1-rows, right part)
                 int mt = 0;
-                for (int l = 0; l < L; l++) {
-                    const LayerDesc &ld = c->layers[l];
+                for (int q = 0; q < nlay; q++) {
+                    const LayerDesc &ld = lsub[q];
                     const int nz = ld.nz, n2 = 2 * nz;
                     const CellDesc &cb = c->cells[ld.cell0 + j + 1];
                     GemmProb<double2> g{};
@@ -446,11 +471,11 @@ void factor_all(hz_ctx *c) {
                     g.ldy = n2;
                     g.beta = 0;
                     g.alpha = 1.f;
-                    pr[l] = g;
+                    pr[q] = g;
                     mt = std::max(mt, ((n2 + 63) / 64) * ((n2 + 31) / 32));
                 }
-                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * L, cudaMemcpyHostToDevice, st));
-                launch_gemm<double2>(d_pr, L, mt, 1, nullptr, nullptr, st, nl);
+                HZ_CU(cudaMemcpyAsync(d_pr, pr.data(), sizeof(GemmProb<double2>) * nlay, cudaMemcpyHostToDevice, st));
+                launch_gemm<double2>(d_pr, nlay, mt, 1, nullptr, nullptr, st, nl);
             }
             HZ_CU(cudaStreamSynchronize(st));  // host vectors reused next step
         }
@@ -462,52 +487,72 @@ void factor_all(hz_ctx *c) {
     c->dfree(K);
     c->dfree(Zi);
 
-    // 4. keep the operators in the working precision
-    if (!c->mixed()) {
-        c->o64.cellW = cellW;
-        c->o64.cz = czv;
-        c->o64.F = F;
-        c->o64.E = E;
-        c->o64.S = S;
-        c->o64.W = Wi;
-        c->o64.P = Pm;
-        c->o64.V = Vi;
-    } else {
+    // 4. mixed precision: the working-precision copies of these layers' operators
+    if (mixed) {
         auto &o = c->o32;
-        o.cellW = alloc_n<float2>(c, c->tot_W);
-        to_f32(cellW, o.cellW, c->tot_W, st, nl);
+        if (first) {
+            o.cellW = alloc_n<float2>(c, c->tot_W);
+            o.cz = alloc_n<float2>(c, c->tot_vol);
+            o.F = alloc_n<float2>(c, c->tot_F);
+            o.E = alloc_n<float2>(c, c->tot_E);
+            o.S = alloc_n<float2>(c, c->tot_S);
+            o.W = alloc_n<float2>(c, c->tot_Wi);
+            o.P = alloc_n<float2>(c, c->tot_P);
+            o.V = alloc_n<float2>(c, c->tot_V);
+            to_f32(cellW, o.cellW, c->tot_W, st, nl);
+            to_f32(czv, o.cz, c->tot_vol, st, nl);
+            to_f32(F, o.F, c->tot_F, st, nl);
+            to_f32(E, o.E, c->tot_E, st, nl);
+            to_f32(S, o.S, c->tot_S, st, nl);
+            to_f32(Wi, o.W, c->tot_Wi, st, nl);
+            to_f32(Pm, o.P, c->tot_P, st, nl);
+            to_f32(Vi, o.V, c->tot_V, st, nl);
+        } else {
+            for (const CellDesc &cd : sub) {
+                const long long nb = (long long)cd.nz * cd.nx * cd.ldw;
+                to_f32(cellW + cd.w_off, o.cellW + cd.w_off, nb, st, nl);
+                to_f32(czv + cd.cz_off, o.cz + cd.cz_off, (long long)cd.nx * cd.nz, st, nl);
+                to_f32(F + cd.F_off, o.F + cd.F_off, 8LL * cd.nz * cd.no, st, nl);
+                to_f32(E + cd.E_off, o.E + cd.E_off, 16LL * cd.no * cd.nz, st, nl);
+                to_f32(S + cd.S_off, o.S + cd.S_off, 16LL * cd.no * cd.no, st, nl);
+            }
+            for (const LayerDesc &ld : lsub) {
+                const long long n2 = 2LL * ld.nz, nb = (long long)std::max(C - 1, 0) * n2 * n2;
+                to_f32(Wi + ld.W_off, o.W + ld.W_off, nb, st, nl);
+                to_f32(Pm + ld.P_off, o.P + ld.P_off, nb, st, nl);
+                to_f32(Vi + ld.V_off, o.V + ld.V_off, nb, st, nl);
+            }
+        }
         if (c->opts.tensor_cores && c->max_nx <= 128) {
             // split TF32 copy of the cell blocks for the tensor-core cell solve
-            long long off = 0;
-            for (CellDesc &cd : c->cells) {
-                cd.tc_off = off;
-                off += cell_tc_floats(cd.nx, cd.nz);
+            if (first) {
+                long long off = 0;
+                for (CellDesc &cd : c->cells) {
+                    cd.tc_off = off;
+                    off += cell_tc_floats(cd.nx, cd.nz);
+                }
+                HZ_CU(cudaMemcpyAsync(c->d_cells, c->cells.data(), sizeof(CellDesc) * c->cells.size(),
+                                      cudaMemcpyHostToDevice, st));
+                c->wtc = (float *)c->dalloc(sizeof(float) * std::max(off, 1LL));
+                build_wtc(c->d_cells, (int)c->cells.size(), cellW, c->wtc, st, nl);
+            } else {
+                build_wtc(d_sub, nsub, cellW, c->wtc, st, nl);  // (sub carries the cells' tc_off)
             }
-            HZ_CU(cudaMemcpyAsync(c->d_cells, c->cells.data(), sizeof(CellDesc) * c->cells.size(),
-                                  cudaMemcpyHostToDevice, st));
-            c->wtc = (float *)c->dalloc(sizeof(float) * std::max(off, 1LL));
-            build_wtc(c->d_cells, ncell, cellW, c->wtc, st, nl);
         }
-        o.cz = alloc_n<float2>(c, c->tot_vol);
-        to_f32(czv, o.cz, c->tot_vol, st, nl);
-        o.F = alloc_n<float2>(c, c->tot_F);
-        to_f32(F, o.F, c->tot_F, st, nl);
-        o.E = alloc_n<float2>(c, c->tot_E);
-        to_f32(E, o.E, c->tot_E, st, nl);
-        o.S = alloc_n<float2>(c, c->tot_S);
-        to_f32(S, o.S, c->tot_S, st, nl);
-        o.W = alloc_n<float2>(c, c->tot_Wi);
-        to_f32(Wi, o.W, c->tot_Wi, st, nl);
-        o.P = alloc_n<float2>(c, c->tot_P);
-        to_f32(Pm, o.P, c->tot_P, st, nl);
-        o.V = alloc_n<float2>(c, c->tot_V);
-        to_f32(Vi, o.V, c->tot_V, st, nl);
         HZ_CU(cudaStreamSynchronize(st));
         for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi})
             c->dfree(q);
     }
     c->dfree(d_info);
+    c->dfree(d_sub);
+    c->dfree(d_lsub);
     HZ_CU(cudaStreamSynchronize(st));
+}
+
+void factor_all(hz_ctx *c) {
+    std::vector<int> all(c->L);
+    for (int l = 0; l < c->L; l++) all[l] = l;
+    factor_layers(c, all, true);
 }
 
 }  // namespace hz

@@ -478,6 +478,18 @@ const float *tc_split_operator(hz_ctx *c0, const float2 *A, long long lda, int M
     return dst;
 }
 
+void tc_refresh_operators(hz_ctx *c) {
+    for (auto &kv : c->tca) {
+        const float2 *A = static_cast<const float2 *>(std::get<0>(kv.first));
+        const long long lda = std::get<1>(kv.first);
+        const int M = std::get<2>(kv.first), K = std::get<3>(kv.first);
+        const long long nf = atc_floats(M, K);
+        const long long blocks = std::min<long long>(4096, (nf / 4 + 255) / 256);
+        k_build_atc<<<(int)std::max(1LL, blocks), 256, 0, c->st>>>(A, lda, M, K, kv.second);
+        HZ_CU(cudaGetLastError());
+    }
+}
+
 void launch_gemm_tc(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int split, float2 *ws, int *cnt,
                     int *err, cudaStream_t st, int *nl) {
     if (nprob <= 0 || max_tiles <= 0) return;

@@ -27,7 +27,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
                 "HZ_ESINGULAR"]
 
 # every entry point declared in include/hz.h
-EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve",
+EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_update_model", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve",
            "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
            "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
             L.hz_default_opts.restype = None
             L.hz_setup.argtypes = [P(vp), vp, i, i, d, d, i, i, i, P(HzOpts)]
             L.hz_factor.argtypes = [vp]
+            L.hz_update_model.argtypes = [vp, vp, P(i)]
             L.hz_solve.argtypes = [vp, vp, i, vp, P(HzStats)]
             L.hz_solve_group.argtypes = [P(vp), i, P(vp), i, P(vp), P(HzStats)]
             L.hz_gradient.argtypes = [vp, vp, i, vp, vp, i, P(d), vp, vp, P(HzStats)]
@@ -208,6 +209,15 @@ class Context:
     # -- calls --
     def hz_factor(self):
         _check(load().hz_factor(self._ctx), self._ctx)
+
+    def hz_update_model(self, m_new) -> int:
+        """Replace the medium (host array, extended grid) and re-factor the touched layers; returns their count."""
+        m_new = np.ascontiguousarray(m_new, dtype=np.float64)
+        if m_new.shape != (self.NZ, self.NX):
+            raise ValueError(f"m_new has shape {m_new.shape}, expected {(self.NZ, self.NX)}")
+        n = ctypes.c_int(0)
+        _check(load().hz_update_model(self._ctx, m_new.ctypes.data, ctypes.byref(n)), self._ctx)
+        return n.value
 
     def hz_solve(self, f, u=None):
         f = self._in(f)

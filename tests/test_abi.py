@@ -90,6 +90,7 @@ def test_null_context_calls_fail_cleanly():
     lib = hz.load()
     assert lib.hz_factor(None) == hz.HZ_EINVAL
     assert lib.hz_solve(None, None, 1, None, None) == hz.HZ_EINVAL
+    assert lib.hz_update_model(None, None, None) == hz.HZ_EINVAL
     assert lib.hz_device_bytes(None) == 0
     lib.hz_destroy(None)
     assert lib.hz_solve_group(None, 1, None, 1, None, None) == hz.HZ_EINVAL
