@@ -302,6 +302,21 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)},
         "clocks": clk.summary(),
     }
+    if args.measure_update:
+        # local model update outside the timed region: a patch of the medium inside one
+        # cell of the middle layer changes; only that layer is re-factored
+        pb0, ctx0 = pbs[0], ctxs[0]
+        rows = pb0.layer_rows if pb0.layer_rows is not None else [pb0.n_z // pb0.L] * pb0.L
+        z0 = pb0.n_pml + sum(rows[:pb0.L // 2]) + rows[pb0.L // 2] // 4
+        x0 = pb0.n_pml + pb0.n_x // (2 * pb0.C)
+        m1 = pb0.m.copy()
+        m1[z0:z0 + 8, x0:x0 + 8] *= 1.05
+        torch.cuda.synchronize()
+        t1 = time.time()
+        nlay = ctx0.hz_update_model(m1)
+        t_upd = time.time() - t1
+        out["local_update"] = {"layers_refactored": nlay, "layers": pb0.L, "t_update_s": round(t_upd, 3),
+                               "t_factor_s": round(t_factor / len(ctxs), 3), "patch": "8 x 8 points, m x 1.05"}
     for c in ctxs:
         c.close()
     return out
@@ -371,6 +386,8 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tensor-cores", action="store_true", help="mixed precision: cell solves on the SIMT pipes")
+    ap.add_argument("--measure-update", action="store_true",
+                    help="after the timed steps, time a local model update of one patch (reported, not timed)")
     ap.add_argument("--rhs-lanes", type=int, default=1,
                     help="solve the right-hand sides as this many groups in lockstep on separate streams")
     ap.add_argument("--tc-gemm", action="store_true",
