@@ -1061,7 +1061,9 @@ static bool inner_sweep_staged(const LayerDesc *d_layers, const int *ids, int nl
 struct SweepCand {
     int nbt, rw, R;
 };
-static const SweepCand kSweepCands[] = {{8, 2, 16}, {16, 2, 16}, {8, 4, 16}, {8, 2, 8}, {16, 2, 8}, {8, 4, 8}};
+static const SweepCand kSweepCands[] = {{8, 2, 16}, {16, 2, 16}, {8, 4, 16}, {8, 2, 8}, {16, 2, 8}, {8, 4, 8},
+                                        {4, 4, 8},  {4, 8, 8},   {4, 2, 16}, {4, 4, 16}, {2, 4, 8},  {2, 8, 8},
+                                        {2, 4, 16}};
 constexpr int kNumSweepCands = (int)(sizeof(kSweepCands) / sizeof(kSweepCands[0]));
 
 template <class T2>
@@ -1074,6 +1076,16 @@ static bool sweep_cand(int i, const LayerDesc *d_layers, const int *ids, int nla
         return inner_sweep_staged<T2, 16, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
     if (k.nbt == 8 && k.rw == 4)
         return inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 4 && k.rw == 2)
+        return inner_sweep_staged<T2, 4, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 4 && k.rw == 4)
+        return inner_sweep_staged<T2, 4, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 4 && k.rw == 8)
+        return inner_sweep_staged<T2, 4, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 2 && k.rw == 4)
+        return inner_sweep_staged<T2, 2, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
+    if (k.nbt == 2 && k.rw == 8)
+        return inner_sweep_staged<T2, 2, 8>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, k.R);
     return false;
 }
 
@@ -1186,10 +1198,20 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
         if (choice >= 0 && choice < kNumSweepCands)
             ok = sweep_cand<T2>(choice, d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     }
-    // default rule (what the tuner picks on the 1024 x 1024 shapes): 8-column tiles;
-    // a single layer in flight takes 8-CTA clusters with 4 rows per warp, several
-    // layers 16-CTA clusters with 2 rows per warp
+    // default rule (what the tuner picks on the 1024 x 1024 and the multi-frequency
+    // 512 x 512 shapes): 4-column tiles in 8-CTA clusters with 4 rows per warp, unless
+    // that leaves SMs idle (a single layer with few right-hand sides): then 2-column
+    // tiles (8-CTA clusters in FP32, 16-CTA clusters in FP64)
+    static int n_sm = 0;
+    if (n_sm == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0) n_sm = 152;
+    }
     const bool narrow = (long long)((B + 7) / 8) * nlayer * 16 <= 608;
+    if (!ok && (long long)((B + 3) / 4) * nlayer * 8 < n_sm)
+        ok = inner_sweep_staged<T2, 2, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, sizeof(T2) == 8 ? 8 : 16);
+    if (!ok) ok = inner_sweep_staged<T2, 4, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 8);
     if (!ok && nlayer == 1)
         ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 8);
     if (!ok) ok = inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);

@@ -92,4 +92,4 @@ def test_autotuned_sweeps_match_oracle_and_fill_cache(tmp_path, monkeypatch):
     import json
     table = json.loads(cache.read_text())
     assert any(k.startswith("sweep es=8") for k in table)
-    assert all(0 <= v < 6 for v in table.values())
+    assert all(isinstance(v, int) and v >= 0 for v in table.values())  # a candidate index per shape
