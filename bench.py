@@ -272,8 +272,10 @@ def run_ours(args, rank, world):
         ratio, traffic_src = DRAM_PER_ALGO[names[top]]
         traffic = round(float(ratio * kt_b[top] / kt_n[top]))
     roof.update({"kernel": names[top], "traffic": traffic, "traffic_source": traffic_src,
-                 "peak_source": src + " (" +
-                 ("FP32 SIMT from 152 SMs x 128 lanes x max clock" if roof["bound"] == "alu" else "copy GB/s") + ")",
+                 "peak_source": (("derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock"
+                                  " (" + src + "); a register-only FMA loop measured 73.3 TFLOP/s")
+                                 if prec == hz.HZ_MIXED else "FP64 DFMA, a register-only loop measured 1.255 TFLOP/s")
+                                if roof["bound"] == "alu" else src + " copy GB/s",
                  "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
                  "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
                  "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)}})
