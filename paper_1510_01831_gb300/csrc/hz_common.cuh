@@ -156,9 +156,12 @@ struct HzError {
 
 // ------------------------------------------------- kernel launchers ---
 // (defined in hz_kernels.cu; all launch on `st` and count launches in *nl)
+// cfg: output tile of a CTA, 0 = 64 x 32 (GBM x GBN), 1 = 32 x 32, 2 = 64 x 16;
+// max_tiles counts tiles of that shape (gemm_tiles)
 template <class T2>
 void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt, cudaStream_t st,
-                 int *nl);
+                 int *nl, int cfg = 0);
+int gemm_tiles(int M, int N, int cfg);
 // batched GEMM tile (complex outputs) and K step
 constexpr int GBM = 64, GBN = 32, GBK = 16;
 // split-K is used while a launch has fewer tiles than this; its workspace

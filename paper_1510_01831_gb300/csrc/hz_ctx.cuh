@@ -24,6 +24,7 @@ template <class T2> struct ProbList {
     GemmProb<T2> *d = nullptr;
     int n = 0, max_tiles = 0;
     int kmax = 0;                 // longest K (both passes) of a problem
+    int max_tiles32 = 0;          // most 32 x 32 tiles of a problem (small lists take that tile)
     int tc_max_tiles = 0;         // tensor-core GEMM: most 128 x 64 tiles of a problem,
     int tc_kchunks = 0;           // most K chunks of 16 (both passes), and
     long long tc_tiles = 0;       // tiles of the whole list

@@ -20,35 +20,37 @@ namespace hz {
 // ================================================================ GEMM ===
 
 
-template <class T2>
+// BM x BN complex outputs per CTA of 256 threads (16 x 16): (BM / 16) x (BN / 16) per thread
+template <class T2, int BM, int BN>
 __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ probs, int S, T2 *ws, int *cnt,
                                               int max_tiles) {
+    constexpr int MI = BM / 16, NJ = BN / 16;
     __shared__ GemmProb<T2> P;
     extern __shared__ __align__(16) unsigned char gsm[];
-    T2 (*As)[GBK][GBM + 1] = reinterpret_cast<T2 (*)[GBK][GBM + 1]>(gsm);
-    T2 (*Xs)[GBK][GBN] = reinterpret_cast<T2 (*)[GBK][GBN]>(gsm + sizeof(T2) * 2 * GBK * (GBM + 1));
+    T2 (*As)[GBK][BM + 1] = reinterpret_cast<T2 (*)[GBK][BM + 1]>(gsm);
+    T2 (*Xs)[GBK][BN] = reinterpret_cast<T2 (*)[GBK][BN]>(gsm + sizeof(T2) * 2 * GBK * (BM + 1));
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     if (tid == 0) P = probs[blockIdx.y];
     __syncthreads();
     const int M = P.M, N = P.N;
-    const int tilesM = (M + GBM - 1) / GBM, tilesN = (N + GBN - 1) / GBN;
+    const int tilesM = (M + BM - 1) / BM, tilesN = (N + BN - 1) / BN;
     const int tile = blockIdx.x / S, sp = blockIdx.x % S;
     if (tile >= tilesM * tilesN) return;
     // split sp of S takes a GBK-aligned slice of the K range of both passes laid end to end
     const int K1 = max(P.K, 0), Kt = K1 + max(P.K2, 0);
     const int per = ((Kt + S - 1) / S + GBK - 1) / GBK * GBK;
     const int kb = min(Kt, sp * per), ke = min(Kt, kb + per);
-    const int m0 = (tile % tilesM) * GBM, n0 = (tile / tilesM) * GBN;
-    T2 acc[4][2];
+    const int m0 = (tile % tilesM) * BM, n0 = (tile / tilesM) * BN;
+    T2 acc[MI][NJ];
 #pragma unroll
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < MI; i++)
 #pragma unroll
-        for (int j = 0; j < 2; j++) acc[i][j] = czero<T2>();
+        for (int j = 0; j < NJ; j++) acc[i][j] = czero<T2>();
     // load slots of this thread: A elements (mm, kk) for q < AQ, X elements (kk, nn) for q < XQ
-    constexpr int AR = 256 / GBK, AQ = GBM / AR;  // A rows per pass, passes
-    constexpr int XR = 256 / GBN, XQ = GBK / XR;  // X rows per pass, passes
+    constexpr int AR = 256 / GBK, AQ = BM / AR;  // A rows per pass, passes
+    constexpr int XR = 256 / BN, XQ = GBK / XR;  // X rows per pass, passes
     const int a_kk = tid % GBK, a_mm = tid / GBK;  // + AR q rows
-    const int x_nn = tid % GBN, x_kk = tid / GBN;  // + XR q rows
+    const int x_nn = tid % BN, x_kk = tid / BN;  // + XR q rows
     T2 ra[AQ], rx[XQ];
     int buf = 0;
     for (int pass = 0; pass < 2; pass++) {
@@ -88,15 +90,15 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
             if (k0 + GBK < K) load(k0 + GBK);  // in flight during the products below
 #pragma unroll
             for (int kk = 0; kk < GBK; kk++) {
-                T2 a[4], x[2];
+                T2 a[MI], x[NJ];
 #pragma unroll
-                for (int i = 0; i < 4; i++) a[i] = As[buf][kk][ty + 16 * i];
+                for (int i = 0; i < MI; i++) a[i] = As[buf][kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 2; j++) x[j] = Xs[buf][kk][tx + 16 * j];
+                for (int j = 0; j < NJ; j++) x[j] = Xs[buf][kk][tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 4; i++)
+                for (int i = 0; i < MI; i++)
 #pragma unroll
-                    for (int j = 0; j < 2; j++) cmac(acc[i][j], a[i], x[j]);
+                    for (int j = 0; j < NJ; j++) cmac(acc[i][j], a[i], x[j]);
             }
             buf ^= 1;  // the other buffer is free: every thread passed this chunk's barrier
         }
@@ -107,11 +109,11 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         // tile to finish adds the partials in split order (deterministic) and
         // writes the output, then re-arms the tile's counter
         const long long slot = (long long)blockIdx.y * max_tiles + tile;
-        T2 *mine = ws + (slot * S + sp) * (GBM * GBN);
+        T2 *mine = ws + (slot * S + sp) * (BM * BN);
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < MI; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) mine[(ty + 16 * i) * GBN + tx + 16 * j] = acc[i][j];
+            for (int j = 0; j < NJ; j++) mine[(ty + 16 * i) * BN + tx + 16 * j] = acc[i][j];
         __threadfence();
         __syncthreads();
         __shared__ int last;
@@ -120,12 +122,12 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         if (!last) return;
         __threadfence();
 #pragma unroll
-        for (int i = 0; i < 4; i++)
+        for (int i = 0; i < MI; i++)
 #pragma unroll
-            for (int j = 0; j < 2; j++) {
+            for (int j = 0; j < NJ; j++) {
                 T2 v = czero<T2>();
                 for (int q = 0; q < S; q++) {
-                    const T2 *pq = ws + (slot * S + q) * (GBM * GBN) + (ty + 16 * i) * GBN + tx + 16 * j;
+                    const T2 *pq = ws + (slot * S + q) * (BM * BN) + (ty + 16 * i) * BN + tx + 16 * j;
                     const T2 w = __ldcg(pq);
                     v.x += w.x;
                     v.y += w.y;
@@ -135,13 +137,13 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
         if (tid == 0) cnt[slot] = 0;
     }
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < MI; i++) {
         const int m = m0 + ty + 16 * i;
         if (m >= M) continue;
         const int sg = m / P.yseg;
         T2 *row = P.Y[sg] + (long long)(m - sg * P.yseg) * P.ldy;
 #pragma unroll
-        for (int j = 0; j < 2; j++) {
+        for (int j = 0; j < NJ; j++) {
             const int n = n0 + tx + 16 * j;
             if (n >= N) continue;
             T2 v = acc[i][j];
@@ -152,24 +154,41 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     }
 }
 
-template <class T2>
-void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt,
-                 cudaStream_t st, int *nl) {
-    if (nprob <= 0 || max_tiles <= 0) return;
-    if (split < 1 || (split > 1 && (!ws || !cnt))) throw HzError(HZ_EINVAL, "batched GEMM: bad split-K workspace");
+int gemm_tiles(int M, int N, int cfg) {
+    const int bm = cfg == 1 ? 32 : 64, bn = cfg == 2 ? 16 : 32;
+    return ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
+}
+
+template <class T2, int BM, int BN>
+static void launch_gemm_cfg(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt,
+                            cudaStream_t st) {
     dim3 grid(max_tiles * split, nprob);
-    const size_t sm = sizeof(T2) * 2 * GBK * (GBM + 1 + GBN);
+    const size_t sm = sizeof(T2) * 2 * GBK * (BM + 1 + BN);
     static bool attr = false;
     if (!attr) {
-        HZ_CU(cudaFuncSetAttribute(k_gemm<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HZ_CU(cudaFuncSetAttribute(k_gemm<T2, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    k_gemm<T2><<<grid, 256, sm, st>>>(d_probs, split, ws, cnt, max_tiles);
+    k_gemm<T2, BM, BN><<<grid, 256, sm, st>>>(d_probs, split, ws, cnt, max_tiles);
+}
+
+template <class T2>
+void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt,
+                 cudaStream_t st, int *nl, int cfg) {
+    if (nprob <= 0 || max_tiles <= 0) return;
+    if (split < 1 || (split > 1 && (!ws || !cnt))) throw HzError(HZ_EINVAL, "batched GEMM: bad split-K workspace");
+    if (cfg == 1)
+        launch_gemm_cfg<T2, 32, 32>(d_probs, nprob, max_tiles, split, ws, cnt, st);
+    else if (cfg == 2)
+        launch_gemm_cfg<T2, 64, 16>(d_probs, nprob, max_tiles, split, ws, cnt, st);
+    else
+        launch_gemm_cfg<T2, 64, 32>(d_probs, nprob, max_tiles, split, ws, cnt, st);
     HZ_CU(cudaGetLastError());
     if (nl) (*nl)++;
 }
-template void launch_gemm<double2>(const GemmProb<double2> *, int, int, int, double2 *, int *, cudaStream_t, int *);
-template void launch_gemm<float2>(const GemmProb<float2> *, int, int, int, float2 *, int *, cudaStream_t, int *);
+template void launch_gemm<double2>(const GemmProb<double2> *, int, int, int, double2 *, int *, cudaStream_t, int *,
+                                   int);
+template void launch_gemm<float2>(const GemmProb<float2> *, int, int, int, float2 *, int *, cudaStream_t, int *, int);
 
 // ========================================================= cell chain ===
 // Solve H^{l,c} x = g for every cell and RHS group.  H^{l,c} is block
