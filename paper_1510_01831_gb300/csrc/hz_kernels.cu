@@ -20,15 +20,32 @@ namespace hz {
 // ================================================================ GEMM ===
 
 
-// BM x BN complex outputs per CTA of 256 threads (16 x 16): (BM / 16) x (BN / 16) per thread
+// asynchronous copy of one complex element (8 or 16 bytes) into shared memory;
+// bytes = 0 fills it with zeros
+template <int SZ> __device__ __forceinline__ void gemm_cp(void *dst, const void *src, unsigned bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(SZ), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void gemm_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void gemm_cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// FP32: two stages filled through registers (measured faster here); FP64: a 3-stage ring of asynchronous copies
+template <class T2> constexpr int gemm_stages() { return sizeof(T2) == 8 ? 2 : 3; }
+
+// BM x BN complex outputs per CTA of 256 threads (16 x 16): (BM / 16) x (BN / 16)
+// per thread, K steps of GBK.  FP32: the next step's operands are loaded into
+// registers during the current step's products and stored to the other of two
+// shared-memory buffers.  FP64: the K steps of both operand pairs, laid end to
+// end, flow through a 3-stage ring filled by asynchronous copies two steps ahead.
 template <class T2, int BM, int BN>
 __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ probs, int S, T2 *ws, int *cnt,
                                               int max_tiles) {
-    constexpr int MI = BM / 16, NJ = BN / 16;
+    constexpr int MI = BM / 16, NJ = BN / 16, NST = gemm_stages<T2>();
     __shared__ GemmProb<T2> P;
     extern __shared__ __align__(16) unsigned char gsm[];
     T2 (*As)[GBK][BM + 1] = reinterpret_cast<T2 (*)[GBK][BM + 1]>(gsm);
-    T2 (*Xs)[GBK][BN] = reinterpret_cast<T2 (*)[GBK][BN]>(gsm + sizeof(T2) * 2 * GBK * (BM + 1));
+    T2 (*Xs)[GBK][BN] = reinterpret_cast<T2 (*)[GBK][BN]>(gsm + sizeof(T2) * NST * GBK * (BM + 1));
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     if (tid == 0) P = probs[blockIdx.y];
     __syncthreads();
@@ -41,67 +58,129 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     const int per = ((Kt + S - 1) / S + GBK - 1) / GBK * GBK;
     const int kb = min(Kt, sp * per), ke = min(Kt, kb + per);
     const int m0 = (tile % tilesM) * BM, n0 = (tile / tilesM) * BN;
+    // this split's part of each pass, in the pass's own K coordinates, and its steps
+    const int klo0 = min(kb, K1), kend0 = min(ke, K1);
+    const int klo1 = max(kb - K1, 0), kend1 = max(ke - K1, 0);
+    const int ns0 = kend0 > klo0 ? (kend0 - klo0 + GBK - 1) / GBK : 0;
+    const int ns1 = kend1 > klo1 ? (kend1 - klo1 + GBK - 1) / GBK : 0;
+    const int nk = ns0 + ns1;
     T2 acc[MI][NJ];
 #pragma unroll
     for (int i = 0; i < MI; i++)
 #pragma unroll
         for (int j = 0; j < NJ; j++) acc[i][j] = czero<T2>();
-    // load slots of this thread: A elements (mm, kk) for q < AQ, X elements (kk, nn) for q < XQ
+    // copy slots of this thread: A elements (mm, kk) for q < AQ, X elements (kk, nn) for q < XQ
     constexpr int AR = 256 / GBK, AQ = BM / AR;  // A rows per pass, passes
     constexpr int XR = 256 / BN, XQ = GBK / XR;  // X rows per pass, passes
     const int a_kk = tid % GBK, a_mm = tid / GBK;  // + AR q rows
-    const int x_nn = tid % BN, x_kk = tid / BN;  // + XR q rows
-    T2 ra[AQ], rx[XQ];
-    int buf = 0;
-    for (int pass = 0; pass < 2; pass++) {
-        const T2 *A = pass ? P.A2 : P.A;
-        const long long lda = pass ? P.lda2 : P.lda;
-        const int xseg = pass ? P.xseg2 : P.xseg;
-        const long long ldx = pass ? P.ldx2 : P.ldx;
-        const T2 *const *Xp = pass ? P.X2 : P.X;
-        // this split's part of the pass, in the pass's own K coordinates
-        const int off = pass ? K1 : 0, Kp = pass ? Kt - K1 : K1;
-        const int klo = max(kb - off, 0), K = min(ke - off, Kp);
-        if (K <= klo) continue;
-        auto load = [&](int k0) {
+    const int x_nn = tid % BN, x_kk = tid / BN;   // + XR q rows
+    if constexpr (sizeof(T2) == 8) {
+        T2 ra[AQ], rx[XQ];
+        int buf = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            const T2 *A = pass ? P.A2 : P.A;
+            const long long lda = pass ? P.lda2 : P.lda;
+            const int xseg = pass ? P.xseg2 : P.xseg;
+            const long long ldx = pass ? P.ldx2 : P.ldx;
+            const T2 *const *Xp = pass ? P.X2 : P.X;
+            // this split's part of the pass, in the pass's own K coordinates
+            const int off = pass ? K1 : 0, Kp = pass ? Kt - K1 : K1;
+            const int klo = max(kb - off, 0), K = min(ke - off, Kp);
+            if (K <= klo) continue;
+            auto load = [&](int k0) {
+#pragma unroll
+                for (int q = 0; q < AQ; q++) {
+                    const int gm = m0 + a_mm + AR * q, gk = k0 + a_kk;
+                    ra[q] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
+                }
+#pragma unroll
+                for (int q = 0; q < XQ; q++) {
+                    const int gk = k0 + x_kk + XR * q, gn = n0 + x_nn;
+                    T2 v = czero<T2>();
+                    if (gk < K && gn < N) {
+                        const int sg = gk / xseg;
+                        v = Xp[sg][(long long)(gk - sg * xseg) * ldx + gn];
+                    }
+                    rx[q] = v;
+                }
+            };
+            load(klo);
+            for (int k0 = klo; k0 < K; k0 += GBK) {
+#pragma unroll
+                for (int q = 0; q < AQ; q++) As[buf][a_kk][a_mm + AR * q] = ra[q];
+#pragma unroll
+                for (int q = 0; q < XQ; q++) Xs[buf][x_kk + XR * q][x_nn] = rx[q];
+                __syncthreads();
+                if (k0 + GBK < K) load(k0 + GBK);  // in flight during the products below
+#pragma unroll
+                for (int kk = 0; kk < GBK; kk++) {
+                    T2 a[MI], x[NJ];
+#pragma unroll
+                    for (int i = 0; i < MI; i++) a[i] = As[buf][kk][ty + 16 * i];
+#pragma unroll
+                    for (int j = 0; j < NJ; j++) x[j] = Xs[buf][kk][tx + 16 * j];
+#pragma unroll
+                    for (int i = 0; i < MI; i++)
+#pragma unroll
+                        for (int j = 0; j < NJ; j++) cmac(acc[i][j], a[i], x[j]);
+                }
+                buf ^= 1;  // the other buffer is free: every thread passed this chunk's barrier
+            }
+        }
+    } else {
+        auto issue = [&](int t) {  // copies of step t into stage t % NST
+            const int bf = t % NST;
+            const bool p2 = t >= ns0;
+            const int k0 = p2 ? klo1 + (t - ns0) * GBK : klo0 + t * GBK, K = p2 ? kend1 : kend0;
+            const T2 *A = p2 ? P.A2 : P.A;
+            const long long lda = p2 ? P.lda2 : P.lda;
+            const int xseg = p2 ? P.xseg2 : P.xseg;
+            const long long ldx = p2 ? P.ldx2 : P.ldx;
+            const T2 *const *Xp = p2 ? P.X2 : P.X;
 #pragma unroll
             for (int q = 0; q < AQ; q++) {
                 const int gm = m0 + a_mm + AR * q, gk = k0 + a_kk;
-                ra[q] = (gm < M && gk < K) ? A[(long long)gm * lda + gk] : czero<T2>();
+                const bool ok = gm < M && gk < K;
+                gemm_cp<sizeof(T2)>(&As[bf][a_kk][a_mm + AR * q], ok ? A + (long long)gm * lda + gk : A,
+                                    ok ? (unsigned)sizeof(T2) : 0u);
             }
 #pragma unroll
             for (int q = 0; q < XQ; q++) {
                 const int gk = k0 + x_kk + XR * q, gn = n0 + x_nn;
-                T2 v = czero<T2>();
-                if (gk < K && gn < N) {
+                const bool ok = gk < K && gn < N;
+                const T2 *src = Xp[0];
+                if (ok) {
                     const int sg = gk / xseg;
-                    v = Xp[sg][(long long)(gk - sg * xseg) * ldx + gn];
+                    src = Xp[sg] + (long long)(gk - sg * xseg) * ldx + gn;
                 }
-                rx[q] = v;
+                gemm_cp<sizeof(T2)>(&Xs[bf][x_kk + XR * q][x_nn], src, ok ? (unsigned)sizeof(T2) : 0u);
             }
         };
-        load(klo);
-        for (int k0 = klo; k0 < K; k0 += GBK) {
 #pragma unroll
-            for (int q = 0; q < AQ; q++) As[buf][a_kk][a_mm + AR * q] = ra[q];
-#pragma unroll
-            for (int q = 0; q < XQ; q++) Xs[buf][x_kk + XR * q][x_nn] = rx[q];
-            __syncthreads();
-            if (k0 + GBK < K) load(k0 + GBK);  // in flight during the products below
+        for (int t = 0; t < NST - 1; t++) {  // prologue: the first NST - 1 steps in flight
+            if (t < nk) issue(t);
+            gemm_cp_commit();
+        }
+        for (int t = 0; t < nk; t++) {
+            gemm_cp_wait<NST - 2>();  // this thread's copies of step t have landed
+            __syncthreads();          // everyone's have; and every thread is done with step t - 1
+            if (t + NST - 1 < nk) issue(t + NST - 1);  // into the stage of step t - 1
+            gemm_cp_commit();
+            const int bf = t % NST;
 #pragma unroll
             for (int kk = 0; kk < GBK; kk++) {
                 T2 a[MI], x[NJ];
 #pragma unroll
-                for (int i = 0; i < MI; i++) a[i] = As[buf][kk][ty + 16 * i];
+                for (int i = 0; i < MI; i++) a[i] = As[bf][kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < NJ; j++) x[j] = Xs[buf][kk][tx + 16 * j];
+                for (int j = 0; j < NJ; j++) x[j] = Xs[bf][kk][tx + 16 * j];
 #pragma unroll
                 for (int i = 0; i < MI; i++)
 #pragma unroll
                     for (int j = 0; j < NJ; j++) cmac(acc[i][j], a[i], x[j]);
             }
-            buf ^= 1;  // the other buffer is free: every thread passed this chunk's barrier
         }
+        gemm_cp_wait<0>();
     }
     const float al = P.alpha;
     if (S > 1) {
@@ -163,7 +242,7 @@ template <class T2, int BM, int BN>
 static void launch_gemm_cfg(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt,
                             cudaStream_t st) {
     dim3 grid(max_tiles * split, nprob);
-    const size_t sm = sizeof(T2) * 2 * GBK * (BM + 1 + BN);
+    const size_t sm = sizeof(T2) * gemm_stages<T2>() * GBK * (BM + 1 + BN);
     static bool attr = false;
     if (!attr) {
         HZ_CU(cudaFuncSetAttribute(k_gemm<T2, BM, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
