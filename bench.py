@@ -278,7 +278,21 @@ def run_ours(args, rank, world):
                                 if roof["bound"] == "alu" else src + " copy GB/s",
                  "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
                  "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
-                 "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)}})
+                 "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)},
+                 # every timed class: algorithmic rates over its own event time, against both roofs
+                 "classes": {n: {"ms_per_step": round(float(kt_ms[i] / args.steps), 3),
+                                 "launches_per_step": round(float(kt_n[i] / args.steps), 1),
+                                 "gb_s": round(float(kt_b[i] / (kt_ms[i] / 1e3) / 1e9), 1) if kt_ms[i] > 0 else 0.0,
+                                 "tflop_s": round(float(kt_f[i] / (kt_ms[i] / 1e3) / 1e12), 3) if kt_ms[i] > 0 else 0.0,
+                                 "frac_hbm": round(float(kt_b[i] / (kt_ms[i] / 1e3) / 1e9 / hbm), 4) if kt_ms[i] > 0 else 0.0,
+                                 "frac_alu": round(float(kt_f[i] / (kt_ms[i] / 1e3) / 1e12 / alu_peak), 4)
+                                 if kt_ms[i] > 0 else 0.0}
+                             for i, n in enumerate(names)}})
+    if prec == hz.HZ_MIXED and not args.no_tensor_cores and kt_ms[0] > 0:
+        # the cell solves run on the tensor cores: 3 TF32 products per real product, against
+        # the TF32 rate measured by an MMA-rate probe (1286 TFLOP/s at N >= 128)
+        roof["classes"]["cell_chain"]["frac_tensor_3xtf32"] = round(float(kt_f[0] / (kt_ms[0] / 1e3) / 1e12 /
+                                                                          (1286.0 / 3)), 4)
     last = stats[-1]
     pb = pbs[0]
     nbytes = sum(f.nbytes for _, f in items)
