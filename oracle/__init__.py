@@ -12,8 +12,9 @@ Layers of the oracle:
   (Sections 2-3: the SIE and polarized reformulations are exact).
 * this module: the decomposition into layers and cells, the local Green's
   integrals of Section 2.3 written through the identity of Appendix C, the
-  polarized system of Section 3 and its preconditioners, and the misfit
-  gradient.  Every operator is applied through explicit local solves; no
+  polarized system of Section 3 and its preconditioners, the inner nested
+  polarized traces of Section 4.2 (a layer solved over its cells by the same
+  functions on its swapped-axes box), and the misfit gradient.  Every operator is applied through explicit local solves; no
   operator is precomputed or compressed.
 
 Readings of the paper taken where it is ambiguous (each is listed with its
@@ -463,6 +464,65 @@ def reconstruct(D: Decomposition, f: np.ndarray, tr: np.ndarray) -> np.ndarray:
         lo, hi = D.owned_rows(l)
         u[..., D.s[l] + lo:D.s[l] + hi, :] = v[..., lo:hi, :]
     return u
+
+
+# --------------------------------------------------------------------------
+# Inner nested polarized traces (Section 4.2): a layer's local problem solved
+# by the method of polarized traces over its cells (GMRES on the cells'
+# polarized system, preconditioned by the Gauss-Seidel sweeps over the cells)
+# instead of a direct factorization.  The layer box with its axes swapped is a
+# problem of the same form -- the operator of Appendix A treats both axes
+# alike, and the cells extend the layer's medium by the rule R3 just as the
+# layers extend the global one -- so the cells are the layers of that problem
+# and the functions above apply to it unchanged.
+# --------------------------------------------------------------------------
+
+def layer_inner_decomposition(D: Decomposition, l: int) -> Decomposition:
+    """Layer l of D with x and z swapped: its C cells become the layers."""
+    return Decomposition(D.layer_medium(l).T, D.rows[l], D.n_x, D.p, D.omega, D.h, D.C_pml, D.C, 1,
+                         layer_rows=D.cols)
+
+
+def nested_layer_solve(DT: Decomposition, g: np.ndarray, tol: float = 1e-10, precond=None, maxit: int = 200):
+    """v = (H^l)^{-1} g for the layer whose swapped-axes decomposition is DT
+    (g, v on the layer's box, (..., n_l + 2p, NX)).  Returns (v, iterations)."""
+    gT = np.swapaxes(g, -1, -2)
+    if DT.L == 1:
+        return DT.layer_factor(0).solve(gT).swapaxes(-1, -2), 0
+    P = precond if precond is not None else precond_gs
+    b = polarized_rhs(DT, gT)
+    x, its, _ = gmres(lambda y: apply_M(DT, y), b, lambda y: P(DT, y), tol=tol, maxit=maxit)
+    tr = x[..., DA:DB + 1, :] + x[..., UA:UB + 1, :]  # interface traces = down + up (R6)
+    return np.swapaxes(reconstruct(DT, gT, tr), -1, -2), its
+
+
+class NestedDecomposition(Decomposition):
+    """The decomposition with every layer solve done by the inner nested
+    polarized traces to relative tolerance tol_inner (the nested method of
+    Section 4: outer polarized traces over layers, inner over cells)."""
+
+    def __init__(self, *args, tol_inner: float = 1e-10, **kw):
+        super().__init__(*args, **kw)
+        self.tol_inner = tol_inner
+        self.inner_iterations = []
+        self._inner = {}
+
+    def inner(self, l: int) -> Decomposition:
+        if l not in self._inner:
+            self._inner[l] = layer_inner_decomposition(self, l)
+        return self._inner[l]
+
+    def green(self, l: int, t0, t1, tn, tn1, f=None, full=False):
+        g = self.interface_source(l, t0, t1, tn, tn1)
+        if f is not None:
+            g = g + self.layer_source(l, f)
+        v, its = nested_layer_solve(self.inner(l), g, self.tol_inner)
+        self.inner_iterations.append(its)
+        if full:
+            return v
+        n = self.rows[l]
+        rows = [self.lrow(0), self.lrow(1), self.lrow(n), self.lrow(n + 1)]
+        return v[..., rows, :]
 
 
 # --------------------------------------------------------------------------
