@@ -421,7 +421,10 @@ def precond_jac(D: Decomposition, v: np.ndarray) -> np.ndarray:
 
 
 def gmres(apply_A, b: np.ndarray, apply_P=None, tol=1e-10, maxit=200):
-    """Right-preconditioned GMRES (MGS Arnoldi, no restart) on one vector.
+    """Right-preconditioned GMRES (MGS Arnoldi, no restart) on one vector, in
+    the flexible form (Saad 1993): the preconditioned directions z_j are kept
+    and x = sum y_j z_j, so a preconditioner that changes between applications
+    (inexact inner solves) is admissible.
 
     Returns (x, iterations, residual history)."""
     shape = b.shape
