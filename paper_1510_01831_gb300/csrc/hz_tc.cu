@@ -3,28 +3,30 @@
 // The cell solve of Alg. inner_solver is the block-tridiagonal chain
 //   y_0 = W_0 g_0,  y_j = W_j (g_j - cz_{j-1} . y_{j-1}),
 //   x_{nz-1} = y_{nz-1},  x_j = y_j - W_j (cz_j . x_{j+1}),
-// i.e. one dense complex product D = W_j T per step, T being the nx x 32
-// panel of right-hand sides the previous step's epilogue produced.  Here every
-// product runs on the 5th-generation tensor cores as four real products
+// i.e. one dense complex product D = W_j T per step, T being the nx x NT
+// panel of right-hand sides (NT = 32 or 64) the previous step's epilogue
+// produced.  Here every product runs on the 5th-generation tensor cores as
+// four real products
 // (Wr Tr, Wi Ti, Wr Ti, Wi Tr), each with the 3xTF32 split
 // X Y ~ Xh Yh + Xh Yl + Xl Yh (Xh = X rounded to TF32, Xl = X - Xh rounded to
 // TF32), which keeps the product accurate to about FP32 roundoff:
 //   - W_j is split offline (from the FP64 factors) into Wr_h, Wr_l, Wi_h,
 //     Wi_l, stored in the no-swizzle K-major canonical layout of the MMA
 //     operand, 16 columns per chunk, so a chunk is one contiguous bulk (TMA)
-//     copy; chunks stream through a 4-stage shared-memory ring (mbarriers
-//     "full" / "empty");
+//     copy; chunks stream through a shared-memory ring (4 stages with
+//     NT = 32, 3 with NT = 64; mbarriers "full" / "empty");
 //   - T is kept in shared memory as Tr_h, Tr_l, Ti_h, Ti_l in the same
 //     canonical layout (rows = right-hand sides, K = cell columns);
 //   - a producer warp streams the W chunks through the ring ahead of use;
 //     one thread issues the tcgen05.mma instructions (M = 128 rows of W,
-//     N = 32 right-hand sides, K = 8 per instruction) into FP32 accumulators
-//     in tensor memory (the Xh Yh terms of even and odd K chunks and the small
-//     cross terms in separate accumulators) and commits them to mbarriers;
+//     N = NT right-hand sides, K = 8 per instruction) into FP32 accumulators
+//     in tensor memory (the small cross terms apart from the main Xh Yh
+//     terms; with NT = 32 also the main terms of even and odd K chunks apart)
+//     and commits them to mbarriers;
 //   - the 128 threads (thread = row of W, = TMEM lane) read the accumulators
 //     with tcgen05.ld, form the step's output (stored to global memory) and
 //     the next T, split it and write it back through a per-warp transpose.
-// One CTA per (cell, 32 right-hand sides); cells up to 128 columns wide.
+// One CTA per (cell, NT right-hand sides); cells up to 128 columns wide.
 // Every wait is bounded (1 s): a timeout sets the error word and the whole
 // CTA leaves the steps together, drains its bulk copies and frees its tensor
 // memory before it returns.
@@ -34,7 +36,6 @@ namespace hz {
 
 namespace {
 
-constexpr int TC_NT = 32;    // right-hand sides per CTA (MMA N)
 constexpr int TC_KC = 16;    // K columns per streamed chunk
 constexpr int TC_ST = 4;     // ring stages
 constexpr int TC_THREADS = 160;  // warps 0-3: MMA issue and epilogue (TMEM lanes 0-127); warp 4: producer
