@@ -88,6 +88,7 @@ def _load():
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
             lib.hzo_alpha.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p]
+            lib.hzo_stencil.argtypes = [P, ctypes.c_void_p]
             _lib = lib
     return _lib
 
@@ -158,6 +159,18 @@ class Box:
         """order 0: smaller band width; 1: x fastest; 2: z fastest."""
         return Factor(self, order)
 
+    def stencil(self) -> np.ndarray:
+        """The five coefficient planes (5, NZ, NX) of the operator: couplings to
+        (z-1, x), (z, x-1), the node itself, (z, x+1), (z+1, x); zero beyond
+        the extended grid."""
+        out = np.empty((5,) + self.shape, dtype=np.complex128)
+        _load().hzo_stencil(ctypes.byref(self._c), out.ctypes.data)
+        return out
+
+    def factor_rows(self, keep_every: int = 1) -> "RowBlockFactor":
+        """Block-tridiagonal elimination over grid rows (see RowBlockFactor)."""
+        return RowBlockFactor(self, keep_every)
+
 
 class Factor:
     """Banded LU (partial pivoting) of a Box's operator."""
@@ -188,6 +201,90 @@ class Factor:
         if h:
             _load().hzo_free(h)
             self._h = None
+
+
+class RowBlockFactor:
+    """u = H^{-1} f by block-tridiagonal elimination over the grid rows, the
+    direct solve for grids whose pivoted band LU does not fit in memory.
+
+    With the unknowns of one grid row z as a block, the operator of Appendix A
+    is block tridiagonal: H = tridiag(A_z, D_z, C_z) with D_z the tridiagonal
+    (x-coupling) block of row z and A_z, C_z the diagonal couplings to rows
+    z-1 and z+1.  Block Gaussian elimination without block pivoting:
+        S_0 = D_0,   S_z = D_z - A_z S_{z-1}^{-1} C_{z-1},
+        y_0 = f_0,   y_z = f_z - A_z S_{z-1}^{-1} y_{z-1},
+        u_last = S_last^{-1} y_last,   u_z = S_z^{-1} (y_z - C_z u_{z+1}),
+    each Schur block S_z factored by LAPACK's LU with partial pivoting
+    (scipy.linalg.lu_factor, a library primitive).  Storage: NZ factors of
+    NX x NX.  keep_every = k > 1 keeps every k-th factor only and recomputes
+    the others a segment at a time when a solve needs them (the same
+    arithmetic from the same inputs; 1/k of the memory, up to three times the
+    factorization work).
+    """
+
+    def __init__(self, box: Box, keep_every: int = 1):
+        import scipy.linalg as sl
+        self._sl = sl
+        self.box = box
+        st = box.stencil()
+        self.NZ, self.NX = box.shape
+        self.A, self.Cp = st[0], st[4]          # couplings of row z to rows z-1 and z+1
+        self.lo, self.di, self.up = st[1], st[2], st[3]
+        self.k = max(1, int(keep_every))
+        self.lu = [None] * self.NZ
+        f = None
+        for z in range(self.NZ):
+            f = sl.lu_factor(self._S(z, f), check_finite=False)
+            if z % self.k == 0:
+                self.lu[z] = f
+
+    def _S(self, z, f_prev):
+        """Schur block S_z from the LU factors of S_{z-1}."""
+        NX = self.NX
+        S = np.zeros((NX, NX), dtype=np.complex128)
+        i = np.arange(NX)
+        S[i, i] = self.di[z]
+        S[i[1:], i[:-1]] = self.lo[z][1:]
+        S[i[:-1], i[1:]] = self.up[z][:-1]
+        if z > 0:
+            X = self._sl.lu_solve(f_prev, np.diag(self.Cp[z - 1]), check_finite=False)
+            S -= self.A[z][:, None] * X
+        return S
+
+    def _segment(self, z0):
+        """Factors of rows z0 .. z0+k-1, recomputed from the kept factor of row z0."""
+        out = {z0: self.lu[z0]}
+        f = self.lu[z0]
+        for z in range(z0 + 1, min(z0 + self.k, self.NZ)):
+            f = self._sl.lu_factor(self._S(z, f), check_finite=False)
+            out[z] = f
+        return out
+
+    def solve(self, f: np.ndarray) -> np.ndarray:
+        """H^{-1} f for f of shape (..., NZ, NX)."""
+        sl, NZ, NX, k = self._sl, self.NZ, self.NX, self.k
+        lead = f.shape[:-2]
+        F = np.asarray(f, dtype=np.complex128).reshape((-1, NZ, NX))
+        Y = np.empty((NZ, NX, F.shape[0]), dtype=np.complex128)
+        seg = {}
+
+        def fac(z):
+            nonlocal seg
+            if k == 1:
+                return self.lu[z]
+            if z not in seg:
+                seg = self._segment((z // k) * k)
+            return seg[z]
+        for z in range(NZ):
+            y = F[:, z, :].T.copy()
+            if z > 0:
+                y -= self.A[z][:, None] * sl.lu_solve(fac(z - 1), Y[z - 1], check_finite=False)
+            Y[z] = y
+        U = np.empty_like(Y)
+        for z in range(NZ - 1, -1, -1):
+            r = Y[z] if z == NZ - 1 else Y[z] - self.Cp[z][:, None] * U[z + 1]
+            U[z] = sl.lu_solve(fac(z), r, check_finite=False)
+        return np.ascontiguousarray(np.transpose(U, (2, 0, 1))).reshape(lead + (NZ, NX))
 
 
 def relative_residual(box: Box, u: np.ndarray, f: np.ndarray) -> np.ndarray:
@@ -545,7 +642,8 @@ def misfit_gradient(box: Box, f: np.ndarray, d: np.ndarray, rec_idx: np.ndarray,
     r = uf[:, rec_idx] - d
     J = 0.5 * float(np.sum(np.abs(r) ** 2))
     g = np.zeros_like(uf)
-    g[:, rec_idx] = np.conj(r)
+    # R^T conj(r): a node listed twice as a receiver takes both residuals
+    np.add.at(g, (np.arange(B)[:, None], np.asarray(rec_idx)[None, :]), np.conj(r))
     lam = fac.solve(g.reshape(f.shape), trans=True).reshape(B, -1)
     grad = box.omega ** 2 * np.sum(np.real(lam * uf), axis=0)
     return J, grad.reshape(box.shape), u

@@ -111,6 +111,29 @@ void hzo_entry(const hzo_box *b, long row, long col, double *re, double *im)
     *im = cimag(v);
 }
 
+/* The five stencil coefficients of every row, as planes of NX*NZ complex
+ * values in grid order: plane 0 couples (iz-1, ix), 1 (iz, ix-1), 2 the node
+ * itself, 3 (iz, ix+1), 4 (iz+1, ix); zero where the neighbour lies beyond
+ * the extended grid (Dirichlet). */
+void hzo_stencil(const hzo_box *b, zc *planes)
+{
+    const int NX = b->nxi + 2 * b->p, NZ = b->nzi + 2 * b->p;
+    const long N = (long)NX * NZ;
+    memset(planes, 0, sizeof(zc) * 5 * N);
+    for (int iz = 0; iz < NZ; iz++)
+        for (int ix = 0; ix < NX; ix++) {
+            int cols[5];
+            zc vals[5];
+            const long r = (long)iz * NX + ix;
+            int n = row_entries(b, iz, ix, cols, vals);
+            for (int t = 0; t < n; t++) {
+                const long d = cols[t] - r;
+                const int k = d == -NX ? 0 : d == -1 ? 1 : d == 0 ? 2 : d == 1 ? 3 : 4;
+                planes[k * N + r] = vals[t];
+            }
+        }
+}
+
 /* out[r] = sum_k H[...] u[r] for nrhs vectors of length NX*NZ (grid order). */
 void hzo_apply(const hzo_box *b, int nrhs, const zc *u, zc *out)
 {
