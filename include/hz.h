@@ -174,7 +174,10 @@ hz_status hz_solve_group(hz_ctx **ctxs, int G, const double *const *f, int B,
  * operator is complex symmetric), then
  *   dJ/dm_i = omega^2 sum_s Re(lambda_{s,i} u_{s,i}),  H^T lambda_s = R^T conj(r_s).
  *   f      : [B][grid] sources; d : [B][n_rec] data; rec_idx: [n_rec] flat
- *            grid indices (host or device per device_ptrs);
+ *            grid indices in [0, grid) (host or device per device_ptrs; read
+ *            back and range-checked on the host in both modes, HZ_EINVAL
+ *            beyond); an index listed twice is two receivers at one node and
+ *            counts twice in J and in the gradient;
  *   J      : scalar out (host pointer always); grad_m : [grid] real out;
  *   u_out  : optional [B][grid] forward fields (may be NULL).
  * Errors as hz_solve. */
@@ -277,7 +280,8 @@ hz_status hz_residual(hz_ctx *ctx, const double *u, const double *f, int B, doub
  * call before any stream capture.  The work is enqueued on the context's
  * stream and res is valid once the stream reaches it.  All calls share the
  * scratch array: calls whose kernels overlap on the GPU race.
- * Errors: HZ_EINVAL (NULL pointer, B out of 1..256), HZ_ECUDA. */
+ * Errors: HZ_EINVAL (NULL pointer, B out of 1..256, u/f/res not device
+ * memory of the context's device, another device current), HZ_ECUDA. */
 hz_status hz_residual_noalloc(hz_ctx *ctx, const double *u, const double *f, int B, double *res);
 
 /* Switch the pointer mode of later calls (same meaning as opts.device_ptrs). */

@@ -23,7 +23,8 @@ __global__ void k_finite(const double2 *a, long long n2, int *flag) {
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(flag, 1);
 }
 
-// d [B][n_rec], u [B][N]: r = R u - d; adjoint source g[b][rec] = conj(r)
+// d [B][n_rec], u [B][N]: r = R u - d; adjoint source g = R^T conj(r) (g zeroed by the
+// caller; a node listed twice as a receiver receives both residuals)
 __global__ void k_misfit(const double2 *__restrict__ u, const double2 *__restrict__ d, const int *__restrict__ rec,
                          int n_rec, long long N, int B, double2 *r, double2 *g) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n_rec * B;
@@ -32,7 +33,8 @@ __global__ void k_misfit(const double2 *__restrict__ u, const double2 *__restric
         long long gi = (long long)b * N + rec[i];
         double2 v = make_double2(u[gi].x - d[e].x, u[gi].y - d[e].y);
         r[e] = v;
-        g[gi] = make_double2(v.x, -v.y);
+        atomicAdd(&g[gi].x, v.x);
+        atomicAdd(&g[gi].y, -v.y);
     }
 }
 
@@ -415,15 +417,21 @@ hz_status hz_gradient(hz_ctx *c, const double *f, int B, const double *d, const 
                 for (void *p : v) c->dfree(p);
             }
         } fr{c, {g, lam, r, dd, rd, gd}};
+        // the receiver indices are range-checked on the host in both pointer modes (a
+        // device list is read back first: the kernel indexes u and g with them)
+        std::vector<int> rh_idx((size_t)n_rec);
         if (c->opts.device_ptrs) {
-            HZ_CU(cudaMemcpyAsync(dd, d, sizeof(double2) * (long long)n_rec * B, cudaMemcpyDeviceToDevice, s_));
-            HZ_CU(cudaMemcpyAsync(rd, rec_idx, sizeof(int) * n_rec, cudaMemcpyDeviceToDevice, s_));
+            HZ_CU(cudaMemcpyAsync(rh_idx.data(), rec_idx, sizeof(int) * n_rec, cudaMemcpyDeviceToHost, s_));
+            HZ_CU(cudaStreamSynchronize(s_));
         } else {
-            for (int i = 0; i < n_rec; i++)
-                if (rec_idx[i] < 0 || rec_idx[i] >= N) throw HzError(HZ_EINVAL, "receiver index out of range");
-            HZ_CU(cudaMemcpyAsync(dd, d, sizeof(double2) * (long long)n_rec * B, cudaMemcpyHostToDevice, s_));
-            HZ_CU(cudaMemcpyAsync(rd, rec_idx, sizeof(int) * n_rec, cudaMemcpyHostToDevice, s_));
+            std::memcpy(rh_idx.data(), rec_idx, sizeof(int) * n_rec);
         }
+        for (int i = 0; i < n_rec; i++)
+            if (rh_idx[i] < 0 || rh_idx[i] >= N) throw HzError(HZ_EINVAL, "receiver index out of range");
+        HZ_CU(cudaMemcpyAsync(dd, d, sizeof(double2) * (long long)n_rec * B,
+                              c->opts.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s_));
+        HZ_CU(cudaMemcpyAsync(rd, rh_idx.data(), sizeof(int) * n_rec, cudaMemcpyHostToDevice, s_));
+        HZ_CU(cudaStreamSynchronize(s_));  // rh_idx is a pageable host vector
         hz_stats s1{}, s2{};
         c->kt_reset();
         int sf = c->mixed() ? hz::solve_impl<float2>(c, fd, B, ud, &s1, true)

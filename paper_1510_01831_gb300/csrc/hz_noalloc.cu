@@ -112,9 +112,31 @@ extern "C" hz_status hz_residual_noalloc(hz_ctx *c, const double *u, const doubl
     }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEV) {
+    if (e != cudaSuccess) {
         c->err = std::string("hz_residual_noalloc: cudaGetDevice failed: ") + cudaGetErrorString(e);
         return HZ_ECUDA;
+    }
+    if (dev != c->dev) {
+        c->err = "hz_residual_noalloc: the current device (" + std::to_string(dev) +
+                 ") is not the context's device (" + std::to_string(c->dev) + "); make it current first";
+        return HZ_EINVAL;
+    }
+    if (dev < 0 || dev >= NA_MAX_DEV) {
+        c->err = "hz_residual_noalloc: device ordinal " + std::to_string(dev) + " is beyond the " +
+                 std::to_string(NA_MAX_DEV) + " devices this entry point serves";
+        return HZ_EINVAL;
+    }
+    // u, f and res must be memory of this device (a host address would be
+    // dereferenced by the kernel)
+    const void *args[3] = {u, f, res};
+    for (const void *a : args) {
+        cudaPointerAttributes pa{};
+        e = cudaPointerGetAttributes(&pa, a);
+        if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice || pa.device != dev) {
+            (void)cudaGetLastError();  // clear a sticky-free error of the query
+            c->err = "hz_residual_noalloc: u, f and res must be device memory of the context's device";
+            return HZ_EINVAL;
+        }
     }
     double *scratch = nullptr;
     {

@@ -115,3 +115,40 @@ def test_autograd_checkpoint_matches_stored_fields(case):
         op.close()
     assert _rel(grads[1][0], grads[0][0]) < 1e-9
     assert _rel(grads[1][1], grads[0][1]) < 1e-9
+
+
+def test_gradient_repeated_and_invalid_receivers(case):
+    """Repeated receiver indices accumulate in the adjoint source (as in the
+    oracle); out-of-range indices are rejected in both pointer modes before
+    any kernel reads them."""
+    torch = pytest.importorskip("torch")
+    pb, C_pml, box, fac = case
+    B = 2
+    f = I.random_sources(pb.shape_ext, pb.n_pml, B, 79)
+    top = I.receivers_top_row(pb.n_x, pb.n_pml).astype(np.int32)
+    rec = np.concatenate([top, top[2:9], top[4:5]]).astype(np.int32)
+    rng = np.random.default_rng(80)
+    d = (rng.standard_normal((B, rec.size)) + 1j * rng.standard_normal((B, rec.size))) * 1e-3
+    ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=hz.HZ_FP64,
+                     pml_C=C_pml, tol=1e-12)
+    ctx.hz_factor()
+    J, g, _, _ = ctx.hz_gradient(f, d, rec)
+    J_ref, g_ref, _ = O.misfit_gradient(box, f, d, rec, fac)
+    assert abs(J - J_ref) <= 1e-9 * J_ref
+    assert _rel(g, g_ref) < 1e-8
+    bad = rec.copy()
+    bad[3] = pb.m.size
+    with pytest.raises(hz.HzError):
+        ctx.hz_gradient(f, d, bad)
+    ctx.hz_set_device_ptrs(True)
+    fd_ = torch.from_numpy(f).cuda()
+    dd_ = torch.from_numpy(d).cuda()
+    Jd, gd, _, _ = ctx.hz_gradient(fd_, dd_, torch.from_numpy(rec).cuda())
+    assert abs(Jd - J_ref) <= 1e-9 * J_ref
+    assert _rel(gd.cpu().numpy(), g_ref) < 1e-8
+    for v in (-1, pb.m.size):
+        badd = torch.from_numpy(rec).cuda()
+        badd[5] = v
+        with pytest.raises(hz.HzError):
+            ctx.hz_gradient(fd_, dd_, badd)
+    ctx.close()

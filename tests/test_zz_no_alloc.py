@@ -48,4 +48,11 @@ def test_noalloc_residual_matches_hz_residual_twice():
                                  ctypes.c_void_p(r.data_ptr()))
     assert st == hz.HZ_EINVAL
     assert b"256" in lib.hz_last_error(ctx._ctx)
+    # host arrays are rejected before any kernel could dereference them
+    uh = np.zeros((2,) + pb.shape_ext, complex)
+    rh = np.zeros(2)
+    st = lib.hz_residual_noalloc(ctx._ctx, ctypes.c_void_p(uh.ctypes.data), ctypes.c_void_p(uh.ctypes.data), 2,
+                                 ctypes.c_void_p(rh.ctypes.data))
+    assert st == hz.HZ_EINVAL
+    assert b"device memory" in lib.hz_last_error(ctx._ctx)
     ctx.close()
