@@ -4,10 +4,13 @@ One step = one hz_solve of the whole batch (Newton potentials, FGMRES on the
 polarized traces with the Gauss-Seidel sweeps, volume reconstruction, FP64
 residual refinement to 1e-8), i.e. every row of the hot path.
 
-Default workload: smooth random medium (c in [1.5, 4.5], correlation length
-20h), 1024 x 1024 interior + 20-point PML, 10 points per wavelength at
-c_min, L = 16 layers x C = 16 cells, 64 point sources on the first interior
-row, mixed precision (complex FP32 operators, FP64 Arnoldi and residual).
+Default workload (the largest single-GPU configuration): a layered medium
+with two dip-slip faults (c from 1.5 to 5.5 with depth), 2000 x 4000
+interior + 30-point PML, 8 points per wavelength at c = 1.5, L = 40 layers x
+C = 20 cells, 16 point sources on the first interior row, mixed precision
+(complex FP32 operators, FP64 Arnoldi and residual).  The same line carries
+the 1024 x 1024 smooth random workload (L = C = 16, 64 sources) as
+`secondary` and the plain FP64 form of the default workload as `fp64`.
 
 Metric: RHS*Mdof/s = B * n_x * n_z / 1e6 / (seconds per step), whole job.
 Prints one JSON line on rank 0.
@@ -45,17 +48,20 @@ WORKLOADS = {
     "multifreq512": dict(n=512, n_pml=20, B=256, ppws=(6.0, 8.0, 10.0), seed=4, part_seed=40),
     # layered medium with faults, 2000 wide x 4000 deep + 30 PML, L=40 x C=20, 16 sources, 8 ppw at c=1.5
     "layered2000x4000": dict(n=2000, n_z=4000, n_pml=30, L=40, C=20, B=16, ppw=8.0, seed=3, layered=True),
+    # the same generator at 2000 x 400 (4 layers): every launch has the shape of the 2000 x 4000 workload
+    "layered2000x400": dict(n=2000, n_z=400, n_pml=30, L=4, C=20, B=16, ppw=8.0, seed=3, layered=True),
 }
+DEFAULT_WORKLOAD = "layered2000x4000"
+SECONDARY_WORKLOAD = "smooth1024"
 METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roofline"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of
-# launches with the per-launch shapes of the 1024x1024 workload) divided by the
-# algorithmic bytes of the same launches; the live traffic estimate of a launch
-# is this ratio times its algorithmic bytes (traffic grows with the steps,
-# layers and cells a launch processes)
-DRAM_PER_ALGO = {
-    "inner_chain": (0.65, "profiles/k_inner_sweep_smooth256_shape1024.md"),
-    "cell_chain": (0.742, "profiles/k_cell_chain_smooth256_shape1024.md"),
-}
+# launches with the per-launch shapes of a workload) divided by the algorithmic
+# bytes of the same launches; the live traffic estimate of a launch is this
+# ratio times its algorithmic bytes (traffic grows with the steps, layers and
+# cells a launch processes).  Keyed by (kernel class, workload whose launch
+# shapes were captured); a class without a capture of its current kernel
+# reports traffic null.
+DRAM_PER_ALGO = {}
 UNIT = "RHS*Mdof/s"
 
 
@@ -172,19 +178,70 @@ def make_problem(wl):
 
 
 # ------------------------------------------------------------ GPU arm ---
-def run_ours(args, rank, world):
+CLASS_NAMES = ["cell_chain", "inner_chain", "batched_fes_gemm"]
+
+
+def roofline(kt_ms, kt_n, kt_b, kt_f, ms, steps, mixed, tensor_cores, workload):
+    """Roofline of the kernel class with the largest device time, against the roof
+    it is closer to, plus every class's algorithmic rates against both roofs."""
+    top = int(np.argmax(kt_ms))
+    peaks, src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    # FP32 SIMT peak from unit counts and the maximum SM clock: 152 SMs x 128 FMA lanes x 2 flops
+    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if mixed else 1.25
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+
+    def rates(i):
+        if kt_ms[i] <= 0:
+            return 0.0, 0.0
+        return kt_b[i] / (kt_ms[i] / 1e3) / 1e9, kt_f[i] / (kt_ms[i] / 1e3) / 1e12
+    gbs, tfl = rates(top)
+    if gbs / hbm >= tfl / alu_peak:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4)}
+    else:
+        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                "frac": round(tfl / alu_peak, 4)}
+    traffic, traffic_src = None, None
+    key = (CLASS_NAMES[top], workload, "tc" if (mixed and tensor_cores) else "simt")
+    if key in DRAM_PER_ALGO and kt_n[top] > 0:
+        ratio, traffic_src = DRAM_PER_ALGO[key]
+        traffic = round(float(ratio * kt_b[top] / kt_n[top]))
+    roof.update({
+        "kernel": CLASS_NAMES[top], "traffic": traffic, "traffic_source": traffic_src,
+        "peak_source": (("derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock"
+                         " (" + src + "); a register-only FMA loop measured 73.3 TFLOP/s")
+                        if mixed else "FP64 DFMA, a register-only loop measured 1.255 TFLOP/s")
+        if roof["bound"] == "alu" else src + " copy GB/s",
+        "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
+        "share_of_step": round(float(kt_ms[top] / (ms * steps)), 3),
+        "classes": {n: {"ms_per_step": round(float(kt_ms[i] / steps), 3),
+                        "launches_per_step": round(float(kt_n[i] / steps), 1),
+                        "gb_s": round(rates(i)[0], 1), "tflop_s": round(rates(i)[1], 3),
+                        "frac_hbm": round(rates(i)[0] / hbm, 4), "frac_alu": round(rates(i)[1] / alu_peak, 4)}
+                    for i, n in enumerate(CLASS_NAMES)}})
+    if mixed and tensor_cores and kt_ms[0] > 0:
+        # the cell solves run on the tensor cores: 3 TF32 products per real product, against
+        # the TF32 rate measured by an MMA-rate probe (1286 TFLOP/s at N >= 128)
+        roof["classes"]["cell_chain"]["frac_tensor_3xtf32"] = round(rates(0)[1] / (1286.0 / 3), 4)
+    return roof
+
+
+def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_update=False):
+    """Factor one workload, time `steps` solves after `warmup` untimed ones (CUDA events on the
+    solver's stream, barrier + synchronize on both sides, max over ranks) and return its record."""
     import torch
 
     from paper_1510_01831_gb300 import hz
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    wl = dict(WORKLOADS[args.workload])
+    wl = dict(WORKLOADS[workload])
     if args.B:
         wl["B"] = args.B
     items = make_problems(wl)
     pbs = [pb for pb, _ in items]
     B = items[0][1].shape[0]
-    prec = hz.HZ_MIXED if args.precision == "mixed" else hz.HZ_FP64
+    mixed = precision == "mixed"
+    prec = hz.HZ_MIXED if mixed else hz.HZ_FP64
+    tc = 0 if args.no_tensor_cores else (2 if args.tc_gemm else 1)
     streams = [torch.cuda.Stream() for _ in items]
     ctxs = []
     t0 = time.time()
@@ -194,7 +251,8 @@ def run_ours(args, rank, world):
             kw = dict(layer_rows=pb.layer_rows, cell_cols=pb.cell_cols)
         ctx = hz.Context(pb.m, pb.n_x, pb.n_z, pb.omega, pb.h, pb.n_pml, pb.L, pb.C, precision=prec,
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
-                         tensor_cores=0 if args.no_tensor_cores else (2 if args.tc_gemm else 1), krylov=1 if args.krylov == "bicgstab" else 0,
+                         tensor_cores=tc, krylov=1 if args.krylov == "bicgstab" else 0,
+                         precond={"gs": hz.HZ_PGS, "jacobi": hz.HZ_PJAC}[args.precond],
                          autotune=args.autotune, tol=args.tol, rhs_lanes=args.rhs_lanes, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
@@ -210,10 +268,9 @@ def run_ours(args, rank, world):
         return sts
 
     torch.cuda.synchronize()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step(f_dev, u_dev)
-    dist = world > 1
-    if dist:
+    if world > 1:
         import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize()
@@ -222,103 +279,56 @@ def run_ours(args, rank, world):
     # every member stream has finished when a step returns, so events on the first stream bracket all of them
     with Clocks(int(os.environ.get("LOCAL_RANK", 0))) as clk:
         ev0.record(streams[0])
-        for _ in range(args.steps):
+        for _ in range(steps):
             stats.append([st.as_dict() for st in step(f_dev, u_dev)])
         ev1.record(streams[0])
         torch.cuda.synchronize()
-    ms = reduce_max(ev0.elapsed_time(ev1) / args.steps, world)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+    ms = reduce_max(ev0.elapsed_time(ev1) / steps, world)
     mdof = sum(pb.n_x * pb.n_z for pb in pbs) / 1e6
-    value = job_throughput(world, B, mdof, ms)
-    # end-to-end through the same entry point with pinned host buffers
-    f_host = [torch.from_numpy(f).pin_memory() for _, f in items]
-    u_host = [torch.empty_like(x).pin_memory() for x in f_host]
-    for c in ctxs:
-        c.hz_set_device_ptrs(False)
-    fh, uh = [x.numpy() for x in f_host], [x.numpy() for x in u_host]
-    step(fh, uh)
-    torch.cuda.synchronize()
-    e_steps = max(1, min(args.steps, 3))
-    t0 = time.perf_counter()
-    for _ in range(e_steps):
-        step(fh, uh)
-    torch.cuda.synchronize()
-    e_ms = (time.perf_counter() - t0) * 1e3 / e_steps
-    for c in ctxs:
-        c.hz_set_device_ptrs(True)
     flat = [m for st in stats for m in st]
-    # kernel-class timings over the timed region
     kt_ms = np.sum([s["kt_ms"] for s in flat], axis=0)
     kt_n = np.sum([s["kt_launches"] for s in flat], axis=0)
     kt_b = np.sum([s["kt_bytes"] for s in flat], axis=0)
     kt_f = np.sum([s["kt_flops"] for s in flat], axis=0)
-    names = ["cell_chain", "inner_chain", "batched_fes_gemm"]
-    top = int(np.argmax(kt_ms))
-    peaks, src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    # FP32 SIMT peak from unit counts and the maximum SM clock: 152 SMs x 128 FMA lanes x 2 flops
-    alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12 if prec == hz.HZ_MIXED else 1.25
-    gbs = kt_b[top] / (kt_ms[top] / 1e3) / 1e9 if kt_ms[top] > 0 else 0.0
-    tfl = kt_f[top] / (kt_ms[top] / 1e3) / 1e12 if kt_ms[top] > 0 else 0.0
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    # the kernel is bound by whichever roof it is closer to
-    if gbs / hbm >= tfl / alu_peak:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(gbs / hbm, 4)}
-    else:
-        roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
-                "frac": round(tfl / alu_peak, 4)}
-    traffic, traffic_src = None, None
-    if names[top] in DRAM_PER_ALGO and kt_n[top] > 0 and (names[top] != "cell_chain" or args.no_tensor_cores):
-        ratio, traffic_src = DRAM_PER_ALGO[names[top]]
-        traffic = round(float(ratio * kt_b[top] / kt_n[top]))
-    roof.update({"kernel": names[top], "traffic": traffic, "traffic_source": traffic_src,
-                 "peak_source": (("derived from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x the max SM clock"
-                                  " (" + src + "); a register-only FMA loop measured 73.3 TFLOP/s")
-                                 if prec == hz.HZ_MIXED else "FP64 DFMA, a register-only loop measured 1.255 TFLOP/s")
-                                if roof["bound"] == "alu" else src + " copy GB/s",
-                 "launches": int(kt_n[top]), "avg_ms": round(float(kt_ms[top] / max(kt_n[top], 1)), 4),
-                 "share_of_step": round(float(kt_ms[top] / (ms * args.steps)), 3),
-                 "classes_ms_per_step": {n: round(float(v / args.steps), 3) for n, v in zip(names, kt_ms)},
-                 # every timed class: algorithmic rates over its own event time, against both roofs
-                 "classes": {n: {"ms_per_step": round(float(kt_ms[i] / args.steps), 3),
-                                 "launches_per_step": round(float(kt_n[i] / args.steps), 1),
-                                 "gb_s": round(float(kt_b[i] / (kt_ms[i] / 1e3) / 1e9), 1) if kt_ms[i] > 0 else 0.0,
-                                 "tflop_s": round(float(kt_f[i] / (kt_ms[i] / 1e3) / 1e12), 3) if kt_ms[i] > 0 else 0.0,
-                                 "frac_hbm": round(float(kt_b[i] / (kt_ms[i] / 1e3) / 1e9 / hbm), 4) if kt_ms[i] > 0 else 0.0,
-                                 "frac_alu": round(float(kt_f[i] / (kt_ms[i] / 1e3) / 1e12 / alu_peak), 4)
-                                 if kt_ms[i] > 0 else 0.0}
-                             for i, n in enumerate(names)}})
-    if prec == hz.HZ_MIXED and not args.no_tensor_cores and kt_ms[0] > 0:
-        # the cell solves run on the tensor cores: 3 TF32 products per real product, against
-        # the TF32 rate measured by an MMA-rate probe (1286 TFLOP/s at N >= 128)
-        roof["classes"]["cell_chain"]["frac_tensor_3xtf32"] = round(float(kt_f[0] / (kt_ms[0] / 1e3) / 1e12 /
-                                                                          (1286.0 / 3)), 4)
     last = stats[-1]
-    pb = pbs[0]
-    nbytes = sum(f.nbytes for _, f in items)
     solve = [{"iterations": m["iterations"], "refinements": m["refinements"], "resid": m["resid"],
               "gmres_resid": m["gmres_resid"],
               "phase_ms": {k: round(m[k], 2) for k in ("t_local_ms", "t_gmres_ms", "t_recon_ms", "t_resid_ms",
                                                        "t_total_ms")}} for m in last]
     solve[0]["t_factor_s"] = round(t_factor, 2)
-    out = {
-        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64+f64" if prec == hz.HZ_MIXED else "c128", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: " + describe(wl, pbs, B, args.precision),
-                   "B": B, "n_x": pb.n_x, "n_z": pb.n_z, "L": pb.L, "C": pb.C, "precision": args.precision,
-                   "frequencies": len(pbs), "krylov": args.krylov, "autotune": args.autotune,
-                   "rhs_lanes": args.rhs_lanes, "tensor_cores": "off" if args.no_tensor_cores else
-                   ("cell solves + batched products" if args.tc_gemm else "cell solves"),
-                   "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
-        "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
-        "solve": solve[0] if len(solve) == 1 else solve,
-        "roofline": roof,
-        "e2e": {"value": round(world * B * mdof / (e_ms / 1e3), 3), "unit": UNIT,
-                "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)},
-        "clocks": clk.summary(),
-    }
-    if args.measure_update:
+    out = {"workload": f"{workload}: " + describe(wl, pbs, B, precision),
+           "value": round(job_throughput(world, B, mdof, ms), 3), "unit": UNIT, "ms_per_step": round(ms, 3),
+           "steps": steps, "warmup": warmup, "B": B, "n_x": pbs[0].n_x, "n_z": pbs[0].n_z, "L": pbs[0].L,
+           "C": pbs[0].C, "frequencies": len(pbs),
+           "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
+           "solve": solve[0] if len(solve) == 1 else solve,
+           "roofline": roofline(kt_ms, kt_n, kt_b, kt_f, ms, steps, mixed, tc > 0, workload),
+           "clocks": clk.summary()}
+    if e2e:
+        # end-to-end through the same entry point with pinned host buffers: the copies of the
+        # sources in and the fields out are inside the timed region
+        f_host = [torch.from_numpy(f).pin_memory() for _, f in items]
+        u_host = [torch.empty_like(x).pin_memory() for x in f_host]
+        for c in ctxs:
+            c.hz_set_device_ptrs(False)
+        fh, uh = [x.numpy() for x in f_host], [x.numpy() for x in u_host]
+        step(fh, uh)
+        torch.cuda.synchronize()
+        e_steps = max(1, min(steps, 3))
+        t1 = time.perf_counter()
+        for _ in range(e_steps):
+            step(fh, uh)
+        torch.cuda.synchronize()
+        e_ms = reduce_max((time.perf_counter() - t1) * 1e3 / e_steps, world)
+        for c in ctxs:
+            c.hz_set_device_ptrs(True)
+        nbytes = sum(f.nbytes for _, f in items)
+        out["e2e"] = {"value": round(job_throughput(world, B, mdof, e_ms), 3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(nbytes), "d2h_bytes_per_step": int(nbytes)}
+    if measure_update:
         # local model update outside the timed region: a patch of the medium inside one
         # cell of the middle layer changes; only that layer is re-factored
         pb0, ctx0 = pbs[0], ctxs[0]
@@ -330,43 +340,119 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t1 = time.time()
         nlay = ctx0.hz_update_model(m1)
-        t_upd = time.time() - t1
-        out["local_update"] = {"layers_refactored": nlay, "layers": pb0.L, "t_update_s": round(t_upd, 3),
+        out["local_update"] = {"layers_refactored": nlay, "layers": pb0.L, "t_update_s": round(time.time() - t1, 3),
                                "t_factor_s": round(t_factor / len(ctxs), 3), "patch": "8 x 8 points, m x 1.05"}
     for c in ctxs:
         c.close()
+    del f_dev, u_dev
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    main_ = measure(args, args.workload, args.precision, args.steps, args.warmup, world, e2e=True,
+                    measure_update=args.measure_update)
+    out = {
+        "metric": METRIC, "value": main_["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main_["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "c128", "data": "synthetic",
+        "config": {"workload": main_["workload"], "B": main_["B"], "n_x": main_["n_x"], "n_z": main_["n_z"],
+                   "L": main_["L"], "C": main_["C"], "precision": args.precision,
+                   "frequencies": main_["frequencies"], "krylov": args.krylov, "precond": args.precond,
+                   "autotune": args.autotune, "rhs_lanes": args.rhs_lanes,
+                   "tensor_cores": "off" if args.no_tensor_cores else
+                   ("cell solves + batched products" if args.tc_gemm else "cell solves"),
+                   "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
+        "gpu_launches": main_["gpu_launches"],
+        "solve": main_["solve"],
+        "roofline": main_["roofline"],
+        "e2e": main_["e2e"],
+        "clocks": main_["clocks"],
+    }
+    if "local_update" in main_:
+        out["local_update"] = main_["local_update"]
+    if not args.no_extra:
+        if args.workload != SECONDARY_WORKLOAD:
+            sec = measure(args, SECONDARY_WORKLOAD, args.precision, args.steps, args.warmup, world)
+            out["secondary"] = {k: sec[k] for k in ("workload", "value", "unit", "ms_per_step", "steps", "warmup",
+                                                    "gpu_launches", "solve", "roofline", "clocks")}
+        if args.precision == "mixed":
+            # the plain FP64 form of the same workload, for "mixed beats FP64 at equal final residual"
+            k = max(1, min(args.steps, 2))
+            f64 = measure(args, args.workload, "fp64", k, 1, world)
+            out["fp64"] = {k_: f64[k_] for k_ in ("workload", "value", "unit", "ms_per_step", "steps", "warmup",
+                                                  "solve", "clocks")}
+            out["fp64"]["mixed_over_fp64"] = round(out["value"] / f64["value"], 2) if f64["value"] else None
     return out
 
 
 # ------------------------------------------------- oracle (CPU) timing ---
-def oracle_sample(wl, rows=4, nthreads=None):
-    """Time the CPU oracle (banded LU) on a full-width strip of the workload's
-    medium and scale to the full grid: with x-fastest ordering the band width
-    is the full extended width, so the cost per grid row is the same as for
-    the full problem.  A multi-frequency workload times one strip per
+ORACLE_ROWS = 12
+
+
+def oracle_sample(wl, rows=ORACLE_ROWS):
+    """Time the CPU oracle on a bounded sample of the workload: the row-block
+    elimination (block-tridiagonal over grid rows, LAPACK-pivoted Schur blocks)
+    of the leading `rows` grid rows of the full-width operator, factor plus the
+    forward and backward substitution of all B sources.  Every row of the
+    elimination costs the same (one NX x NX Schur block), so the time scales by
+    rows to the whole grid.  A multi-frequency workload times one sample per
     frequency."""
     import oracle as O
     t_full = t_fac = t_sol = 0.0
     work = 0.0
     for pb, f in make_problems(wl):
+        # the top strip of the medium (its own bottom PML) holds the sampled rows; the
+        # rows eliminated cost what the same rows of the whole grid cost
         p = pb.n_pml
-        NZs = rows + 2 * p
-        m = np.ascontiguousarray(pb.m[:NZs, :])
-        fs = np.ascontiguousarray(f[:, :NZs, :])
-        box = O.Box(m, pb.n_x, rows, p, pb.omega, pb.h, O.default_pml_C(pb.m))
+        nz_s = max(1, rows - 2 * p + 1)
+        strip = O.Box(np.ascontiguousarray(pb.m[:nz_s + 2 * p]), pb.n_x, nz_s, p, pb.omega, pb.h,
+                      O.default_pml_C(pb.m))
+        fs = np.ascontiguousarray(f[:, :nz_s + 2 * p])
         t0 = time.perf_counter()
-        fac = box.factor(order=1)
+        fac = strip.factor_rows(rows=rows)
         t1 = time.perf_counter()
         fac.solve(fs)
         t2 = time.perf_counter()
-        scale = (pb.n_z + 2 * p) / NZs
+        scale = (pb.n_z + 2 * p) / fac.NZ
         t_full += (t2 - t0) * scale
         t_fac += t1 - t0
         t_sol += t2 - t1
         work += f.shape[0] * pb.n_x * pb.n_z / 1e6
-    value = work / t_full
-    return value, {"factor_s": round(t_fac, 2), "solve_s": round(t_sol, 2), "rows": rows, "scale": scale,
-                   "work": work}
+    return work / t_full, {"factor_s": round(t_fac, 3), "solve_s": round(t_sol, 3), "rows": rows,
+                           "scale": round(scale, 2), "work": work, "sample_s": round(t_fac + t_sol, 3)}
+
+
+def _sample_text(det, B):
+    return (f"row-block elimination of the leading {det['rows']} grid rows of the full-width operator (on the "
+            f"top strip of the medium) "
+            f"(factor + forward/backward substitution of {B} sources), time scaled x{det['scale']:.1f} to the "
+            f"whole grid")
+
+
+def oracle_single_thread(workload, B):
+    """The same sample with the BLAS limited to one thread (a child process, so the
+    thread count is fixed before numpy loads)."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", "--workload", workload, "--B", str(B)]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, never fatal for the GPU line
+        return {"error": str(e)[:200]}
+
+
+def cpu_baseline(workload, B):
+    wl = dict(WORKLOADS[workload])
+    wl["B"] = B
+    v, det = oracle_sample(wl)
+    one = oracle_single_thread(workload, B)
+    return {"value": round(v, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": _sample_text(det, B) + f"; measured sample time {det['sample_s']} s",
+            "single_thread": one}
 
 
 def run_reference(args, rank, world):
@@ -374,33 +460,38 @@ def run_reference(args, rank, world):
     if args.B:
         wl["B"] = args.B
     cores = os.cpu_count()
-    steps = []
+    vals, samples = [], []
     det = None
     for _ in range(args.warmup + args.steps):
         v, det = oracle_sample(wl)
-        steps.append(v)
-    v = float(np.mean(steps[args.warmup:]))
+        vals.append(v)
+        samples.append(det["sample_s"])
+    v = float(np.mean(vals[args.warmup:]))
+    sample_ms = float(np.mean(samples[args.warmup:])) * 1e3
     ms = det["work"] / v * 1e3
-    sample = (f"banded LU (x-fastest, band = full extended width) of a {det['rows']}-row full-width strip of the "
-              f"workload, factor + {wl['B']} solves, time scaled by {det['scale']:.1f} to the full grid")
     return {"impl": "reference", "metric": METRIC, "value": round(v, 5), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1),
+            "ms_per_step_is": f"extrapolated: the measured sample ({round(sample_ms, 1)} ms per step) x{det['scale']}",
+            "sample_ms_per_step": round(sample_ms, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
             "config": {"workload": args.workload, "B": wl["B"]},
-            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(v, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": _sample_text(det, wl["B"])},
             "e2e": {"value": round(v, 5), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="smooth1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precond", default="gs", choices=["gs", "jacobi"], help="outer preconditioner")
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workload and the FP64 form")
     ap.add_argument("--no-tensor-cores", action="store_true", help="mixed precision: cell solves on the SIMT pipes")
     ap.add_argument("--measure-update", action="store_true",
                     help="after the timed steps, time a local model update of one patch (reported, not timed)")
@@ -411,28 +502,36 @@ def main():
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
     ap.add_argument("--tol", type=float, default=0.0, help="GMRES tolerance of the first pass (0: library default)")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_sample:  # child process of oracle_single_thread
+        wl = dict(WORKLOADS[args.workload])
+        if args.B:
+            wl["B"] = args.B
+        v, det = oracle_sample(wl, rows=2)
+        print(json.dumps({"value": round(v, 6), "unit": UNIT, "cores": 1, "sample": _sample_text(det, wl["B"]),
+                          "sample_s": det["sample_s"]}))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
-    if world > 1 and args.impl == "ours":
+    if args.gpus != world:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={world}; launch one process per GPU with "
+              f"torch.distributed.run --nproc-per-node {args.gpus}", file=sys.stderr)
+        sys.exit(2)
+    if args.impl == "reference":
+        # the CPU oracle runs once, on rank 0; the other ranks exit without work
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    if world > 1:
         import torch
         import torch.distributed as tdist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
-    if args.impl == "reference":
-        if rank == 0:
-            print(json.dumps(run_reference(args, rank, world)), flush=True)
-        return
     out = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            wl = dict(WORKLOADS[args.workload])
-            if args.B:
-                wl["B"] = args.B
-            v, det = oracle_sample(wl)
-            out["cpu_baseline"] = {"value": round(v, 5), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                                   "sample": f"{det['rows']}-row full-width strip, band LU factor + solves, "
-                                             f"scaled x{det['scale']:.1f} to the full grid"}
+            out["cpu_baseline"] = cpu_baseline(args.workload, out["config"]["B"])
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as tdist

@@ -167,9 +167,9 @@ class Box:
         _load().hzo_stencil(ctypes.byref(self._c), out.ctypes.data)
         return out
 
-    def factor_rows(self, keep_every: int = 1) -> "RowBlockFactor":
+    def factor_rows(self, keep_every: int = 1, rows: int | None = None) -> "RowBlockFactor":
         """Block-tridiagonal elimination over grid rows (see RowBlockFactor)."""
-        return RowBlockFactor(self, keep_every)
+        return RowBlockFactor(self, keep_every, rows)
 
 
 class Factor:
@@ -219,15 +219,19 @@ class RowBlockFactor:
     NX x NX.  keep_every = k > 1 keeps every k-th factor only and recomputes
     the others a segment at a time when a solve needs them (the same
     arithmetic from the same inputs; 1/k of the memory, up to three times the
-    factorization work).
+    factorization work).  rows = r eliminates only the leading r grid rows,
+    i.e. solves the leading principal r x r block system of H (every row of
+    the elimination costs the same, so this times a bounded sample of it).
     """
 
-    def __init__(self, box: Box, keep_every: int = 1):
+    def __init__(self, box: Box, keep_every: int = 1, rows: int | None = None):
         import scipy.linalg as sl
         self._sl = sl
         self.box = box
         st = box.stencil()
         self.NZ, self.NX = box.shape
+        if rows is not None:
+            self.NZ = max(1, min(int(rows), self.NZ))
         self.A, self.Cp = st[0], st[4]          # couplings of row z to rows z-1 and z+1
         self.lo, self.di, self.up = st[1], st[2], st[3]
         self.k = max(1, int(keep_every))
@@ -264,7 +268,7 @@ class RowBlockFactor:
         """H^{-1} f for f of shape (..., NZ, NX)."""
         sl, NZ, NX, k = self._sl, self.NZ, self.NX, self.k
         lead = f.shape[:-2]
-        F = np.asarray(f, dtype=np.complex128).reshape((-1, NZ, NX))
+        F = np.asarray(f, dtype=np.complex128).reshape((-1,) + f.shape[-2:])[:, :NZ, :]
         Y = np.empty((NZ, NX, F.shape[0]), dtype=np.complex128)
         seg = {}
 

@@ -1,15 +1,21 @@
 """Parity at the full workload sizes, in the launch configuration the
-benchmark times (mixed precision, 1e-8 refinement target), through properties
-that hold at any size: the FP64 residual ||H u - f|| / ||f|| of the GPU
-solution measured with the oracle's own Appendix A operator on the CPU, and
-for the gradient workload the adjoint gradient against central differences
-of the misfit at sampled nodes.
+benchmark times (mixed precision, 1e-8 refinement target).
 
-- 1024 x 1024 + 20 PML, L = C = 16, 64 point sources on row 1 (smooth random)
-- 2000 x 4000 + 30 PML, L = 40 x C = 20, 16 sources (layered, faulted)
+Element by element against the oracle's direct solve (relative L2 error per
+source: <= 1e-5 mixed, <= 1e-8 FP64):
+- 1024 x 1024 + 20 PML, L = C = 16, 64 point sources on row 1 (smooth
+  random), every source, both precisions, against the oracle's row-block
+  elimination of the whole grid (19 GB of Schur factors on the host);
+- the layered, faulted medium at 1000 x 2000 + 30 PML with L = 20 x C = 10:
+  the 2000 x 4000 generator halved in each direction, so layers and cells
+  keep the 100 x 100 shape of the full workload (the full grid's direct
+  solve needs 275 GB of factors);
 - 512 x 512 + 20 PML, uneven 24-64 point layers and cells, 6/8/10 points per
-  wavelength, 256 sources each, solved as one group
-- 512 x 512 + 20 PML, L = C = 8, 32 sources, misfit gradient
+  wavelength, 256 sources each, solved as one group, every source.
+At the full 2000 x 4000 size, through the FP64 residual ||H u - f|| / ||f||
+of the GPU solution measured with the oracle's Appendix A operator.  For the
+gradient workload (512 x 512, L = C = 8, 32 sources) the adjoint gradient
+against central differences of the misfit at sampled nodes.
 """
 import numpy as np
 import pytest
@@ -32,16 +38,47 @@ def _solve(pb, f, C_pml, precision=None, **kw):
     return ctx, u, st
 
 
-def test_smooth1024_residual():
+def _rel_per_source(u, ref):
+    d = (u - ref).reshape(u.shape[0], -1)
+    return np.linalg.norm(d, axis=1) / np.linalg.norm(ref.reshape(u.shape[0], -1), axis=1)
+
+
+def test_smooth1024_elementwise_against_oracle():
     pb = I.smooth_random(1024, n_pml=20, L=16, C=16, seed=2, ppw=10.0)
     f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, 64)
     C_pml = O.default_pml_C(pb.m)
+    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
     ctx, u, st = _solve(pb, f, C_pml)
     ctx.close()
-    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
     res = O.relative_residual(box, u, f)
     assert np.all(res < 1e-8), res.max()
     assert abs(res.max() - st.resid) <= 1e-3 * st.resid + 1e-12  # the library's own FP64 residual agrees
+    ctx, u64, st64 = _solve(pb, f, C_pml, precision=hz.HZ_FP64)
+    ctx.close()
+    ref = box.factor_rows().solve(f)
+    e_mixed, e_fp64 = _rel_per_source(u, ref), _rel_per_source(u64, ref)
+    print(f"\n1024^2 smooth, 64 sources: relative L2 vs oracle mixed max {e_mixed.max():.3e} "
+          f"median {np.median(e_mixed):.3e} (residual {st.resid:.2e}); FP64 max {e_fp64.max():.3e}")
+    assert np.all(e_mixed <= 1e-5), e_mixed.max()
+    assert np.all(e_fp64 <= 1e-8), e_fp64.max()
+
+
+def test_layered_faulted_twin_1000x2000_elementwise_against_oracle():
+    pb = I.layered_faulted(n_x=1000, n_z=2000, n_pml=30, L=20, C=10, seed=3, ppw=8.0)
+    assert pb.n_x // pb.C == 100 and pb.n_z // pb.L == 100   # the cells of the 2000 x 4000 workload
+    f = I.point_sources_row(pb.n_x, pb.n_z, pb.n_pml, pb.h, 16)
+    C_pml = O.default_pml_C(pb.m)
+    box = O.Box(pb.m, pb.n_x, pb.n_z, pb.n_pml, pb.omega, pb.h, C_pml)
+    ctx, u, st = _solve(pb, f, C_pml)
+    ctx.close()
+    ctx, u64, _ = _solve(pb, f, C_pml, precision=hz.HZ_FP64)
+    ctx.close()
+    ref = box.factor_rows().solve(f)
+    e_mixed, e_fp64 = _rel_per_source(u, ref), _rel_per_source(u64, ref)
+    print(f"\n1000x2000 layered twin, 16 sources: relative L2 vs oracle mixed max {e_mixed.max():.3e} "
+          f"(residual {st.resid:.2e}); FP64 max {e_fp64.max():.3e}")
+    assert np.all(e_mixed <= 1e-5), e_mixed.max()
+    assert np.all(e_fp64 <= 1e-8), e_fp64.max()
 
 
 def test_layered_faulted_2000x4000_residual():
@@ -55,7 +92,7 @@ def test_layered_faulted_2000x4000_residual():
     assert np.all(res < 1e-8), res.max()
 
 
-def test_uneven_multifrequency_512_group_residual():
+def test_uneven_multifrequency_512_group_elementwise_against_oracle():
     probs = I.uneven_multifreq(n=512, n_pml=20, seed=4, part_seed=40)
     ctxs, fs, boxes = [], [], []
     for pb in probs:
@@ -74,6 +111,9 @@ def test_uneven_multifrequency_512_group_residual():
     for box, u, f, st in zip(boxes, us, fs, sts):
         res = O.relative_residual(box, u, f)
         assert np.all(res < 1e-8), res.max()
+        e = _rel_per_source(u, box.factor_rows().solve(f))
+        print(f"\n512^2 uneven, omega {box.omega:.1f}, 256 sources: relative L2 vs oracle max {e.max():.3e}")
+        assert np.all(e <= 1e-5), e.max()
 
 
 def test_gradient_512_against_central_differences():
