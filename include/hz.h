@@ -28,6 +28,14 @@
  *     a message for the last failure on that context.
  *   - Calls on one context must not overlap; distinct contexts are
  *     independent (they may share a stream).
+ *   - Fault injection for tests of the failure paths (read at hz_setup from
+ *     the environment variable HZ_FAULT; unset in normal use):
+ *       alloc[:n]  the n-th device allocation of the context, counted from
+ *                  hz_setup, fails (HZ_ENOMEM);
+ *       singular   the factorization reports a zero pivot (HZ_ESINGULAR);
+ *       nan        a NaN enters the polarized right-hand side of each solve
+ *                  pass (the solve returns HZ_ENOTCONV, residual NaN);
+ *       noconv     one GMRES iteration and one pass per solve (HZ_ENOTCONV).
  */
 #ifndef HZ_H
 #define HZ_H
@@ -101,6 +109,11 @@ typedef struct {
                            workspaces but the context's factorization, so that
                            the latency-bound sweep chains of the groups overlap on
                            the GPU (1, the default: one group) */
+    double wait_ms;     /* limit of every bounded device wait (the mbarrier waits of
+                           the inner sweep, the tensor-core kernels and the
+                           cluster exchange), in milliseconds; a wait that runs
+                           out makes the call return HZ_ETIMEOUT with its results
+                           invalid, the context staying usable (<= 0: 1000) */
 } hz_opts;
 
 typedef struct {
@@ -283,6 +296,14 @@ hz_status hz_residual(hz_ctx *ctx, const double *u, const double *f, int B, doub
  * Errors: HZ_EINVAL (NULL pointer, B out of 1..256, u/f/res not device
  * memory of the context's device, another device current), HZ_ECUDA. */
 hz_status hz_residual_noalloc(hz_ctx *ctx, const double *u, const double *f, int B, double *res);
+
+/* Check of the timeout path (not in the paper): launches one thread block that
+ * waits, through the same bounded wait every kernel of the library uses, on an
+ * mbarrier that nothing completes, so the wait runs out after opts.wait_ms.
+ * Returns HZ_ETIMEOUT when the limit and the error report work (the context
+ * stays usable; nothing else is launched), HZ_OK if the wait completed (it
+ * cannot), HZ_ECUDA on a CUDA failure. */
+hz_status hz_check_timeout(hz_ctx *ctx);
 
 /* Switch the pointer mode of later calls (same meaning as opts.device_ptrs). */
 hz_status hz_set_device_ptrs(hz_ctx *ctx, int device_ptrs);

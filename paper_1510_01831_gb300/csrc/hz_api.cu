@@ -2,6 +2,7 @@
 // error capture.  The numerical work is in hz_factor.cu and hz_solve.cu.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "hz_ctx.cuh"
@@ -144,6 +145,24 @@ void hz_default_opts(hz_opts *o) {
     o->pml_C = 0.0;
     o->tensor_cores = 1;
     o->rhs_lanes = 1;
+    o->wait_ms = 1000.0;
+}
+
+// HZ_FAULT=alloc[:n] | singular | nan | noconv (documented in hz.h)
+static void read_fault(hz_ctx *c) {
+    const char *e = std::getenv("HZ_FAULT");
+    if (!e || !*e) return;
+    const std::string v(e);
+    if (v.rfind("alloc", 0) == 0) {
+        c->fault = hz_ctx::FAULT_ALLOC;
+        if (v.size() > 6 && v[5] == ':') c->fault_n = std::max(1LL, std::atoll(v.c_str() + 6));
+    } else if (v == "singular") {
+        c->fault = hz_ctx::FAULT_SINGULAR;
+    } else if (v == "nan") {
+        c->fault = hz_ctx::FAULT_NAN;
+    } else if (v == "noconv") {
+        c->fault = hz_ctx::FAULT_NOCONV;
+    }
 }
 
 hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega, double h, int n_pml, int L, int C,
@@ -159,6 +178,8 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     if (!c) return fail(nullptr, HZ_ENOMEM, "host allocation failed");
     hz_default_opts(&c->opts);
     if (opts) c->opts = *opts;
+    if (!(c->opts.wait_ms > 0)) c->opts.wait_ms = 1000.0;
+    read_fault(c);
     if (c->opts.restart < 1) c->opts.restart = 30;
     if (c->opts.max_it < 1) c->opts.max_it = 200;
     // mixed: the first pass only has to bring the volume residual near the FP32
@@ -672,6 +693,25 @@ hz_status hz_reconstruct(hz_ctx *c, const double *f, const double *tr, int B, do
             hz::comp_reconstruct<double2>(c, fd, td, B, ud);
         from_dev(c, u, ud, N * B);
         return HZ_OK;
+    });
+}
+
+hz_status hz_check_timeout(hz_ctx *c) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    return guarded(c, [&]() -> hz_status {
+        c->nl = 0;
+        HZ_CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+        hz::launch_wait_check(c->d_err, c->st, &c->nl);
+        int e = 0;
+        HZ_CU(cudaMemcpyAsync(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+        HZ_CU(cudaStreamSynchronize(c->st));
+        if (!e) return HZ_OK;
+        HZ_CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
+        HZ_CU(cudaStreamSynchronize(c->st));
+        char b[160];
+        snprintf(b, sizeof b, "a bounded device wait gave up after %.3f ms (timeout check)", c->opts.wait_ms);
+        c->err = b;
+        return HZ_ETIMEOUT;
     });
 }
 

@@ -11,6 +11,17 @@
 
 namespace hz {
 
+// ------------------------------------------------------ status block ---
+// Device status block of a context (16 bytes, 8-byte aligned): int 0 is the
+// error word (1 = a bounded wait in a kernel gave up), bytes 8-15 hold the
+// limit of every bounded wait in nanoseconds (hz_opts.wait_ms).  Kernels
+// receive the block as `int *err`.
+__device__ __forceinline__ unsigned long long wait_limit_ns(const int *err) {
+    return *reinterpret_cast<const volatile unsigned long long *>(err + 2);
+}
+// limit after a thread has given up once (draining its own copies)
+constexpr unsigned long long DRAIN_WAIT_NS = 1000000ull;
+
 // ------------------------------------------------------------ complex ---
 template <class T> struct cx;
 template <> struct cx<double> { using t = double2; };
@@ -182,6 +193,7 @@ void launch_gemm_tc(const GemmProb<float2> *d_probs, int nprob, int max_tiles, i
 size_t cell_chain_tc_smem(int max_nx);
 long long cell_tc_floats(int nx, int nz);
 void build_wtc(const CellDesc *d_cells, int ncell, const double2 *W, float *wtc, cudaStream_t st, int *nl);
+void launch_wait_check(int *err, cudaStream_t st, int *nl);
 void launch_cell_chain_tc(const CellDesc *d_cells, int ncell, const float *wtc, const float2 *cz, float2 *vol, int B,
                           int max_nx, int *err, cudaStream_t st, int *nl);
 template <class T2>

@@ -138,7 +138,13 @@ struct hz_ctx {
     double2 *stage = nullptr;
     long long stage_n = 0;
     int *d_flag = nullptr;
-    int *d_err = nullptr;  // device error word: 1 = a bounded wait in a kernel gave up
+    int *d_err = nullptr;  // device status block (error word + wait limit, see hz_common.cuh)
+    // host-side fault injection (environment HZ_FAULT, read at hz_setup): the
+    // failure paths of the library are exercised without faulting a GPU
+    enum { FAULT_NONE = 0, FAULT_ALLOC, FAULT_NAN, FAULT_NOCONV, FAULT_SINGULAR };
+    int fault = FAULT_NONE;
+    long long fault_n = 1;    // FAULT_ALLOC: the n-th device allocation after hz_setup fails
+    long long n_dalloc = 0;   // device allocations made so far
     int dev = 0;           // CUDA device current at hz_setup
     void *gemm_ws = nullptr;  // split-K partial tiles of the batched GEMM (sized for double2)
     float *wtc = nullptr;     // split TF32 W blocks of the tensor-core cell solve (null: SIMT cell solve)

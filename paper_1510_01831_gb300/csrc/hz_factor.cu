@@ -11,6 +11,11 @@
 void *hz_ctx::dalloc(size_t bytes) {
     void *p = nullptr;
     if (bytes == 0) bytes = 16;
+    if (fault == FAULT_ALLOC && ++n_dalloc == fault_n) {
+        char b[160];
+        snprintf(b, sizeof b, "device allocation of %.3f GB failed (injected by HZ_FAULT=alloc)", bytes / 1e9);
+        throw hz::HzError(HZ_ENOMEM, b);
+    }
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -268,10 +273,11 @@ static void to_f32(const double2 *a, float2 *b, long long n, cudaStream_t st, in
     (*nl)++;
 }
 
-static void check_info(int *d_info, cudaStream_t st, const char *what) {
+static void check_info(hz_ctx *c, int *d_info, cudaStream_t st, const char *what) {
     int info = 0;
     HZ_CU(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, st));
     HZ_CU(cudaStreamSynchronize(st));
+    if (c->fault == hz_ctx::FAULT_SINGULAR && !info) info = -1;  // as if a pivot had been exactly zero
     if (info) {
         char b[200];
         snprintf(b, sizeof b, "%s: zero pivot (code %d)", what, info);
@@ -322,7 +328,7 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
     launch_cell_coeffs(d_sub, nsub, c->d_m, c->NX, c->omega, c->h, c->pml_C, p, diag, cxv, czv, st, nl);
     double2 *cellW = fp64_buf(c->o64.cellW, c->tot_W, true);  // row padding stays zero
     launch_cell_factor(d_sub, nsub, diag, cxv, czv, cellW, c->max_nx, d_info, st, nl);
-    check_info(d_info, st, "cell factorization");
+    check_info(c, d_info, st, "cell factorization");
     c->dfree(diag);
     c->dfree(cxv);
 
@@ -479,7 +485,7 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
             }
             HZ_CU(cudaStreamSynchronize(st));  // host vectors reused next step
         }
-        check_info(d_info, st, "inner block LU");
+        check_info(c, d_info, st, "inner block LU");
         c->dfree(d_pr);
         c->dfree(d_mats);
         c->dfree(d_ns);

@@ -603,12 +603,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
     return t;
 }
-// wait for phase `parity` of an mbarrier for at most 1 s (1 ms once the
-// thread has already given up somewhere); on expiry set the error word and
-// `dead` and return false
+// wait for phase `parity` of an mbarrier for at most the context's wait limit
+// (1 ms once the thread has already given up somewhere); on expiry set the
+// error word and `dead` and return false
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned mb, unsigned parity, bool cluster_scope, bool &dead,
                                                   int *err) {
-    const unsigned long long limit_ns = dead ? 1000000ull : 1000000000ull;
+    const unsigned long long limit_ns = dead ? DRAIN_WAIT_NS : wait_limit_ns(err);
     unsigned long long t0 = 0;
     for (unsigned it = 0;; it++) {
         if (cluster_scope ? mbar_try_acq_cluster(mb, parity) : mbar_try(mb, parity)) return true;

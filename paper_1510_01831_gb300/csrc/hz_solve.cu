@@ -20,6 +20,9 @@ namespace hz {
 template <> Ops<double2> &ops<double2>(hz_ctx *c) { return c->o64; }
 template <> Ops<float2> &ops<float2>(hz_ctx *c) { return c->o32; }
 
+// max that keeps a NaN (std::max drops it when it comes second)
+static inline double nanmax(double a, double b) { return (std::isnan(a) || std::isnan(b)) ? NAN : std::max(a, b); }
+
 static inline int grid1(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 65535LL * 8); }
 
 // ----------------------------------------------------------- kernels ---
@@ -1196,8 +1199,12 @@ template <class T2> struct Fgmres {
     }
     void init_host() {  // after a sync
         for (int b = 0; b < B; b++) {
-            beta0[b] = std::sqrt(std::max(Hh()[b].x, 0.0));
-            if (!(beta0[b] > 0)) {
+            const double n2 = Hh()[b].x;
+            beta0[b] = std::sqrt(std::max(n2, 0.0));
+            if (!std::isfinite(n2)) {  // a non-finite right-hand side: stop, report NaN
+                conv[b] = 1;
+                res[b] = NAN;
+            } else if (!(beta0[b] > 0)) {
                 conv[b] = 1;
                 res[b] = 0;
             }
@@ -1297,7 +1304,12 @@ template <class T2> struct Fgmres {
             g[b][j + 1] = make_double2(-(snj.x * gj.x + snj.y * gj.y), -(snj.x * gj.y - snj.y * gj.x));
             kb[b] = j + 1;
             res[b] = std::hypot(g[b][j + 1].x, g[b][j + 1].y) / beta0[b];
-            if (res[b] <= tol) {
+            if (!std::isfinite(res[b]) || !std::isfinite(nrm)) {  // non-finite: stop this RHS, report NaN
+                res[b] = NAN;
+                kb[b] = j;  // the last column holds non-finite entries
+                act[b] = 0;
+                conv[b] = 1;
+            } else if (res[b] <= tol) {
                 conv[b] = 1;
                 act[b] = 0;
             } else if (nrm > 1e-300) {
@@ -1358,7 +1370,7 @@ template <class T2> struct Fgmres {
     GmresOut out() const {
         GmresOut o;
         o.iters = total;
-        for (int b = 0; b < B; b++) o.resid = std::max(o.resid, res[b]);
+        for (int b = 0; b < B; b++) o.resid = nanmax(o.resid, res[b]);
         return o;
     }
 };
@@ -1440,8 +1452,8 @@ template <class T2> struct Bicgstab {
         bool any = false;
         for (int b = 0; b < B; b++) {
             bnorm[b] = std::sqrt(std::max(Hh()[b].x, 0.0));
-            act[b] = bnorm[b] > 0;
-            res[b] = act[b] ? 1.0 : 0.0;
+            act[b] = bnorm[b] > 0 && std::isfinite(Hh()[b].x);
+            res[b] = act[b] ? 1.0 : (std::isfinite(Hh()[b].x) ? 0.0 : NAN);
             rho[b] = Hh()[b];  // <r^, r> with r^ = r = b
             any = any || act[b];
         }
@@ -1533,7 +1545,10 @@ template <class T2> struct Bicgstab {
             if (!act[b]) continue;
             res[b] = std::sqrt(std::max(Hh()[B + b].x, 0.0)) / bnorm[b];
             rho[b] = Hh()[b];
-            if (res[b] <= tol || std::hypot(rho[b].x, rho[b].y) == 0 ||
+            if (!std::isfinite(Hh()[B + b].x) || !std::isfinite(rho[b].x) || !std::isfinite(rho[b].y)) {
+                res[b] = NAN;  // non-finite: stop this RHS, report NaN
+                act[b] = 0;
+            } else if (res[b] <= tol || std::hypot(rho[b].x, rho[b].y) == 0 ||
                 std::hypot(omega[b].x, omega[b].y) == 0)
                 act[b] = 0;
             any = any || act[b];
@@ -1543,7 +1558,7 @@ template <class T2> struct Bicgstab {
     GmresOut out() const {
         GmresOut o;
         o.iters = total;
-        for (int b = 0; b < B; b++) o.resid = std::max(o.resid, res[b]);
+        for (int b = 0; b < B; b++) o.resid = nanmax(o.resid, res[b]);
         return o;
     }
 };
@@ -1716,9 +1731,18 @@ static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, doubl
     HZ_CU(cudaStreamSynchronize(c->st));
 }
 
+// the context's device status block: error word cleared, wait limit from the options
+static void init_status(hz_ctx *c) {
+    c->d_err = (int *)c->dalloc(16);
+    const double ms = c->opts.wait_ms > 0 ? c->opts.wait_ms : 1000.0;
+    int blk[4] = {0, 0, 0, 0};
+    const unsigned long long ns = (unsigned long long)(ms * 1e6);
+    std::memcpy(blk + 2, &ns, sizeof ns);
+    HZ_CU(cudaMemcpy(c->d_err, blk, sizeof blk, cudaMemcpyHostToDevice));
+}
+
 void init_global_alpha(hz_ctx *c) {
-    c->d_err = (int *)c->dalloc(sizeof(int));
-    HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
+    init_status(c);
     c->d_ax = (double2 *)c->dalloc(sizeof(double2) * c->NX);
     c->d_axh = (double2 *)c->dalloc(sizeof(double2) * (c->NX + 1));
     c->d_az = (double2 *)c->dalloc(sizeof(double2) * c->NZ);
@@ -1806,14 +1830,20 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
         for (size_t q = 0; q < idx.size(); q++) {
             hz_ctx *c = cs[idx[q]];
             const double tol = c->opts.tol, rtol = c->opts.refine_tol;
+            const int maxit = c->fault == hz_ctx::FAULT_NOCONV ? 1 : c->opts.max_it;
             double ptol = tol;
             // a pass on the residual only has to shrink it to the target, with a 10x margin
             if (pass > 0 && rtol > 0) ptol = std::min(0.1, std::max(tol, 0.1 * rtol / std::max(prev[idx[q]], 1e-300)));
             gtol[q] = ptol;
+            if (c->fault == hz_ctx::FAULT_NAN) {  // injected: a NaN in the polarized right-hand side
+                const double2 nan2 = make_double2(NAN, 0.0);
+                HZ_CU(cudaMemcpyAsync(Ws[idx[q]]->rhs64, &nan2, sizeof nan2, cudaMemcpyHostToDevice, c->st));
+                HZ_CU(cudaStreamSynchronize(c->st));
+            }
             if (bicg)
-                bm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
+                bm[q].init(c, *Ws[idx[q]], ptol, maxit, c->opts.precond);
             else
-                gm[q].init(c, *Ws[idx[q]], ptol, c->opts.max_it, c->opts.precond);
+                gm[q].init(c, *Ws[idx[q]], ptol, maxit, c->opts.precond);
         }
         if (bicg) {
             std::vector<Bicgstab<T2> *> bp;
@@ -1849,12 +1879,13 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
             worst[i] = 0;
             for (int b = 0; b < B; b++) {
                 rn[i][b] = fn[i][b] > 0 ? std::sqrt(W.rhost[b]) / fn[i][b] : 0.0;
-                worst[i] = std::max(worst[i], rn[i][b]);
+                worst[i] = nanmax(worst[i], rn[i][b]);
             }
             const double rtol = c->opts.refine_tol;
-            if (go.resid > gtol[q] && !c->mixed()) status[i] = HZ_ENOTCONV;
+            // a NaN compares false with everything: every convergence test is written so that it fails
+            if (!(go.resid <= gtol[q]) && (!c->mixed() || std::isnan(go.resid))) status[i] = HZ_ENOTCONV;
             prev[i] = worst[i];
-            if (rtol <= 0 || worst[i] <= rtol) {
+            if (rtol <= 0 || worst[i] <= rtol || std::isnan(worst[i]) || c->fault == hz_ctx::FAULT_NOCONV) {
                 live[i] = 0;
             } else {
                 src[i] = W.io;  // next pass solves for the correction from the FP64 residual
@@ -1865,7 +1896,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
         hz_ctx *c = cs[i];
         Work<T2> &W = *Ws[i];
         const double rtol = c->opts.refine_tol;
-        if (rtol > 0 && worst[i] > rtol) status[i] = HZ_ENOTCONV;
+        if (rtol > 0 && !(worst[i] <= rtol)) status[i] = HZ_ENOTCONV;
         stats[i].resid = worst[i];
         transpose_out(c, W.u, u_dev[i], (long long)c->NX * c->NZ, B);
     }
@@ -1919,8 +1950,7 @@ static hz_ctx *make_lane(hz_ctx *c) {
     s->parent = c;
     HZ_CU(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking));
     s->own_stream = true;
-    s->d_err = (int *)s->dalloc(sizeof(int));
-    HZ_CU(cudaMemset(s->d_err, 0, sizeof(int)));
+    init_status(s);
     return s;
 }
 

@@ -418,4 +418,24 @@ void launch_cell_chain_tc(const CellDesc *d_cells, int ncell, const float *wtc, 
     if (nl) (*nl)++;
 }
 
+// Timeout check: one warp; lane 0 initialises an mbarrier that expects one
+// arrival nobody makes and waits for it through the library's bounded wait,
+// which runs out after the context's limit and sets the error word.  Nothing
+// asynchronous is in flight, so the block simply ends.
+__global__ void k_wait_check(int *err) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        mb_init(su32(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        bool dead = false;
+        mb_wait(su32(&bar), 0u, dead, err);
+    }
+}
+
+void launch_wait_check(int *err, cudaStream_t st, int *nl) {
+    k_wait_check<<<1, 32, 0, st>>>(err);
+    HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+
 }  // namespace hz

@@ -29,9 +29,9 @@ __device__ __forceinline__ bool mb_try(unsigned mb, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait (1 s, or 1 ms once this thread has given up before)
+// bounded wait (the context's wait limit, or 1 ms once this thread has given up before)
 __device__ __forceinline__ bool mb_wait(unsigned mb, unsigned parity, bool &dead, int *err) {
-    const unsigned long long lim = dead ? 1000000ull : 1000000000ull;
+    const unsigned long long lim = dead ? DRAIN_WAIT_NS : wait_limit_ns(err);
     unsigned long long t0 = 0;
     for (unsigned it = 0;; it++) {
         if (mb_try(mb, parity)) return true;

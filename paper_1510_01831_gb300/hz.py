@@ -29,7 +29,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
 # every entry point declared in include/hz.h
 EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_update_model", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve",
            "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
-           "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
+           "hz_check_timeout", "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
 
 class HzError(RuntimeError):
@@ -46,7 +46,7 @@ class HzOpts(ctypes.Structure):
                 ("layer_rows", ctypes.POINTER(ctypes.c_int)), ("cell_cols", ctypes.POINTER(ctypes.c_int)),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("rhs_lanes", ctypes.c_int)]
+                ("rhs_lanes", ctypes.c_int), ("wait_ms", ctypes.c_double)]
 
 
 class HzStats(ctypes.Structure):
@@ -101,6 +101,8 @@ def load() -> ctypes.CDLL:
             L.hz_residual.argtypes = [vp, vp, vp, i, vp]
             L.hz_residual_noalloc.argtypes = [vp, vp, vp, i, vp]
             L.hz_residual_noalloc.restype = ctypes.c_int
+            L.hz_check_timeout.argtypes = [vp]
+            L.hz_check_timeout.restype = ctypes.c_int
             L.hz_set_device_ptrs.argtypes = [vp, i]
             L.hz_set_device_ptrs.restype = ctypes.c_int
             L.hz_device_bytes.argtypes = [vp]
@@ -145,7 +147,7 @@ class Context:
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
                  cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False,
-                 rhs_lanes=1):
+                 rhs_lanes=1, wait_ms=0.0):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -165,6 +167,8 @@ class Context:
         o.krylov = int(krylov)
         o.autotune = 1 if autotune else 0
         o.rhs_lanes = int(rhs_lanes)
+        if wait_ms > 0:
+            o.wait_ms = float(wait_ms)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")
@@ -326,6 +330,14 @@ class Context:
         _check(load().hz_residual_noalloc(self._ctx, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(f.data_ptr()),
                                           int(f.shape[0]), ctypes.c_void_p(res.data_ptr())), self._ctx)
         return res
+
+    def hz_check_timeout(self) -> int:
+        """Run the timeout check (a bounded device wait that nothing completes); returns
+        the status (HZ_ETIMEOUT when the timeout path works) without raising."""
+        return load().hz_check_timeout(self._ctx)
+
+    def last_error(self) -> str:
+        return load().hz_last_error(self._ctx).decode(errors="replace")
 
     def hz_set_device_ptrs(self, device: bool):
         _check(load().hz_set_device_ptrs(self._ctx, 1 if device else 0), self._ctx)

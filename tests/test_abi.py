@@ -32,6 +32,7 @@ def test_default_opts():
     o = hz.hz_default_opts()
     assert o.precision == hz.HZ_FP64 and o.precond == hz.HZ_PGS
     assert o.restart == 30 and o.max_it == 200 and o.refine_tol == 1e-8
+    assert o.wait_ms == 1000.0
 
 
 def test_struct_layouts_match_header():
