@@ -353,7 +353,7 @@ def run_ours(args, rank, world):
     import torch
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
-    main_ = measure(args, args.workload, args.precision, args.steps, args.warmup, world, e2e=True,
+    main_ = measure(args, args.workload, args.precision, args.steps, args.warmup, world, e2e=not args.no_e2e,
                     measure_update=args.measure_update)
     out = {
         "metric": METRIC, "value": main_["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -369,7 +369,7 @@ def run_ours(args, rank, world):
         "gpu_launches": main_["gpu_launches"],
         "solve": main_["solve"],
         "roofline": main_["roofline"],
-        "e2e": main_["e2e"],
+        "e2e": main_.get("e2e"),
         "clocks": main_["clocks"],
     }
     if "local_update" in main_:
@@ -492,6 +492,7 @@ def main():
     ap.add_argument("--B", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workload and the FP64 form")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end (host buffer) measurement")
     ap.add_argument("--no-tensor-cores", action="store_true", help="mixed precision: cell solves on the SIMT pipes")
     ap.add_argument("--measure-update", action="store_true",
                     help="after the timed steps, time a local model update of one patch (reported, not timed)")

@@ -173,6 +173,9 @@ template <class T2>
 void launch_gemm(const GemmProb<T2> *d_probs, int nprob, int max_tiles, int split, T2 *ws, int *cnt, cudaStream_t st,
                  int *nl, int cfg = 0);
 int gemm_tiles(int M, int N, int cfg);
+// skinny batched GEMM: every problem's N <= nmax <= 16; max_m = most rows of a problem
+template <class T2>
+void launch_gemm_skinny(const GemmProb<T2> *d_probs, int nprob, int max_m, int nmax, cudaStream_t st, int *nl);
 // batched GEMM tile (complex outputs) and K step
 constexpr int GBM = 64, GBN = 32, GBK = 16;
 // split-K is used while a launch has fewer tiles than this; its workspace

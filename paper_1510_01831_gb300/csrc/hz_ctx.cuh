@@ -28,6 +28,7 @@ template <class T2> struct ProbList {
     int tc_max_tiles = 0;         // tensor-core GEMM: most 128 x 64 tiles of a problem,
     int tc_kchunks = 0;           // most K chunks of 16 (both passes), and
     long long tc_tiles = 0;       // tiles of the whole list
+    int max_m = 0, max_n = 0;     // most rows and most right-hand-side columns of a problem
     double bytes = 0, flops = 0;  // algorithmic traffic and real flops of one launch
 };
 

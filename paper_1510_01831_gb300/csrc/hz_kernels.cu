@@ -233,6 +233,139 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmProb<T2> *__restrict__ p
     }
 }
 
+// two complex values held as one 16-byte (float) or two 16-byte (double) registers
+template <class T2> struct Pair {
+    T2 a, b;
+};
+template <class T2> __device__ __forceinline__ Pair<T2> ld_pair(const T2 *p) {
+    return Pair<T2>{p[0], p[1]};
+}
+template <> __device__ __forceinline__ Pair<float2> ld_pair<float2>(const float2 *p) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    return Pair<float2>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+// Skinny form of the batched GEMM for short lists whose right-hand-side panels
+// have at most 16 columns (a sweep step's products for batches of <= 16
+// sources): every operator element is read once and meets all N columns, and
+// the K loop keeps the next block's loads in flight.  A CTA of 4 warps owns 32
+// rows of one problem (lane = row); the K range of both operand pairs, laid end
+// to end, is cut into four slices, one per warp.  Per block of 32 K a warp
+// loads 32 x 32 of A (coalesced rows) and 32 x 16 of X into registers one block
+// ahead, stores them to its shared-memory area, and reads A back transposed
+// (its own row) and X as 16-byte broadcasts.  The four partial sums are added
+// in warp order (deterministic) and written with alpha / beta.
+constexpr int SK_NB = 16;
+template <class T2>
+__global__ void __launch_bounds__(128) k_gemm_skinny(const GemmProb<T2> *__restrict__ probs) {
+    __shared__ GemmProb<T2> P;
+    extern __shared__ __align__(16) unsigned char gsm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T2 *Aw = reinterpret_cast<T2 *>(gsm) + warp * (32 * 33 + 32 * SK_NB);  // [32 rows][33]
+    T2 *Xw = Aw + 32 * 33;                                                // [32 k][16]
+    if (tid == 0) P = probs[blockIdx.y];
+    __syncthreads();
+    const int M = P.M, N = P.N;
+    const int m0 = blockIdx.x * 32;
+    if (m0 >= M) return;  // uniform over the CTA
+    const int K1 = max(P.K, 0), Kt = K1 + max(P.K2, 0);
+    const int per = ((Kt + 3) / 4 + 31) / 32 * 32;
+    const int kb = min(Kt, warp * per), ke = min(Kt, kb + per);
+    // this warp's part of each pass (pass coordinates) and its blocks of 32
+    const int lo0 = min(kb, K1), hi0 = min(ke, K1), lo1 = max(kb - K1, 0), hi1 = max(ke - K1, 0);
+    const int c0 = hi0 > lo0 ? (hi0 - lo0 + 31) / 32 : 0, c1 = hi1 > lo1 ? (hi1 - lo1 + 31) / 32 : 0;
+    const int nblk = c0 + c1;
+    // X element this lane loads for row i of a block: lanes 0-15 even rows, 16-31 odd rows
+    const int xn = lane & 15, xr0 = lane >> 4;
+    T2 ra[32], rx[16];
+    auto load = [&](int t) {
+        const bool p2 = t >= c0;
+        const int k0 = p2 ? lo1 + 32 * (t - c0) : lo0 + 32 * t, hi = p2 ? hi1 : hi0;
+        const T2 *A = p2 ? P.A2 : P.A;
+        const long long lda = p2 ? P.lda2 : P.lda;
+        const int xseg = p2 ? P.xseg2 : P.xseg;
+        const long long ldx = p2 ? P.ldx2 : P.ldx;
+        const T2 *const *Xp = p2 ? P.X2 : P.X;
+        const bool kin = k0 + lane < hi;
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int gm = m0 + i;
+            ra[i] = (gm < M && kin) ? A[(long long)gm * lda + k0 + lane] : czero<T2>();
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int gk = k0 + 2 * i + xr0;
+            T2 v = czero<T2>();
+            if (gk < hi && xn < N) {
+                const int sg = gk / xseg;
+                v = Xp[sg][(long long)(gk - sg * xseg) * ldx + xn];
+            }
+            rx[i] = v;
+        }
+    };
+    T2 acc[SK_NB];
+#pragma unroll
+    for (int n = 0; n < SK_NB; n++) acc[n] = czero<T2>();
+    if (nblk > 0) load(0);
+    for (int t = 0; t < nblk; t++) {
+        __syncwarp();  // the previous block's reads of Aw / Xw are done
+#pragma unroll
+        for (int i = 0; i < 32; i++) Aw[i * 33 + lane] = ra[i];
+#pragma unroll
+        for (int i = 0; i < 16; i++) Xw[(2 * i + xr0) * SK_NB + xn] = rx[i];
+        __syncwarp();
+        if (t + 1 < nblk) load(t + 1);  // in flight during this block's products
+        const bool p2 = t >= c0;
+        const int k0 = p2 ? lo1 + 32 * (t - c0) : lo0 + 32 * t;
+        const int kc = min(32, (p2 ? hi1 : hi0) - k0);
+        for (int kk = 0; kk < kc; kk++) {
+            const T2 a = Aw[lane * 33 + kk];
+            const T2 *xr = Xw + kk * SK_NB;
+#pragma unroll
+            for (int n = 0; n < SK_NB; n += 2) {
+                const Pair<T2> x = ld_pair(xr + n);
+                cmac(acc[n], a, x.a);
+                cmac(acc[n + 1], a, x.b);
+            }
+        }
+    }
+    __syncthreads();  // every warp is done with its blocks: the buffers hold the partial sums now
+    T2 *red = reinterpret_cast<T2 *>(gsm);  // [4][32][16]
+#pragma unroll
+    for (int n = 0; n < SK_NB; n++) red[(warp * 32 + lane) * SK_NB + n] = acc[n];
+    __syncthreads();
+    const float al = P.alpha;
+    for (int e = tid; e < 32 * N; e += 128) {
+        const int r = e / N, n = e % N, m = m0 + r;
+        if (m >= M) continue;
+        T2 v = red[r * SK_NB + n];
+#pragma unroll
+        for (int w = 1; w < 4; w++) v = v + red[(w * 32 + r) * SK_NB + n];
+        v.x *= al;
+        v.y *= al;
+        const int sg = m / P.yseg;
+        T2 *row = P.Y[sg] + (long long)(m - sg * P.yseg) * P.ldy;
+        row[n] = P.beta ? row[n] + v : v;
+    }
+}
+
+template <class T2>
+void launch_gemm_skinny(const GemmProb<T2> *d_probs, int nprob, int max_m, int nmax, cudaStream_t st, int *nl) {
+    if (nprob <= 0 || max_m <= 0) return;
+    if (nmax > SK_NB) throw HzError(HZ_EINVAL, "skinny GEMM: too many columns");
+    dim3 grid((max_m + 31) / 32, nprob);
+    const size_t sm = sizeof(T2) * 4 * (32 * 33 + 32 * SK_NB);
+    static bool attr = false;
+    if (!attr) {  // FP64 needs more than the default 48 KB
+        HZ_CU(cudaFuncSetAttribute(k_gemm_skinny<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    k_gemm_skinny<T2><<<grid, 128, sm, st>>>(d_probs);
+    HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+template void launch_gemm_skinny<float2>(const GemmProb<float2> *, int, int, int, cudaStream_t, int *);
+
 int gemm_tiles(int M, int N, int cfg) {
     const int bm = cfg == 1 ? 32 : 64, bn = cfg == 2 ? 16 : 32;
     return ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
@@ -287,18 +420,6 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
-
-// two complex values held as one 16-byte (float) or two 16-byte (double) registers
-template <class T2> struct Pair {
-    T2 a, b;
-};
-template <class T2> __device__ __forceinline__ Pair<T2> ld_pair(const T2 *p) {
-    return Pair<T2>{p[0], p[1]};
-}
-template <> __device__ __forceinline__ Pair<float2> ld_pair<float2>(const float2 *p) {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    return Pair<float2>{make_float2(v.x, v.y), make_float2(v.z, v.w)};
-}
 
 template <class T2, int NT, int CH, int ST>
 __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__ cells, const T2 *__restrict__ W,
@@ -1299,7 +1420,10 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
     // default rule (what the tuner picks on the 1024 x 1024 and the multi-frequency
     // 512 x 512 shapes): 4-column tiles in 8-CTA clusters with 4 rows per warp, unless
     // that leaves SMs idle (a single layer with few right-hand sides): then 2-column
-    // tiles (8-CTA clusters in FP32, 16-CTA clusters in FP64)
+    // tiles (8-CTA clusters in FP32, 16-CTA clusters in FP64).  Interface blocks whose
+    // row slabs do not fit 8 CTAs (2nz' = 320 on the 2000 x 4000 shape): a single layer
+    // takes 4-column tiles in 16-CTA clusters, several layers 8-column tiles (the
+    // tuner's choices there).
     static int n_sm = 0;
     if (n_sm == 0) {
         int dev = 0;
@@ -1312,6 +1436,7 @@ void launch_inner_sweep(const LayerDesc *d_layers, const int *ids, int nlayer, c
     if (!ok) ok = inner_sweep_staged<T2, 4, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 8);
     if (!ok && nlayer == 1)
         ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 8);
+    if (!ok && nlayer == 1) ok = inner_sweep_staged<T2, 4, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st, 16);
     if (!ok) ok = inner_sweep_staged<T2, 8, 2>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) ok = inner_sweep_staged<T2, 8, 4>(d_layers, ids, nlayer, P, V, H, X, B, max_n2, err, st);
     if (!ok) {

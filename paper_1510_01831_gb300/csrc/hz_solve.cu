@@ -582,7 +582,7 @@ template <class T2> struct ListBuilder {
     hz_ctx *c;
     Ops<T2> &o;
     std::vector<GemmProb<T2>> v;
-    int max_tiles = 0, kmax = 0, max_tiles32 = 0, tc_max_tiles = 0, tc_kchunks = 0;
+    int max_tiles = 0, kmax = 0, max_tiles32 = 0, tc_max_tiles = 0, tc_kchunks = 0, max_m = 0, max_n = 0;
     long long tc_tiles = 0;
     ListBuilder(hz_ctx *c_, Ops<T2> &o_) : c(c_), o(o_) {}
 
@@ -600,6 +600,8 @@ template <class T2> struct ListBuilder {
         v.push_back(g);
         max_tiles = std::max(max_tiles, ((g.M + GBM - 1) / GBM) * ((g.N + GBN - 1) / GBN));
         max_tiles32 = std::max(max_tiles32, gemm_tiles(g.M, g.N, 1));
+        max_m = std::max(max_m, g.M);
+        max_n = std::max(max_n, g.N);
         kmax = std::max(kmax, std::max(g.K, 0) + std::max(g.K2, 0));
         const int tct = ((g.M + GT_M - 1) / GT_M) * ((g.N + GT_N - 1) / GT_N);
         tc_max_tiles = std::max(tc_max_tiles, tct);
@@ -701,6 +703,8 @@ template <class T2> struct ListBuilder {
         pl.tc_max_tiles = tc_max_tiles;
         pl.tc_kchunks = tc_kchunks;
         pl.tc_tiles = tc_tiles;
+        pl.max_m = max_m;
+        pl.max_n = max_n;
         pl.bytes = bytes;
         pl.flops = flops;
         bytes = flops = 0;
@@ -709,7 +713,7 @@ template <class T2> struct ListBuilder {
             HZ_CU(cudaMemcpy(pl.d, v.data(), sizeof(GemmProb<T2>) * v.size(), cudaMemcpyHostToDevice));
         }
         v.clear();
-        max_tiles = kmax = max_tiles32 = tc_max_tiles = tc_kchunks = 0;
+        max_tiles = kmax = max_tiles32 = tc_max_tiles = tc_kchunks = max_m = max_n = 0;
         tc_tiles = 0;
         return pl;
     }
@@ -755,6 +759,14 @@ static bool run_tc(hz_ctx *, const ProbList<double2> &) { return false; }
 template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
     if (!pl.n) return;
     if (run_tc(c, pl)) return;
+    // FP32 short lists (a sweep step's products) with narrow panels (<= 16 columns):
+    // the skinny kernel, whose K loop keeps the next block's loads in flight
+    if (sizeof(T2) == 8 && pl.max_n <= 16 && (long long)pl.n * pl.max_tiles32 < GEMM_SPLIT_TILES) {
+        c->kt_begin(2, pl.bytes, pl.flops);
+        launch_gemm_skinny<T2>(pl.d, pl.n, pl.max_m, pl.max_n, c->st, &c->nl);
+        c->kt_end();
+        return;
+    }
     // lists of fewer than GEMM_SPLIT_TILES 64 x 32 tiles (a sweep step's products) take
     // 32 x 32 tiles: measured 7-9 % faster on the E+S and 2B-wide W g steps, equal on the
     // others; long lists keep the larger tile
