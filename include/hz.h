@@ -60,6 +60,7 @@ typedef enum {
 enum { HZ_FP64 = 0, HZ_MIXED = 1 };            /* hz_opts.precision */
 enum { HZ_PGS = 0, HZ_PJAC = 1, HZ_PNONE = 2 }; /* hz_opts.precond */
 enum { HZ_GMRES = 0, HZ_BICGSTAB = 1 };         /* hz_opts.krylov */
+enum { HZ_INNER_LU = 0, HZ_INNER_NESTED = 1 };  /* hz_opts.inner */
 
 typedef struct {
     int precision;      /* HZ_FP64: every online operator in FP64.
@@ -114,6 +115,21 @@ typedef struct {
                            cluster exchange), in milliseconds; a wait that runs
                            out makes the call return HZ_ETIMEOUT with its results
                            invalid, the context staying usable (<= 0: 1000) */
+    int inner;          /* solver of each layer's local problem (Section 4.2):
+                           HZ_INNER_LU (default): the inner SIE over the cells by
+                           block LU (exact); HZ_INNER_NESTED: the inner nested
+                           polarized traces -- the layer's box with x and z
+                           swapped is a problem of the same form whose layers are
+                           the cells, solved by FGMRES on its polarized traces with
+                           the Gauss-Seidel sweeps over the cells, to inner_tol
+                           inside the preconditioner (the outer solver is then a
+                           flexible GMRES, which admits it); needs C >= 2,
+                           krylov HZ_GMRES and rhs_lanes 1, and hz_update_model is
+                           not available with it */
+    double inner_tol;   /* HZ_INNER_NESTED: relative GMRES tolerance of the inner
+                           solves inside the preconditioner (<= 0: 1e-6); the
+                           polarized operator, the Newton potentials and the
+                           reconstruction use 1e-10 (HZ_FP64) or 1e-6 (HZ_MIXED) */
 } hz_opts;
 
 typedef struct {
@@ -134,6 +150,8 @@ typedef struct {
     double kt_ms[3];
     double kt_bytes[3];    /* algorithmic bytes moved by those launches */
     double kt_flops[3];    /* algorithmic real flops of those launches */
+    int inner_iterations;  /* HZ_INNER_NESTED: GMRES iterations of all inner solves of
+                              the call (max over right-hand sides per inner solve) */
 } hz_stats;
 
 /* Fill opts with the defaults documented above (precision HZ_FP64). */

@@ -205,6 +205,15 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
         delete c;
         return fail(nullptr, HZ_EINVAL, "tensor_cores must be 0, 1 or 2");
     }
+    if (c->opts.inner != HZ_INNER_LU && c->opts.inner != HZ_INNER_NESTED) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "inner must be HZ_INNER_LU or HZ_INNER_NESTED");
+    }
+    if (c->opts.inner == HZ_INNER_NESTED && (C < 2 || c->opts.krylov != HZ_GMRES || c->opts.rhs_lanes != 1)) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "inner HZ_INNER_NESTED needs C >= 2, krylov HZ_GMRES and rhs_lanes 1");
+    }
+    if (!(c->opts.inner_tol > 0)) c->opts.inner_tol = 1e-6;
     c->n_x = n_x;
     c->n_z = n_z;
     c->p = n_pml;
@@ -263,12 +272,65 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
     return HZ_OK;
 }
 
+// Inner nested level (opts.inner = HZ_INNER_NESTED, Section 4.2): per layer, a
+// context of the layer's box with x and z swapped -- the layer's medium with
+// its artificial PML rows extending its first / last row, transposed; its
+// layers are the cells (one cell each) -- factored, with a lane for 2B-wide
+// applications.
+static void build_inner(hz_ctx *c) {
+    const int L = c->L, p = c->p, NX = c->NX;
+    for (hz_ctx *ic : c->inner_ctx) hz_destroy(ic);  // a failed earlier attempt
+    c->inner_ctx.assign(L, nullptr);
+    c->inner_wide.assign(L, nullptr);
+    for (int l = 0; l < L; l++) {
+        const hz::LayerDesc &ld = c->layers[l];
+        const int nz = ld.nz, n = ld.n;
+        std::vector<double> mt((size_t)NX * nz);
+        for (int r = 0; r < nz; r++) {
+            int g = ld.s + r;  // global array row of local row r
+            if (l > 0) g = std::max(g, ld.s + p);
+            if (l < L - 1) g = std::min(g, ld.s + n + p - 1);
+            for (int x = 0; x < NX; x++) mt[(size_t)x * nz + r] = c->h_m[(size_t)g * NX + x];
+        }
+        hz_opts io;
+        hz_default_opts(&io);
+        io.precision = c->opts.precision;
+        io.precond = HZ_PGS;
+        io.max_it = 60;
+        io.tol = c->opts.inner_tol;
+        io.refine_tol = 0.0;
+        io.max_refine = 1;
+        io.pml_C = c->pml_C;
+        io.layer_rows = c->cols.data();
+        io.device_ptrs = 1;
+        io.tensor_cores = c->opts.tensor_cores;
+        io.wait_ms = c->opts.wait_ms;
+        cudaStream_t s = nullptr;
+        HZ_CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        io.stream = s;
+        hz_ctx *ic = nullptr;
+        hz_status st = hz_setup(&ic, mt.data(), n, c->n_x, c->omega, c->h, p, c->C, 1, &io);
+        if (st != HZ_OK) {
+            cudaStreamDestroy(s);
+            throw HzError(st, std::string("inner context of a layer: ") + hz_last_error(nullptr));
+        }
+        ic->own_stream = true;
+        c->inner_ctx[l] = ic;
+        st = hz_factor(ic);
+        if (st != HZ_OK) throw HzError(st, "inner context of a layer: " + ic->err);
+        hz_ctx *w = hz::make_lane(ic);
+        ic->lanes.push_back(w);
+        c->inner_wide[l] = w;
+    }
+}
+
 hz_status hz_factor(hz_ctx *c) {
     if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
     if (c->factored) return HZ_OK;
     c->nl = 0;
     return guarded(c, [&]() -> hz_status {
         hz::factor_all(c);
+        if (c->nested()) build_inner(c);
         c->factored = true;
         return HZ_OK;
     });
@@ -278,6 +340,7 @@ hz_status hz_update_model(hz_ctx *c, const double *m_new, int *n_layers) {
     if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
     if (!m_new) return fail(c, HZ_EINVAL, "m_new must be non-NULL");
     if (!c->factored) return fail(c, HZ_ESTATE, "hz_update_model before hz_factor");
+    if (c->nested()) return fail(c, HZ_EINVAL, "hz_update_model is not available with the nested inner level");
     const int NX = c->NX, NZ = c->NZ;
     const long long N = (long long)NX * NZ;
     for (long long i = 0; i < N; i++)
@@ -732,6 +795,9 @@ static void destroy_one(hz_ctx *c);
 
 void hz_destroy(hz_ctx *c) {
     if (!c) return;
+    for (hz_ctx *ic : c->inner_ctx) hz_destroy(ic);  // their lanes go with them
+    c->inner_ctx.clear();
+    c->inner_wide.clear();
     for (hz_ctx *s : c->lanes) destroy_one(s);  // lanes own only their streams and workspaces
     c->lanes.clear();
     destroy_one(c);

@@ -57,6 +57,7 @@ template <class T2> struct Work {
     double2 *gsrc = nullptr;   // symmetric-form source / residual [NZ*NX][B]
     double2 *u = nullptr;      // FP64 solution [NZ*NX][B]
     double2 *io = nullptr;     // batch-outer staging [B][NZ*NX]
+    const double2 *cur_src = nullptr;  // source of the current pass (nested inner level: reconstruction)
     double *rnorm = nullptr;   // [B] norms
     double *rhost = nullptr;   // pinned [4B]
     int restart = 0;
@@ -163,6 +164,15 @@ struct hz_ctx {
     // error word and timers
     std::vector<hz_ctx *> lanes;
     hz_ctx *parent = nullptr;  // set on a lane
+    // inner nested polarized traces (opts.inner = HZ_INNER_NESTED): per layer, a
+    // context of the layer's box with x and z swapped (its layers are the cells),
+    // a lane of it for 2B-wide applications, and FP64 source / solution volumes
+    // on its grid ([2B][NX][nz_l]); inner GMRES iterations of the current call
+    std::vector<hz_ctx *> inner_ctx, inner_wide;
+    std::vector<double2 *> nsrc, nsol;
+    int n_bw = 0;
+    long long inner_its = 0;
+    bool nested() const { return opts.inner == HZ_INNER_NESTED; }
     bool own_stream = false;
     // allocations
     std::map<void *, size_t> allocs;
@@ -191,4 +201,5 @@ void comp_traces(hz_ctx *c, const double2 *u_dev, int B, double2 *tr_dev);
 template <class T2> void comp_reconstruct(hz_ctx *c, const double2 *f_dev, const double2 *tr_dev, int B, double2 *u_dev);
 template <class T2> Ops<T2> &ops(hz_ctx *c);
 template <class T2> Work<T2> &work(hz_ctx *c, int B);
+hz_ctx *make_lane(hz_ctx *c);
 }  // namespace hz

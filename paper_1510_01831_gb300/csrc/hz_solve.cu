@@ -1089,8 +1089,12 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     c->kt_end();
 }
 
+template <class T2> static void nested_apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, double2 *y);
+template <class T2> static void nested_precond(hz_ctx *c, Work<T2> &W, int kind);
+
 // polarized operator: y (FP64) = M x (x in the working precision)
 template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, double2 *y) {
+    if (c->nested()) return nested_apply_M(c, W, x, y);
     const int B = W.B;
     const long long n = (long long)c->L * 4 * c->NX * 2 * B;
     k_stage_M<T2><<<grid1(n), 256, 0, c->st>>>(x, W.lin, c->L, c->NX, B);
@@ -1108,6 +1112,7 @@ template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, dou
 // preconditioner on W.pb in place (input copied there by the caller):
 // kind 0 GS, 1 Jacobi, 2 down only, 3 up only, 4 reflections only
 template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind) {
+    if (c->nested()) return nested_precond(c, W, kind);
     const int L = c->L;
     if (kind == 0 || kind == 1 || kind == 2) {
         for (int k = 1; k <= L - 2; k++) {
@@ -1140,6 +1145,226 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
             run(c, W.f_up[k]);
             chain_layers(c, W, false, k + 1, 1);
             run(c, W.es_up[k]);
+        }
+    }
+}
+
+
+// ------------------------------------------ inner nested polarized traces ---
+// (opts.inner = HZ_INNER_NESTED, Section 4.2.)  A layer's local problem with x
+// and z swapped is a problem of the same form whose layers are the cells, so
+// the layer's inner context (hz_factor builds one per layer, with a lane for
+// 2B-wide applications) solves it with its own FGMRES on the cells' polarized
+// traces, preconditioned by the Gauss-Seidel sweeps over the cells.  Every
+// local solve of the online stage goes through these inner solves: the source
+// volume of each listed layer (its part of the source and the Appendix C
+// forcing of trace rows 0, 1, n, n+1, symmetric form) on the transposed layer
+// grid [Bw][NX][nz_l] -> the inner solves of the listed layers as one lockstep
+// group -> samples at rows 0, 1, n, n+1 and / or the owned rows added to the
+// global field.
+
+// f[b][x][r] of layer ld: vsrc ([N][B], rows ld.s + r, owned rows only) and the
+// forcing of in ([4][NX][Bw]: rows 0, 1, n, n+1; null: none)
+template <class T2>
+__global__ void k_nested_src(LayerDesc ld, const T2 *__restrict__ in, const double2 *__restrict__ vsrc,
+                             const double2 *__restrict__ ggam, int NX, int Bw, int B, int p, double2 *f) {
+    const int nz = ld.nz;
+    const long long rowsz = (long long)NX * Bw, n = (long long)Bw * NX * nz;
+    const int r0 = p - 1, r1 = p, rn = p + ld.n - 1, rn1 = p + ld.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e % nz);
+        const long long q = e / nz;
+        const int x = (int)(q % NX), b = (int)(q / NX);
+        double2 v = make_double2(0.0, 0.0);
+        if (vsrc && r >= ld.row_lo && r < ld.row_hi) v = vsrc[((long long)(ld.s + r) * NX + x) * B + b];
+        if (in && (r == r0 || r == r1 || r == rn || r == rn1)) {
+            const long long ix = (long long)x * Bw + b;
+            double2 s = make_double2(0.0, 0.0);
+            if (r == r0) s = s + to2(in[rowsz + ix], double2{});       // row 0  <- +gamma t(row 1)
+            if (r == r1) s = s - to2(in[ix], double2{});               // row 1  <- -gamma t(row 0)
+            if (r == rn) s = s - to2(in[3 * rowsz + ix], double2{});   // row n  <- -gamma t(row n+1)
+            if (r == rn1) s = s + to2(in[2 * rowsz + ix], double2{});  // row n+1 <- +gamma t(row n)
+            v = v + ggam[x] * s;
+        }
+        f[e] = v;
+    }
+}
+
+// samples of u[b][x][r] at rows 0, 1, n, n+1 into out ([4][NX][Bw]), and the
+// owned rows added to uacc ([N][B], Bw == B)
+template <class T2>
+__global__ void k_nested_out(LayerDesc ld, const double2 *__restrict__ u, T2 *out, double2 *uacc, int NX, int Bw,
+                             int B, int p) {
+    const int nz = ld.nz;
+    const long long rowsz = (long long)NX * Bw;
+    const long long stride = (long long)gridDim.x * blockDim.x, e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (out) {
+        for (long long e = e0; e < 4 * rowsz; e += stride) {
+            const int q = (int)(e / rowsz);
+            const long long rem = e % rowsz;
+            const int x = (int)(rem / Bw), b = (int)(rem % Bw);
+            const int r = q == 0 ? p - 1 : (q == 1 ? p : (q == 2 ? p + ld.n - 1 : p + ld.n));
+            out[e] = to2(u[((long long)b * NX + x) * nz + r], T2{});
+        }
+    }
+    if (uacc) {
+        const long long nr = (long long)(ld.row_hi - ld.row_lo) * NX * B;
+        for (long long e = e0; e < nr; e += stride) {
+            const int r = ld.row_lo + (int)(e / ((long long)NX * B));
+            const long long rem = e % ((long long)NX * B);
+            const int x = (int)(rem / B), b = (int)(rem % B);
+            double2 &g = uacc[((long long)(ld.s + r) * NX + x) * B + b];
+            g = g + u[((long long)b * NX + x) * nz + r];
+        }
+    }
+}
+
+template <class T2> __global__ void k_add(T2 *dst, const T2 *__restrict__ src, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = dst[i] + src[i];
+}
+
+// local solves of layers `lays` through their inner contexts (see above); in /
+// out: [L][4][NX][Bw] (null: none); vsrc: [N][B] or null; uacc: [N][B] or null.
+// precise: the polarized operator, Newton potentials and reconstruction (tight
+// inner tolerance), else the preconditioner (opts.inner_tol)
+template <class T2>
+static void nested_apply(hz_ctx *c, int B, const std::vector<int> &lays, const T2 *in, int Bw, const double2 *vsrc,
+                         T2 *out, double2 *uacc, bool precise) {
+    const int NX = c->NX, L = c->L;
+    if (c->n_bw < Bw) {  // FP64 source / solution volumes on the transposed layer grids
+        for (int l = 0; l < L; l++) {
+            if (c->nsrc.size() == (size_t)L) {
+                c->dfree(c->nsrc[l]);
+                c->dfree(c->nsol[l]);
+            }
+        }
+        c->nsrc.assign(L, nullptr);
+        c->nsol.assign(L, nullptr);
+        for (int l = 0; l < L; l++) {
+            const long long n = (long long)Bw * NX * c->layers[l].nz;
+            c->nsrc[l] = (double2 *)c->dalloc(sizeof(double2) * n);
+            c->nsol[l] = (double2 *)c->dalloc(sizeof(double2) * n);
+        }
+        c->n_bw = Bw;
+    }
+    const long long rowsz = (long long)NX * Bw;
+    for (int l : lays) {
+        k_nested_src<T2><<<1024, 256, 0, c->st>>>(c->layers[l], in ? in + (long long)l * 4 * rowsz : nullptr, vsrc,
+                                                  c->d_ggam, NX, Bw, B, c->p, c->nsrc[l]);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+    }
+    HZ_CU(cudaStreamSynchronize(c->st));  // the inner contexts run on their own streams
+    const double tol = precise ? (c->mixed() ? 1e-6 : 1e-10) : c->opts.inner_tol;
+    std::vector<hz_ctx *> ics;
+    std::vector<const double2 *> fs;
+    std::vector<double2 *> us;
+    for (int l : lays) {
+        hz_ctx *ic = Bw == B ? c->inner_ctx[l] : c->inner_wide[l];
+        ic->opts.tol = tol;
+        ic->nl = 0;
+        ics.push_back(ic);
+        fs.push_back(c->nsrc[l]);
+        us.push_back(c->nsol[l]);
+    }
+    std::vector<hz_stats> sts;
+    // an inner solve that stops at its iteration cap is still a usable inexact
+    // solve (the outer FGMRES admits it); any other failure is the call's
+    solve_group_impl<T2>(ics, fs, Bw, us, sts, false);
+    for (const hz_stats &x : sts) c->inner_its += x.iterations;
+    for (hz_ctx *ic : ics) c->nl += ic->nl;
+    for (int l : lays) {
+        k_nested_out<T2><<<1024, 256, 0, c->st>>>(c->layers[l], c->nsol[l], out ? out + (long long)l * 4 * rowsz : nullptr,
+                                                  uacc, NX, Bw, B, c->p);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+    }
+}
+
+template <class T2> static void nested_apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, double2 *y) {
+    const int B = W.B, L = c->L;
+    const long long n = (long long)L * 4 * c->NX * 2 * B;
+    k_stage_M<T2><<<grid1(n), 256, 0, c->st>>>(x, W.lin, L, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    std::vector<int> all(L);
+    for (int l = 0; l < L; l++) all[l] = l;
+    nested_apply<T2>(c, B, all, W.lin, 2 * B, nullptr, W.lout, nullptr, true);
+    const long long m = c->n_tr() * B;
+    k_combine_M<T2><<<grid1(m), 256, 0, c->st>>>(x, W.lout, y, L, c->NX, B);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+}
+
+// the preconditioner variants of precond_inplace with every layer application an
+// inner solve (B wide, inputs staged into lin, outputs added from lout)
+template <class T2> static void nested_precond(hz_ctx *c, Work<T2> &W, int kind) {
+    const int L = c->L, B = W.B;
+    const long long rowsz = (long long)c->NX * B;
+    cudaStream_t st = c->st;
+    auto vrow = [&](int k, int comp) { return W.pb + ((long long)k * 4 + comp) * rowsz; };
+    auto lrow = [&](T2 *base, int l, int q) { return base + ((long long)l * 4 + q) * rowsz; };
+    auto cp = [&](T2 *dst, const T2 *src) {
+        HZ_CU(cudaMemcpyAsync(dst, src, sizeof(T2) * rowsz, cudaMemcpyDeviceToDevice, st));
+    };
+    auto zero = [&](T2 *dst) { HZ_CU(cudaMemsetAsync(dst, 0, sizeof(T2) * rowsz, st)); };
+    auto add = [&](T2 *dst, const T2 *src) {
+        k_add<T2><<<grid1(rowsz), 256, 0, st>>>(dst, src, rowsz);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+    };
+    if (kind == 0 || kind == 1 || kind == 2) {  // d_k = v_k + G_down^k(d_{k-1})
+        for (int k = 1; k <= L - 2; k++) {
+            cp(lrow(W.lin, k, 0), vrow(k - 1, 0));
+            cp(lrow(W.lin, k, 1), vrow(k - 1, 1));
+            zero(lrow(W.lin, k, 2));
+            zero(lrow(W.lin, k, 3));
+            nested_apply<T2>(c, B, {k}, W.lin, B, nullptr, W.lout, nullptr, false);
+            add(vrow(k, 0), lrow(W.lout, k, 2));
+            add(vrow(k, 1), lrow(W.lout, k, 3));
+        }
+    }
+    if (kind == 0 || kind == 4) {  // u-part += rows 0,1 of layer k+1 from the d-parts of interfaces k, k+1
+        if (kind == 4)
+            for (int k = 0; k < L - 1; k++) HZ_CU(cudaMemsetAsync(vrow(k, 2), 0, sizeof(T2) * 2 * rowsz, st));
+        k_gs_fix<T2><<<grid1((long long)(L - 1) * rowsz), 256, 0, st>>>(W.pb, L - 1, c->NX, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        std::vector<int> lays;
+        for (int k = 0; k < L - 1; k++) {
+            const int l = k + 1;
+            cp(lrow(W.lin, l, 0), vrow(k, 0));
+            cp(lrow(W.lin, l, 1), vrow(k, 1));
+            if (l <= L - 2) {
+                cp(lrow(W.lin, l, 2), vrow(l, 0));
+                cp(lrow(W.lin, l, 3), vrow(l, 1));
+            } else {
+                zero(lrow(W.lin, l, 2));
+                zero(lrow(W.lin, l, 3));
+            }
+            lays.push_back(l);
+        }
+        nested_apply<T2>(c, B, lays, W.lin, B, nullptr, W.lout, nullptr, false);
+        for (int k = 0; k < L - 1; k++) {
+            add(vrow(k, 2), lrow(W.lout, k + 1, 0));
+            add(vrow(k, 3), lrow(W.lout, k + 1, 1));
+        }
+        if (kind == 4) {
+            k_refl_finish<T2><<<grid1((long long)(L - 1) * rowsz), 256, 0, st>>>(W.pb, L - 1, c->NX, B);
+            HZ_CU(cudaGetLastError());
+            c->nl++;
+        }
+    }
+    if (kind == 0 || kind == 1 || kind == 3) {  // u_k = v_k + G_up^{k+1}(u_{k+1})
+        for (int k = L - 3; k >= 0; k--) {
+            zero(lrow(W.lin, k + 1, 0));
+            zero(lrow(W.lin, k + 1, 1));
+            cp(lrow(W.lin, k + 1, 2), vrow(k + 1, 2));
+            cp(lrow(W.lin, k + 1, 3), vrow(k + 1, 3));
+            nested_apply<T2>(c, B, {k + 1}, W.lin, B, nullptr, W.lout, nullptr, false);
+            add(vrow(k, 2), lrow(W.lout, k + 1, 0));
+            add(vrow(k, 3), lrow(W.lout, k + 1, 1));
         }
     }
 }
@@ -1674,6 +1899,16 @@ template <class T2> static void local_enqueue(hz_ctx *c, Work<T2> &W, const doub
 template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const double2 *src) {
     cudaStream_t st = c->st;
     const int B = W.B, L = c->L, ncell = (int)c->cells.size();
+    W.cur_src = src;
+    if (c->nested()) {  // every layer's Newton potential by an inner solve, sampled at rows 0, 1, n, n+1
+        std::vector<int> all(L);
+        for (int l = 0; l < L; l++) all[l] = l;
+        nested_apply<T2>(c, B, all, (const T2 *)nullptr, B, src, W.lout, nullptr, true);
+        k_pol_rhs<T2><<<grid1(c->n_tr() * B), 256, 0, st>>>(W.lout, W.rhs64, L - 1, c->NX, B);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        return;
+    }
     local_enqueue<T2>(c, W, src);
     // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
@@ -1695,6 +1930,24 @@ template <class T2> static void recon_enqueue(hz_ctx *c, Work<T2> &W) {
     k_traces<T2><<<grid1((long long)(L - 1) * 2 * c->NX * B), 256, 0, st>>>(W.x64, W.pc, L - 1, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
+    if (c->nested()) {  // every layer's field: source + forcing of its interface traces, owned rows into u
+        const long long rowsz = (long long)c->NX * B;
+        std::vector<int> all(L);
+        for (int l = 0; l < L; l++) {
+            all[l] = l;
+            T2 *li = W.lin + (long long)l * 4 * rowsz;
+            for (int q = 0; q < 4; q++) {
+                const int k = q < 2 ? l - 1 : l;  // top pair: interface l-1; bottom pair: interface l
+                if (k >= 0 && k < L - 1)
+                    HZ_CU(cudaMemcpyAsync(li + q * rowsz, W.pc + ((long long)k * 2 + (q & 1)) * rowsz,
+                                          sizeof(T2) * rowsz, cudaMemcpyDeviceToDevice, st));
+                else
+                    HZ_CU(cudaMemsetAsync(li + q * rowsz, 0, sizeof(T2) * rowsz, st));
+            }
+        }
+        nested_apply<T2>(c, B, all, W.lin, B, W.cur_src, (T2 *)nullptr, W.u, true);
+        return;
+    }
     HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
     run(c, W.f_rec);
     chain_layers(c, W, false, 0, L);
@@ -1811,6 +2064,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
     const double t0 = now_ms();
     for (int i = 0; i < G; i++) {
         hz_ctx *c = cs[i];
+        c->inner_its = 0;
         Ws[i] = &work<T2>(c, B);
         Work<T2> &W = *Ws[i];
         const long long N = (long long)c->NX * c->NZ;
@@ -1922,6 +2176,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
             throw HzError(HZ_ETIMEOUT, "an inter-CTA exchange in the inner sweep timed out; results are invalid");
         }
         stats[i].t_total_ms = now_ms() - t0;
+        stats[i].inner_iterations = (int)c->inner_its;
         stats[i].t_local_ms = tm[i].local;
         stats[i].t_gmres_ms = tm[i].gmres;
         stats[i].t_recon_ms = tm[i].recon;
@@ -1940,7 +2195,7 @@ template int solve_group_impl<float2>(const std::vector<hz_ctx *> &, const std::
 // A lane of context c: shares c's decomposition, operators and split copies
 // (device pointers it does not own) and owns a non-blocking stream, its error
 // word and, on first use, its workspaces.
-static hz_ctx *make_lane(hz_ctx *c) {
+hz_ctx *make_lane(hz_ctx *c) {
     hz_ctx *s = new hz_ctx();
     s->n_x = c->n_x, s->n_z = c->n_z, s->p = c->p, s->L = c->L, s->C = c->C;
     s->omega = c->omega, s->h = c->h, s->pml_C = c->pml_C, s->NX = c->NX, s->NZ = c->NZ;
@@ -2053,9 +2308,13 @@ template <class T2> void comp_layer_green(hz_ctx *c, int l, const double2 *tr_de
     k_cast<double2, T2><<<grid1(n4 * B), 256, 0, c->st>>>(W.io, lin_l, n4 * B);
     HZ_CU(cudaGetLastError());
     c->nl++;
-    run(c, W.f_layer[l]);
-    chain_layers(c, W, false, l, 1);
-    run(c, W.es_layer[l]);
+    if (c->nested()) {
+        nested_apply<T2>(c, B, {l}, W.lin, B, nullptr, W.lout, nullptr, true);
+    } else {
+        run(c, W.f_layer[l]);
+        chain_layers(c, W, false, l, 1);
+        run(c, W.es_layer[l]);
+    }
     T2 *lout_l = W.lout + (long long)l * 4 * rowsz;
     k_cast<T2, double2><<<grid1(n4 * B), 256, 0, c->st>>>(lout_l, W.io, n4 * B);
     HZ_CU(cudaGetLastError());
@@ -2109,7 +2368,8 @@ template <class T2> void comp_reconstruct(hz_ctx *c, const double2 *f_dev, const
     const long long N = (long long)c->NX * c->NZ;
     transpose_in(c, f_dev, W.gsrc, N, B, true);
     HZ_CU(cudaMemsetAsync(W.u, 0, sizeof(double2) * N * B, c->st));
-    local_enqueue<T2>(c, W, W.gsrc);
+    W.cur_src = W.gsrc;
+    if (!c->nested()) local_enqueue<T2>(c, W, W.gsrc);
     k_put_traces<<<grid1(c->n_tr() * B), 256, 0, c->st>>>(tr_dev, W.x64, c->L - 1, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;

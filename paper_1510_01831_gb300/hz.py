@@ -23,6 +23,7 @@ HZ_OK, HZ_EINVAL, HZ_ENOMEM, HZ_ECUDA, HZ_ESTATE, HZ_ENOTCONV, HZ_ETIMEOUT, HZ_E
 HZ_FP64, HZ_MIXED = 0, 1
 HZ_PGS, HZ_PJAC, HZ_PNONE = 0, 1, 2
 HZ_GMRES, HZ_BICGSTAB = 0, 1
+HZ_INNER_LU, HZ_INNER_NESTED = 0, 1
 STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_ENOTCONV", "HZ_ETIMEOUT",
                 "HZ_ESINGULAR"]
 
@@ -46,7 +47,8 @@ class HzOpts(ctypes.Structure):
                 ("layer_rows", ctypes.POINTER(ctypes.c_int)), ("cell_cols", ctypes.POINTER(ctypes.c_int)),
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int),
-                ("rhs_lanes", ctypes.c_int), ("wait_ms", ctypes.c_double)]
+                ("rhs_lanes", ctypes.c_int), ("wait_ms", ctypes.c_double), ("inner", ctypes.c_int),
+                ("inner_tol", ctypes.c_double)]
 
 
 class HzStats(ctypes.Structure):
@@ -54,7 +56,8 @@ class HzStats(ctypes.Structure):
                 ("resid", ctypes.c_double), ("t_total_ms", ctypes.c_double), ("t_local_ms", ctypes.c_double),
                 ("t_gmres_ms", ctypes.c_double), ("t_recon_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
                 ("gpu_launches", ctypes.c_int), ("kt_launches", ctypes.c_int * 3), ("kt_ms", ctypes.c_double * 3),
-                ("kt_bytes", ctypes.c_double * 3), ("kt_flops", ctypes.c_double * 3)]
+                ("kt_bytes", ctypes.c_double * 3), ("kt_flops", ctypes.c_double * 3),
+                ("inner_iterations", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -147,7 +150,7 @@ class Context:
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
                  cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False,
-                 rhs_lanes=1, wait_ms=0.0):
+                 rhs_lanes=1, wait_ms=0.0, inner=HZ_INNER_LU, inner_tol=0.0):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -169,6 +172,8 @@ class Context:
         o.rhs_lanes = int(rhs_lanes)
         if wait_ms > 0:
             o.wait_ms = float(wait_ms)
+        o.inner = int(inner)
+        o.inner_tol = float(inner_tol)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")

@@ -130,3 +130,15 @@ def test_setup_rejects_bad_lane_count():
     h_ = ctypes.c_void_p()
     assert lib.hz_setup(ctypes.byref(h_), m.ctypes.data, 8, 8, 10.0, 0.1, 2, 2, 2, ctypes.byref(o)) == hz.HZ_EINVAL
     assert b"rhs_lanes" in lib.hz_last_error(None)
+
+
+@pytest.mark.parametrize("C,krylov,lanes,inner", [(1, 0, 1, 1), (2, 1, 1, 1), (2, 0, 2, 1), (2, 0, 1, 5)])
+def test_setup_rejects_unsupported_nested_inner_level(C, krylov, lanes, inner):
+    # the nested inner level needs cells to sweep over, a flexible outer solver and one lane
+    lib = hz.load()
+    m = np.ones((12, 12))
+    o = hz.hz_default_opts()
+    o.inner, o.krylov, o.rhs_lanes = inner, krylov, lanes
+    h_ = ctypes.c_void_p()
+    assert lib.hz_setup(ctypes.byref(h_), m.ctypes.data, 8, 8, 10.0, 0.1, 2, 2, C, ctypes.byref(o)) == hz.HZ_EINVAL
+    assert b"inner" in lib.hz_last_error(None)
