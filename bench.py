@@ -48,6 +48,8 @@ WORKLOADS = {
     "multifreq512": dict(n=512, n_pml=20, B=256, ppws=(6.0, 8.0, 10.0), seed=4, part_seed=40),
     # layered medium with faults, 2000 wide x 4000 deep + 30 PML, L=40 x C=20, 16 sources, 8 ppw at c=1.5
     "layered2000x4000": dict(n=2000, n_z=4000, n_pml=30, L=40, C=20, B=16, ppw=8.0, seed=3, layered=True),
+    # the decomposition of the paper's runtime figure (L = 9 layers x L_c = 3 cells), smooth random medium
+    "smooth384_9x3": dict(n=384, n_pml=20, L=9, C=3, B=16, ppw=10.0, seed=6),
     # the same generator at 2000 x 400 (4 layers): every launch has the shape of the 2000 x 4000 workload
     "layered2000x400": dict(n=2000, n_z=400, n_pml=30, L=4, C=20, B=16, ppw=8.0, seed=3, layered=True),
 }
@@ -253,6 +255,8 @@ def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_
                          device_ptrs=True, stream=stream.cuda_stream, time_kernels=True, refine_tol=1e-8,
                          tensor_cores=tc, krylov=1 if args.krylov == "bicgstab" else 0,
                          precond={"gs": hz.HZ_PGS, "jacobi": hz.HZ_PJAC}[args.precond],
+                         inner=hz.HZ_INNER_NESTED if args.inner == "nested" else hz.HZ_INNER_LU,
+                         inner_tol=args.inner_tol, compress=args.compress,
                          autotune=args.autotune, tol=args.tol, rhs_lanes=args.rhs_lanes, **kw)
         ctx.hz_factor()
         ctxs.append(ctx)
@@ -295,7 +299,8 @@ def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_
     kt_f = np.sum([s["kt_flops"] for s in flat], axis=0)
     last = stats[-1]
     solve = [{"iterations": m["iterations"], "refinements": m["refinements"], "resid": m["resid"],
-              "gmres_resid": m["gmres_resid"],
+              "gmres_resid": m["gmres_resid"], "inner_iterations": m["inner_iterations"],
+              "compress_rank": m["compress_rank"],
               "phase_ms": {k: round(m[k], 2) for k in ("t_local_ms", "t_gmres_ms", "t_recon_ms", "t_resid_ms",
                                                        "t_total_ms")}} for m in last]
     solve[0]["t_factor_s"] = round(t_factor, 2)
@@ -362,6 +367,7 @@ def run_ours(args, rank, world):
         "config": {"workload": main_["workload"], "B": main_["B"], "n_x": main_["n_x"], "n_z": main_["n_z"],
                    "L": main_["L"], "C": main_["C"], "precision": args.precision,
                    "frequencies": main_["frequencies"], "krylov": args.krylov, "precond": args.precond,
+                   "inner": args.inner, "compress": args.compress,
                    "autotune": args.autotune, "rhs_lanes": args.rhs_lanes,
                    "tensor_cores": "off" if args.no_tensor_cores else
                    ("cell solves + batched products" if args.tc_gemm else "cell solves"),
@@ -501,6 +507,11 @@ def main():
     ap.add_argument("--tc-gemm", action="store_true",
                     help="mixed precision: batched F/E/S/W products with long K on the tensor cores too")
     ap.add_argument("--krylov", default="gmres", choices=["gmres", "bicgstab"], help="outer Krylov method")
+    ap.add_argument("--inner", default="lu", choices=["lu", "nested"],
+                    help="local solver of the layers: exact inner block LU or inner nested polarized traces")
+    ap.add_argument("--inner-tol", type=float, default=0.0, help="nested inner level: preconditioner inner tolerance")
+    ap.add_argument("--compress", type=float, default=0.0,
+                    help="compressed-block LU tolerance for the inner factors (0: dense factors)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
     ap.add_argument("--tol", type=float, default=0.0, help="GMRES tolerance of the first pass (0: library default)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

@@ -126,6 +126,14 @@ typedef struct {
                            flexible GMRES, which admits it); needs C >= 2,
                            krylov HZ_GMRES and rhs_lanes 1, and hz_update_model is
                            not available with it */
+    double compress;    /* compressed-block LU (Section 4.2.2, with the compression
+                           of Section 4.3): > 0 stores every inner block-LU factor
+                           P_j = W_j(:,a) Z_j and V_j = W_j(:,b) K_{j+1} (the cell's
+                           Green's function between its two sides) as a rank-r
+                           product, r the largest numerical rank at relative
+                           Frobenius accuracy `compress` found by an adaptive
+                           randomized range finder; the inner sweeps then run on
+                           r-vectors.  0 (default): dense factors */
     double inner_tol;   /* HZ_INNER_NESTED: relative GMRES tolerance of the inner
                            solves inside the preconditioner (<= 0: 1e-6); the
                            polarized operator, the Newton potentials and the
@@ -152,6 +160,8 @@ typedef struct {
     double kt_flops[3];    /* algorithmic real flops of those launches */
     int inner_iterations;  /* HZ_INNER_NESTED: GMRES iterations of all inner solves of
                               the call (max over right-hand sides per inner solve) */
+    int compress_rank;     /* opts.compress > 0: the rank r of the compressed inner
+                              factors (0: dense) */
 } hz_stats;
 
 /* Fill opts with the defaults documented above (precision HZ_FP64). */

@@ -214,6 +214,10 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
         return fail(nullptr, HZ_EINVAL, "inner HZ_INNER_NESTED needs C >= 2, krylov HZ_GMRES and rhs_lanes 1");
     }
     if (!(c->opts.inner_tol > 0)) c->opts.inner_tol = 1e-6;
+    if (!(c->opts.compress >= 0) || c->opts.compress >= 1) {
+        delete c;
+        return fail(nullptr, HZ_EINVAL, "compress must be 0 (dense) or a tolerance in (0, 1)");
+    }
     c->n_x = n_x;
     c->n_z = n_z;
     c->p = n_pml;

@@ -110,6 +110,10 @@ struct LayerDesc {
     long long P_off;     // C-1 blocks (2nz)^2: P_j = W_j(:, 0:nz) Z_j (slot 0 unused)
     long long V_off;     // C-1 blocks (2nz)^2 (last unused)
     long long zoff;      // offset of the layer's per-row arrays (nz entries)
+    // compressed-block LU (rank r of the context): C-1 blocks of 2r x 2nz (STW, and
+    // their transposes' shape 2nz x 2r for UX), C-1 triples of r x r (MRN), C-1 vectors
+    // of 2r per right-hand side (the recursion's inputs AC and outputs TS)
+    long long lr_off, m_off, ac_off;
 };
 
 // Batched, segmented complex GEMM problem:  Y (+)= alpha (A X + A2 X2)

@@ -17,6 +17,10 @@ template <class T2> struct Ops {
     T2 *cz = nullptr;     // per cell: z couplings (nz x nx, last row unused)
     T2 *F = nullptr, *E = nullptr, *S = nullptr;
     T2 *W = nullptr, *P = nullptr, *V = nullptr;  // inner block LU: W_j, P_j = W_j(:,0:nz) Z_j, V_j
+    // compressed-block LU (opts.compress > 0): P_j ~ QP_j BP_j, V_j ~ QV_j BV_j (rank r);
+    // STW_j = [BP_{j+1} W_j; BV_{j-1} W_j] (2r x 2nz), UX_j = [QP_j QV_j] (2nz x 2r),
+    // MRN_j = [BP_j QP_{j-1}, BV_j QP_{j+1}, BV_j QV_{j+1}] (three r x r)
+    T2 *STW = nullptr, *UX = nullptr, *MRN = nullptr;
 };
 
 // Problem lists of batched GEMMs, kept on the device (built once per workspace).
@@ -42,6 +46,10 @@ template <class T2> struct Work {
     T2 *inner_f = nullptr; // inner right-hand side of the Newton potentials (saved)
     T2 *innerH = nullptr;  // h_j = W_j g_j, B wide
     T2 *innerH2 = nullptr; // h_j = W_j g_j, 2B wide
+                           // (compressed-block LU: innerH / innerH2 hold the right-hand sides g_j
+                           // and inner / inner2 receive h_j, then x_j)
+    T2 *ac = nullptr, *ts = nullptr;    // compressed-block LU recursion inputs / outputs [tot_ac][B]
+    T2 *ac2 = nullptr, *ts2 = nullptr;  // the same, 2B wide
     T2 *lin = nullptr;     // layer-application inputs  [L][4][T][2B]
     T2 *lout = nullptr;    // layer-application outputs [L][4][T][2B]
     T2 *pa = nullptr, *pb = nullptr, *pc = nullptr;  // polarized vectors [K][4][T][B]
@@ -71,6 +79,10 @@ template <class T2> struct Work {
     // h_j = W_j g_j problems ordered by layer; layers [l0, l1) are problems [hoff[l0], hoff[l1])
     ProbList<T2> hB, h2B;
     std::vector<int> hoff;
+    // compressed-block LU: x_j += UX_j ts_j, layers [l0, l1) are problems [uoff[l0], uoff[l1]);
+    // hB / h2B then also hold ac_j = STW_j g_j (layer by layer with the h_j problems)
+    ProbList<T2> uxB, ux2B;
+    std::vector<int> uoff;
     std::vector<double> hbytes, hflops;  // per layer (B wide)
 };
 
@@ -104,6 +116,8 @@ struct hz_ctx {
     int *d_layer_ids = nullptr;  // 0..L-1
     long long tot_vol = 0, tot_W = 0, tot_F = 0, tot_E = 0, tot_S = 0, tot_K = 0;
     long long tot_inner = 0, tot_Wi = 0, tot_P = 0, tot_V = 0;
+    int lr_r = 0;  // compressed-block LU rank (0: dense inner factors)
+    long long tot_lr = 0, tot_m = 0, tot_ac = 0;
     int max_nx = 0, max_nz = 0, max_no = 0;
     // global medium and PML profiles (FP64)
     std::vector<double> h_m;  // host copy of the medium (local model updates compare against it)

@@ -287,6 +287,391 @@ static void check_info(hz_ctx *c, int *d_info, cudaStream_t st, const char *what
 
 template <class T2> static T2 *alloc_n(hz_ctx *c, long long n) { return (T2 *)c->dalloc(sizeof(T2) * std::max(n, 1LL)); }
 
+// ------------------------------------------- compressed-block LU (offline) ---
+// Low-rank form of the inner block-LU factors P_j and V_j (Section 4.2.2, with
+// the compression of Section 4.3): each is the cell's Green's function between
+// its two sides, of low numerical rank.  For every block A (n2 x n2) an
+// adaptive randomized range finder (Halko, Martinsson & Tropp 2011, Alg. 4.2)
+// builds an orthonormal Q with ||A - Q Q^H A||_F <= eps ||A||_F: samples
+// y = A w of complex Gaussian vectors w are orthogonalised against the columns
+// found so far (classical Gram-Schmidt, two passes); a sample whose remainder
+// is above the threshold adds a column, and four consecutive ones below it end
+// the search.  Then B = Q^H A, and the bound is checked explicitly.
+
+// complex Gaussian entries (real and imaginary parts N(0, 1/2)) from a counter-based
+// generator (SplitMix64 of the entry index, Box-Muller)
+__device__ inline unsigned long long smix(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__global__ void k_gauss(double2 *w, long long n, unsigned long long seed) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = smix(seed + 2 * (unsigned long long)i), b = smix(seed + 2 * (unsigned long long)i + 1);
+        const double u1 = ((a >> 11) + 1.0) * (1.0 / 9007199254740993.0), u2 = (b >> 11) * (1.0 / 9007199254740992.0);
+        const double r = sqrt(-log(u1)), t = 6.283185307179586 * u2;
+        w[i] = make_double2(r * cos(t), r * sin(t));
+    }
+}
+
+// sum of |a|^2 over the n2 x n2 block at mats[b] (one block per CTA)
+__global__ void k_fro2(double2 *const *mats, const int *n2s, double *out) {
+    const double2 *A = mats[blockIdx.x];
+    const long long n = (long long)n2s[blockIdx.x] * n2s[blockIdx.x];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += A[i].x * A[i].x + A[i].y * A[i].y;
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// sum of |a - d|^2 of two n2 x n2 blocks (one pair per CTA)
+__global__ void k_diff2(double2 *const *mats, double2 *const *dmats, const int *n2s, double *out) {
+    const double2 *A = mats[blockIdx.x], *D = dmats[blockIdx.x];
+    const long long n = (long long)n2s[blockIdx.x] * n2s[blockIdx.x];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = A[i].x - D[i].x, y = A[i].y - D[i].y;
+        s += x * x + y * y;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// range finder of one block per CTA on its samples Y ([n2][kmax], y_c = A w_c in
+// column c): the accepted columns, orthonormal, are compacted to the left of Y and
+// the rest zeroed; kout = their number, or -1 if kmax samples did not capture the
+// range.  thr = threshold on a sample's remainder.
+__global__ void __launch_bounds__(256) k_range(double2 *const *Ys, const int *n2s, int kmax, int vlen,
+                                               const double *thr, int *kout) {
+    extern __shared__ double2 rsm[];
+    double2 *v = rsm;         // [vlen >= n2]
+    double2 *d = rsm + vlen;  // [kmax]
+    __shared__ double red[8];
+    __shared__ int s_acc;
+    double2 *Y = Ys[blockIdx.x];
+    const int n2 = n2s[blockIdx.x];
+    const double th = thr[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int k = 0, small = 0;
+    for (int c = 0; c < kmax && small < 4; c++) {
+        for (int r = tid; r < n2; r += 256) v[r] = Y[(long long)r * kmax + c];
+        __syncthreads();
+        for (int pass = 0; pass < 2; pass++) {
+            for (int i = warp; i < k; i += 8) {  // d_i = q_i^H v
+                double2 a = make_double2(0.0, 0.0);
+                for (int r = lane; r < n2; r += 32) {
+                    const double2 q = Y[(long long)r * kmax + i], x = v[r];
+                    a.x += q.x * x.x + q.y * x.y;
+                    a.y += q.x * x.y - q.y * x.x;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    a.x += __shfl_xor_sync(0xffffffffu, a.x, o);
+                    a.y += __shfl_xor_sync(0xffffffffu, a.y, o);
+                }
+                if (lane == 0) d[i] = a;
+            }
+            __syncthreads();
+            for (int r = tid; r < n2; r += 256) {  // v -= Q d
+                double2 a = v[r];
+                for (int i = 0; i < k; i++) {
+                    const double2 q = Y[(long long)r * kmax + i], di = d[i];
+                    a.x -= q.x * di.x - q.y * di.y;
+                    a.y -= q.x * di.y + q.y * di.x;
+                }
+                v[r] = a;
+            }
+            __syncthreads();
+        }
+        double s = 0.0;
+        for (int r = tid; r < n2; r += 256) s += v[r].x * v[r].x + v[r].y * v[r].y;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; w++) t += red[w];
+            s_acc = sqrt(t) > th ? 1 : 0;
+            red[0] = sqrt(t);
+        }
+        __syncthreads();
+        if (s_acc) {
+            const double inv = 1.0 / red[0];
+            for (int r = tid; r < n2; r += 256) Y[(long long)r * kmax + k] = make_double2(v[r].x * inv, v[r].y * inv);
+            k++;
+            small = 0;
+        } else {
+            small++;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n2 * (kmax - k); e += 256) {
+        const int r = e / (kmax - k), cc = k + e % (kmax - k);
+        Y[(long long)r * kmax + cc] = make_double2(0.0, 0.0);
+    }
+    if (tid == 0) kout[blockIdx.x] = small >= 4 ? k : -1;
+}
+
+// QH = Q^H (kmax x n2) of Q ([n2][kmax])
+__global__ void k_conj_t(double2 *const *Qs, double2 *const *QHs, const int *n2s, int kmax) {
+    const double2 *Q = Qs[blockIdx.y];
+    double2 *QH = QHs[blockIdx.y];
+    const int n2 = n2s[blockIdx.y];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * kmax; e += gridDim.x * blockDim.x) {
+        const int i = e / n2, r = e % n2;
+        const double2 q = Q[(long long)r * kmax + i];
+        QH[e] = make_double2(q.x, -q.y);
+    }
+}
+
+// UX_j = [QP_j QV_j] (n2 x 2r): columns 0..r-1 from QP_j, r..2r-1 from QV_j (null: zero)
+__global__ void k_build_ux(double2 *const *qp, double2 *const *qv, double2 *const *ux, const int *n2s, int kmax, int r) {
+    const double2 *P = qp[blockIdx.y], *V = qv[blockIdx.y];
+    double2 *U = ux[blockIdx.y];
+    const int n2 = n2s[blockIdx.y];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n2 * 2 * r; e += gridDim.x * blockDim.x) {
+        const int row = e / (2 * r), cc = e % (2 * r);
+        const double2 *src = cc < r ? P : V;
+        const int col = cc < r ? cc : cc - r;
+        U[e] = src ? src[(long long)row * kmax + col] : make_double2(0.0, 0.0);
+    }
+}
+
+// run a host-built list of FP64 products (64 x 32 tiles, no split)
+static void run_list64(hz_ctx *c, const std::vector<GemmProb<double2>> &v) {
+    if (v.empty()) return;
+    int mt = 0;
+    for (const auto &g : v) mt = std::max(mt, gemm_tiles(g.M, g.N, 0));
+    GemmProb<double2> *d = (GemmProb<double2> *)c->dalloc(sizeof(GemmProb<double2>) * v.size());
+    HZ_CU(cudaMemcpyAsync(d, v.data(), sizeof(GemmProb<double2>) * v.size(), cudaMemcpyHostToDevice, c->st));
+    launch_gemm<double2>(d, (int)v.size(), mt, 1, nullptr, nullptr, c->st, &c->nl);
+    HZ_CU(cudaStreamSynchronize(c->st));
+    c->dfree(d);
+}
+static GemmProb<double2> prob64(const double2 *A, long long lda, int M, int K, int N, const double2 *X, long long ldx,
+                                double2 *Y, long long ldy) {
+    GemmProb<double2> g{};
+    g.A = A;
+    g.lda = lda;
+    g.M = M;
+    g.K = K;
+    g.N = N;
+    g.xseg = g.yseg = 1 << 30;
+    g.X[0] = X;
+    g.ldx = ldx;
+    g.Y[0] = Y;
+    g.ldy = ldy;
+    g.beta = 0;
+    g.alpha = 1.f;
+    return g;
+}
+
+// Compress the P / V factors of layers `lsub` (FP64, full-size arrays Pm / Vi / Wi)
+// and write the compressed operators STW / UX / MRN (FP64, full-size arrays).  The
+// first call fixes the rank r of the context (largest block rank, rounded up to a
+// multiple of 8) and the layers' offsets; later calls (local updates) must fit in it.
+static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<LayerDesc> &lsub, const double2 *Wi,
+                           const double2 *Pm, const double2 *Vi, double2 *&STW, double2 *&UX, double2 *&MRN,
+                           bool first) {
+    const double eps = c->opts.compress;
+    const int C = c->C, J = C - 1;
+    if (J < 2) return;
+    int max_n2 = 0;
+    for (const LayerDesc &ld : lsub) max_n2 = std::max(max_n2, 2 * ld.nz);
+    const int kmax = std::min(max_n2, 128);
+    // the blocks: P_j (j = 1..J-1) and V_j (j = 0..J-2) of every layer
+    struct Blk {
+        int q, j, isV;
+    };
+    std::vector<Blk> blks;
+    for (int q = 0; q < (int)lsub.size(); q++)
+        for (int j = 0; j < J; j++) {
+            if (j >= 1) blks.push_back({q, j, 0});
+            if (j <= J - 2) blks.push_back({q, j, 1});
+        }
+    const int nb = (int)blks.size();
+    std::vector<double2 *> A(nb), Y(nb), QH(nb), Bm(nb), D(nb);
+    std::vector<int> n2s(nb);
+    double2 *Om = alloc_n<double2>(c, (long long)max_n2 * kmax);
+    k_gauss<<<256, 256, 0, c->st>>>(Om, (long long)max_n2 * kmax, 0x5eedull);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    long long per = 0;  // scratch per block: Y, QH, Bm, D
+    per = (long long)max_n2 * kmax * 3 + (long long)max_n2 * max_n2;
+    double2 *scr = alloc_n<double2>(c, per * nb);
+    HZ_CU(cudaMemsetAsync(scr, 0, sizeof(double2) * per * nb, c->st));
+    for (int b = 0; b < nb; b++) {
+        const LayerDesc &ld = lsub[blks[b].q];
+        const int n2 = 2 * ld.nz;
+        n2s[b] = n2;
+        A[b] = const_cast<double2 *>((blks[b].isV ? Vi + ld.V_off : Pm + ld.P_off) + (long long)blks[b].j * n2 * n2);
+        Y[b] = scr + per * b;
+        QH[b] = Y[b] + (long long)max_n2 * kmax;
+        Bm[b] = QH[b] + (long long)max_n2 * kmax;
+        D[b] = Bm[b] + (long long)max_n2 * kmax;
+    }
+    double2 **dA = (double2 **)c->dalloc(sizeof(double2 *) * nb * 3);
+    double2 **dY = dA + nb, **dQH = dA + 2 * nb;
+    int *dn = (int *)c->dalloc(sizeof(int) * nb * 2);
+    int *dk = dn + nb;
+    double *dv = (double *)c->dalloc(sizeof(double) * nb * 2);
+    HZ_CU(cudaMemcpyAsync(dA, A.data(), sizeof(double2 *) * nb, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(dY, Y.data(), sizeof(double2 *) * nb, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(dQH, QH.data(), sizeof(double2 *) * nb, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(dn, n2s.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, c->st));
+    k_fro2<<<nb, 256, 0, c->st>>>(dA, dn, dv);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    std::vector<double> nrm2(nb), thr(nb);
+    HZ_CU(cudaMemcpyAsync(nrm2.data(), dv, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+    // a sample's remainder estimates ||(I - Q Q^H) A||_F; stop well below the target
+    for (int b = 0; b < nb; b++) thr[b] = 0.25 * eps * std::sqrt(nrm2[b]);
+    HZ_CU(cudaMemcpyAsync(dv + nb, thr.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, c->st));
+    {  // samples Y = A W
+        std::vector<GemmProb<double2>> v;
+        for (int b = 0; b < nb; b++) v.push_back(prob64(A[b], n2s[b], n2s[b], n2s[b], kmax, Om, kmax, Y[b], kmax));
+        run_list64(c, v);
+    }
+    const size_t rsm = sizeof(double2) * (max_n2 + kmax);
+    if (rsm > 48 * 1024) HZ_CU(cudaFuncSetAttribute(k_range, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
+    k_range<<<nb, 256, rsm, c->st>>>(dY, dn, kmax, max_n2, dv + nb, dk);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    std::vector<int> ks(nb);
+    HZ_CU(cudaMemcpyAsync(ks.data(), dk, sizeof(int) * nb, cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+    int kbig = 0;
+    for (int b = 0; b < nb; b++) {
+        if (ks[b] < 0)
+            throw HzError(HZ_EINVAL, "compressed-block LU: a factor's numerical rank exceeds " + std::to_string(kmax) +
+                                         " at this tolerance; use a larger tolerance or dense factors");
+        kbig = std::max(kbig, ks[b]);
+    }
+    k_conj_t<<<dim3(64, nb), 256, 0, c->st>>>(dY, dQH, dn, kmax);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    {  // B = Q^H A, then D = Q B for the explicit check
+        std::vector<GemmProb<double2>> v;
+        for (int b = 0; b < nb; b++) v.push_back(prob64(QH[b], n2s[b], kmax, n2s[b], n2s[b], A[b], n2s[b], Bm[b], n2s[b]));
+        run_list64(c, v);
+        v.clear();
+        for (int b = 0; b < nb; b++) v.push_back(prob64(Y[b], kmax, n2s[b], kmax, n2s[b], Bm[b], n2s[b], D[b], n2s[b]));
+        run_list64(c, v);
+    }
+    double2 **dD = dQH;  // reuse the pointer table
+    HZ_CU(cudaMemcpyAsync(dD, D.data(), sizeof(double2 *) * nb, cudaMemcpyHostToDevice, c->st));
+    k_diff2<<<nb, 256, 0, c->st>>>(dA, dD, dn, dv);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    std::vector<double> err2(nb);
+    HZ_CU(cudaMemcpyAsync(err2.data(), dv, sizeof(double) * nb, cudaMemcpyDeviceToHost, c->st));
+    HZ_CU(cudaStreamSynchronize(c->st));
+    for (int b = 0; b < nb; b++)
+        if (!(err2[b] <= eps * eps * nrm2[b]))
+            throw HzError(HZ_EINVAL, "compressed-block LU: the low-rank form of a factor missed its tolerance");
+    // the rank and layout (fixed by the first factorization)
+    if (first) {
+        c->lr_r = std::min(kmax, std::max(8, (kbig + 7) / 8 * 8));
+        const int r = c->lr_r;
+        long long lo = 0, mo = 0, ao = 0;
+        for (LayerDesc &ld : c->layers) {
+            ld.lr_off = lo;
+            lo += (long long)J * 2 * r * 2 * ld.nz;
+            ld.m_off = mo;
+            mo += (long long)J * 3 * r * r;
+            ld.ac_off = ao;
+            ao += (long long)J * 2 * r;
+        }
+        c->tot_lr = lo;
+        c->tot_m = mo;
+        c->tot_ac = ao;
+        HZ_CU(cudaMemcpyAsync(c->d_layers, c->layers.data(), sizeof(LayerDesc) * c->layers.size(),
+                              cudaMemcpyHostToDevice, c->st));
+        for (int q = 0; q < (int)lsub.size(); q++) lsub[q] = c->layers[lays[q]];
+    } else if (kbig > c->lr_r) {
+        throw HzError(HZ_EINVAL, "compressed-block LU: the updated medium needs a larger rank than the first "
+                                 "factorization; factor afresh");
+    }
+    const int r = c->lr_r;
+    if (r > kmax) throw HzError(HZ_EINVAL, "compressed-block LU: rank layout larger than the samples");
+    // FP64 operator arrays (full size; null: allocated here)
+    if (!STW) STW = alloc_n<double2>(c, c->tot_lr);
+    if (!UX) UX = alloc_n<double2>(c, c->tot_lr);
+    if (!MRN) MRN = alloc_n<double2>(c, c->tot_m);
+    // STW_j = [BP_{j+1} W_j; BV_{j-1} W_j], UX_j = [QP_j QV_j], and the r x r matrices of the
+    // recursion in the order of its steps: forward step j (1..J-1) at (j-1) 2r^2 holds
+    // [M_{j+1}; R_{j-1}] (M_j = BP_j QP_{j-1}, R_j = BV_j QP_{j+1}; M_J = 0), backward step j
+    // (J-2..1) at (J-1) 2r^2 + (J-2-j) r^2 holds N_{j-1} (N_j = BV_j QV_{j+1})
+    auto blk = [&](int q, int j, int isV) {
+        for (int b = 0; b < nb; b++)
+            if (blks[b].q == q && blks[b].j == j && blks[b].isV == isV) return b;
+        return -1;
+    };
+    for (const LayerDesc &ld : lsub) {
+        HZ_CU(cudaMemsetAsync(STW + ld.lr_off, 0, sizeof(double2) * (long long)J * 2 * r * 2 * ld.nz, c->st));
+        HZ_CU(cudaMemsetAsync(MRN + ld.m_off, 0, sizeof(double2) * (long long)J * 3 * r * r, c->st));
+    }
+    std::vector<GemmProb<double2>> v;
+    std::vector<double2 *> qp, qv, ux;
+    std::vector<int> uxn;
+    for (int q = 0; q < (int)lsub.size(); q++) {
+        const LayerDesc &ld = lsub[q];
+        const int n2 = 2 * ld.nz;
+        for (int j = 0; j < J; j++) {
+            const double2 *Wj = Wi + ld.W_off + (long long)j * n2 * n2;
+            double2 *stw = STW + ld.lr_off + (long long)j * 2 * r * n2;
+            double2 *mrn = MRN + ld.m_off + (long long)j * 3 * r * r;
+            const int bp1 = j + 1 <= J - 1 ? blk(q, j + 1, 0) : -1, bvm1 = j >= 1 ? blk(q, j - 1, 1) : -1;
+            if (bp1 >= 0) v.push_back(prob64(Bm[bp1], n2, r, n2, n2, Wj, n2, stw, n2));
+            if (bvm1 >= 0) v.push_back(prob64(Bm[bvm1], n2, r, n2, n2, Wj, n2, stw + (long long)r * n2, n2));
+            const int bp = j >= 1 ? blk(q, j, 0) : -1, bv = j <= J - 2 ? blk(q, j, 1) : -1;
+            const int bpm = j >= 2 ? blk(q, j - 1, 0) : -1;
+            const int bpp = j + 1 <= J - 1 ? blk(q, j + 1, 0) : -1, bvp = j + 1 <= J - 2 ? blk(q, j + 1, 1) : -1;
+            const double2 *m0 = MRN + ld.m_off;
+            const long long rr = (long long)r * r;
+            if (bp >= 0 && bpm >= 0)  // M_j -> forward step j-1
+                v.push_back(prob64(Bm[bp], n2, r, n2, r, Y[bpm], kmax, const_cast<double2 *>(m0) + (j - 2) * 2 * rr, r));
+            if (bv >= 0 && bpp >= 0)  // R_j -> forward step j+1
+                v.push_back(prob64(Bm[bv], n2, r, n2, r, Y[bpp], kmax, const_cast<double2 *>(m0) + j * 2 * rr + rr, r));
+            if (bv >= 0 && bvp >= 0)  // N_j -> backward step j+1
+                v.push_back(prob64(Bm[bv], n2, r, n2, r, Y[bvp], kmax,
+                                   const_cast<double2 *>(m0) + (long long)(J - 1) * 2 * rr + (J - 3 - j) * rr, r));
+            (void)mrn;
+            qp.push_back(bp >= 0 ? Y[bp] : nullptr);
+            qv.push_back(bv >= 0 ? Y[bv] : nullptr);
+            ux.push_back(UX + ld.lr_off + (long long)j * n2 * 2 * r);
+            uxn.push_back(n2);
+        }
+    }
+    run_list64(c, v);
+    const int nu = (int)ux.size();
+    double2 **du = (double2 **)c->dalloc(sizeof(double2 *) * nu * 3);
+    int *dun = (int *)c->dalloc(sizeof(int) * nu);
+    HZ_CU(cudaMemcpyAsync(du, qp.data(), sizeof(double2 *) * nu, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(du + nu, qv.data(), sizeof(double2 *) * nu, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(du + 2 * nu, ux.data(), sizeof(double2 *) * nu, cudaMemcpyHostToDevice, c->st));
+    HZ_CU(cudaMemcpyAsync(dun, uxn.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, c->st));
+    k_build_ux<<<dim3(32, nu), 256, 0, c->st>>>(du, du + nu, du + 2 * nu, dun, kmax, r);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(c->st));
+    for (void *q : {(void *)Om, (void *)scr, (void *)dA, (void *)dn, (void *)dv, (void *)du, (void *)dun}) c->dfree(q);
+}
+
+
 // ---------------------------------------------------------- factor ---
 // Factorization of the layers in `lays` (all layers on the first call, from
 // hz_factor; the layers whose cells read a changed medium on a local update,
@@ -493,6 +878,22 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
     c->dfree(K);
     c->dfree(Zi);
 
+    // 3b. compressed-block LU: low-rank P_j, V_j and the operators of the r-vector recursion
+    double2 *STW64 = nullptr, *UX64 = nullptr, *MRN64 = nullptr;
+    if (c->opts.compress > 0 && C > 2) {
+        if (!mixed) {  // kept by the context in FP64 (allocated by the first call)
+            STW64 = c->o64.STW;
+            UX64 = c->o64.UX;
+            MRN64 = c->o64.MRN;
+        }
+        compress_inner(c, lays, lsub, Wi, Pm, Vi, STW64, UX64, MRN64, first);
+        if (!mixed) {
+            c->o64.STW = STW64;
+            c->o64.UX = UX64;
+            c->o64.MRN = MRN64;
+        }
+    }
+
     // 4. mixed precision: the working-precision copies of these layers' operators
     if (mixed) {
         auto &o = c->o32;
@@ -529,6 +930,24 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
                 to_f32(Vi + ld.V_off, o.V + ld.V_off, nb, st, nl);
             }
         }
+        if (c->lr_r > 0 && STW64) {  // FP32 copies of the compressed-block LU operators
+            const int J = C - 1, r = c->lr_r;
+            if (first) {
+                o.STW = alloc_n<float2>(c, c->tot_lr);
+                o.UX = alloc_n<float2>(c, c->tot_lr);
+                o.MRN = alloc_n<float2>(c, c->tot_m);
+                to_f32(STW64, o.STW, c->tot_lr, st, nl);
+                to_f32(UX64, o.UX, c->tot_lr, st, nl);
+                to_f32(MRN64, o.MRN, c->tot_m, st, nl);
+            } else {
+                for (const LayerDesc &ld : lsub) {
+                    const long long nlr = (long long)J * 2 * r * 2 * ld.nz, nm = (long long)J * 3 * r * r;
+                    to_f32(STW64 + ld.lr_off, o.STW + ld.lr_off, nlr, st, nl);
+                    to_f32(UX64 + ld.lr_off, o.UX + ld.lr_off, nlr, st, nl);
+                    to_f32(MRN64 + ld.m_off, o.MRN + ld.m_off, nm, st, nl);
+                }
+            }
+        }
         if (c->opts.tensor_cores && c->max_nx <= 128) {
             // split TF32 copy of the cell blocks for the tensor-core cell solve
             if (first) {
@@ -546,7 +965,8 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
             }
         }
         HZ_CU(cudaStreamSynchronize(st));
-        for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi})
+        for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi,
+                        (void *)STW64, (void *)UX64, (void *)MRN64})
             c->dfree(q);
     }
     c->dfree(d_info);

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "hz_ctx.cuh"
+#include "hz_tc.cuh"
 
 namespace hz {
 
@@ -577,6 +578,199 @@ __global__ void k_zaxpy(double2 *out, const double2 *__restrict__ a, const doubl
         out[e] = a[e] + coef[e % B] * x[e];
 }
 
+// ---------------------------------------- compressed-block LU recursion ---
+// The inner block-LU sweeps of a layer with its factors in low-rank form
+// (P_j ~ QP_j BP_j, V_j ~ QV_j BV_j, rank r).  With ac_j = [a_{j+1}; c_{j-1}] =
+// [BP_{j+1} h_j; BV_{j-1} h_j] computed beforehand (h_j = W_j g_j):
+//   forward step j = 1..J-1:  [t_{j+1}; u_j] = ac_j + [M_{j+1}; R_{j-1}] t_j,
+//                             t_1 = a_1 (M_{j+1} = BP_{j+1} QP_j, R_{j-1} = BV_{j-1} QP_j),
+//   backward step j = J-2..1: s_{j-1} = u_j + N_{j-1} s_j, s_{J-2} = u_{J-1}
+//                             (N_{j-1} = BV_{j-1} QV_j),
+// and x_j = h_j + QP_j t_j + QV_j s_j follows as one batched product.  Each step
+// is one product of a prefetched matrix with the previous step's vector; its
+// other input (ac_j or u_j, known in advance) is loaded a step ahead into
+// registers.  One CTA per (layer, NB right-hand sides); ts_j = [t_j; s_j]
+// (t_0 = 0, s_{J-1} = 0; u_j is kept in the s slot j-1 until s_{j-1} replaces it).
+// The matrices stream in step order through a shared-memory ring by bulk copies
+// issued ST steps ahead (mbarrier-completed, bounded waits).
+template <class T2, int NB>
+__global__ void __launch_bounds__(256) k_lr_chain(const LayerDesc *__restrict__ layers, const int *__restrict__ ids,
+                                                  const T2 *__restrict__ MRN, const T2 *__restrict__ AC, T2 *TS, int r,
+                                                  int Bw, int *err) {
+    constexpr int ST = sizeof(T2) == 8 ? 3 : 2;  // ring stages
+    constexpr int PT = 2 * 64 * NB / 256;        // outputs per thread for r <= 64
+    extern __shared__ __align__(16) unsigned char lsm[];
+    __shared__ __align__(8) unsigned long long full[ST];
+    __shared__ int s_dead;
+    const long long r2 = (long long)r * r;
+    T2 *ring = reinterpret_cast<T2 *>(lsm);  // ST stages of 2 r^2
+    T2 *vb = ring + ST * 2 * r2;              // the recursion's vector (r x NB)
+    const LayerDesc ld = layers[ids[blockIdx.y]];
+    const int J = ld.C - 1, n0 = blockIdx.x * NB, tid = threadIdx.x;
+    const long long vs = 2LL * r * Bw;  // one interface's [2r][Bw] vector
+    const T2 *ac = AC + ld.ac_off * Bw;
+    T2 *ts = TS + ld.ac_off * Bw;
+    const T2 *mrn = MRN + ld.m_off;
+    const int nf = J >= 2 ? J - 1 : 0, nbk = J >= 3 ? J - 2 : 0, ncopy = nf + nbk;
+    int q_issued = 0, q_waited = 0;  // thread 0: copies issued / consumed
+    auto issue = [&](int q) {  // thread 0: the matrices of step q (forward 2 r^2, backward r^2)
+        if (q >= ncopy) return;
+        q_issued = q + 1;
+        const long long off = q < nf ? (long long)q * 2 * r2 : (long long)nf * 2 * r2 + (long long)(q - nf) * r2;
+        const unsigned bytes = (unsigned)((q < nf ? 2 : 1) * r2 * sizeof(T2));
+        const unsigned mb = su32(&full[q % ST]);
+        mb_expect(mb, bytes);
+        bulk_g2s(su32(ring + (q % ST) * 2 * r2), mrn + off, bytes, mb);
+    };
+    if (tid == 0) {
+        for (int i = 0; i < ST; i++) mb_init(su32(&full[i]), 1);
+        s_dead = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int q = 0; q < ST; q++) issue(q);
+    }
+    bool dead = false;
+    auto wait = [&](int q) {  // the whole CTA learns a timeout together
+        if (tid == 0 && !s_dead) {
+            if (!mb_wait(su32(&full[q % ST]), (unsigned)((q / ST) & 1), dead, err))
+                s_dead = 1;
+            else
+                q_waited = q + 1;
+        }
+        __syncthreads();
+        return s_dead == 0;
+    };
+    // thread-owned outputs e = tid + 256 p of an m x NB step output (m = 2r forward, r backward)
+    auto load_base = [&](const T2 *base, int m, T2 (&pre)[PT]) {
+#pragma unroll
+        for (int p = 0; p < PT; p++) {
+            const int e = tid + 256 * p;
+            const int i = e / NB, n = e % NB;
+            pre[p] = (e < m * NB && n0 + n < Bw) ? base[(long long)i * Bw + n0 + n] : czero<T2>();
+        }
+    };
+    // out[p] = base[p] + A v over this thread's outputs (A: m x r in shared memory)
+    auto mul = [&](const T2 *A, int m, const T2 (&base)[PT], T2 (&out)[PT]) {
+#pragma unroll
+        for (int p = 0; p < PT; p++) {
+            const int e = tid + 256 * p;
+            T2 p0 = base[p], p1 = czero<T2>(), p2 = czero<T2>(), p3 = czero<T2>();
+            if (e < m * NB) {
+                const int i = e / NB, n = e % NB;
+                const T2 *a = A + (long long)i * r;
+                int k = 0;
+                for (; k + 3 < r; k += 4) {
+                    cmac(p0, a[k], vb[k * NB + n]);
+                    cmac(p1, a[k + 1], vb[(k + 1) * NB + n]);
+                    cmac(p2, a[k + 2], vb[(k + 2) * NB + n]);
+                    cmac(p3, a[k + 3], vb[(k + 3) * NB + n]);
+                }
+                for (; k < r; k++) cmac(p0, a[k], vb[k * NB + n]);
+            }
+            out[p] = (p0 + p1) + (p2 + p3);
+        }
+    };
+    auto store = [&](int m, const T2 (&out)[PT], T2 *dst_lo, T2 *dst_hi) {  // rows < r -> dst_lo, >= r -> dst_hi
+#pragma unroll
+        for (int p = 0; p < PT; p++) {
+            const int e = tid + 256 * p;
+            if (e >= m * NB) continue;
+            const int i = e / NB, n = e % NB;
+            if (n0 + n >= Bw) continue;
+            T2 *d = i < r ? dst_lo : dst_hi;
+            if (d) d[(long long)(i < r ? i : i - r) * Bw + n0 + n] = out[p];
+        }
+    };
+    T2 cur[PT], nxt[PT], out[PT];
+    // t_0 = 0 and s_{J-1} = 0
+    for (int e = tid; e < r * NB; e += 256) {
+        const int i = e / NB, n = e % NB;
+        if (n0 + n < Bw) {
+            ts[(long long)i * Bw + n0 + n] = czero<T2>();
+            ts[(J - 1) * vs + (long long)(r + i) * Bw + n0 + n] = czero<T2>();
+        }
+    }
+    if (J >= 2) {
+        // t_1 = a_1 into the vector
+        for (int e = tid; e < r * NB; e += 256) {
+            const int i = e / NB, n = e % NB;
+            const T2 v = n0 + n < Bw ? ac[(long long)i * Bw + n0 + n] : czero<T2>();
+            vb[e] = v;
+            if (n0 + n < Bw) ts[vs + (long long)i * Bw + n0 + n] = v;
+        }
+        load_base(ac + vs, 2 * r, cur);  // ac_1
+        __syncthreads();
+        int q = 0;
+        for (int j = 1; j <= J - 1; j++, q++) {
+            if (j + 1 <= J - 1) load_base(ac + (j + 1) * vs, 2 * r, nxt);  // a step ahead
+            if (!wait(q)) break;
+            mul(ring + (q % ST) * 2 * r2, 2 * r, cur, out);
+            __syncthreads();  // every thread has read vb and the stage
+            if (tid == 0 && !s_dead) issue(q + ST);
+            // t_{j+1} (rows < r; not for j = J-1) -> ts_{j+1} and the vector; u_j (rows >= r) -> s slot j-1
+            store(2 * r, out, j + 1 <= J - 1 ? ts + (j + 1) * vs : nullptr, ts + (j - 1) * vs + (long long)r * Bw);
+#pragma unroll
+            for (int p = 0; p < PT; p++) {
+                const int e = tid + 256 * p;
+                if (e < r * NB) vb[e] = out[p];
+                cur[p] = nxt[p];
+            }
+            __syncthreads();
+        }
+        if (s_dead == 0 && J >= 3) {
+            __threadfence_block();
+            __syncthreads();
+            // backward: s_{J-2} = u_{J-1} (already in its slot), s_{j-1} = u_j + N_{j-1} s_j
+            for (int e = tid; e < r * NB; e += 256) {
+                const int i = e / NB, n = e % NB;
+                vb[e] = n0 + n < Bw ? ts[(J - 2) * vs + (long long)(r + i) * Bw + n0 + n] : czero<T2>();
+            }
+            load_base(ts + (J - 3) * vs + (long long)r * Bw, r, cur);  // u_{J-2}
+            __syncthreads();
+            for (int j = J - 2; j >= 1; j--, q++) {
+                if (j - 1 >= 1) load_base(ts + (j - 2) * vs + (long long)r * Bw, r, nxt);  // u_{j-1}
+                if (!wait(q)) break;
+                mul(ring + (q % ST) * 2 * r2, r, cur, out);
+                __syncthreads();
+                if (tid == 0 && !s_dead) issue(q + ST);
+                store(r, out, ts + (j - 1) * vs + (long long)r * Bw, nullptr);
+#pragma unroll
+                for (int p = 0; p < PT; p++) {
+                    const int e = tid + 256 * p;
+                    if (e < r * NB) vb[e] = out[p];
+                    cur[p] = nxt[p];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    // after a timeout: let the copies this CTA issued land before it leaves (bounded)
+    if (tid == 0 && s_dead) {
+        for (int q = q_waited; q < q_issued; q++) mb_wait(su32(&full[q % ST]), (unsigned)((q / ST) & 1), dead, err);
+    }
+    __syncthreads();
+}
+
+template <class T2>
+static void launch_lr_chain(hz_ctx *c, const int *ids, int nl, const T2 *MRN, const T2 *AC, T2 *TS, int Bw) {
+    const int r = c->lr_r;
+    if (r > 64) throw HzError(HZ_EINVAL, "compressed-block LU: rank above 64");
+    constexpr int ST = sizeof(T2) == 8 ? 3 : 2;
+    // 4 right-hand sides per CTA for narrow batches (more CTAs, shorter steps), else 16
+    const int NB = Bw <= 32 ? 4 : 16;
+    const size_t sm = sizeof(T2) * ((size_t)ST * 2 * r * r + (size_t)r * NB);
+    if (sm > 220 * 1024) throw HzError(HZ_EINVAL, "compressed-block LU: rank too large for the recursion kernel");
+    static size_t attr4 = 0, attr16 = 0;
+    size_t &attr = NB == 4 ? attr4 : attr16;
+    auto kern = NB == 4 ? k_lr_chain<T2, 4> : k_lr_chain<T2, 16>;
+    if (sm > 48 * 1024 && sm > attr) {
+        HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = sm;
+    }
+    kern<<<dim3((Bw + NB - 1) / NB, nl), 256, sm, c->st>>>(c->d_layers, ids, MRN, AC, TS, r, Bw, c->d_err);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+}
+
 // ------------------------------------------------- problem-list build ---
 template <class T2> struct ListBuilder {
     hz_ctx *c;
@@ -838,10 +1032,13 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         return base + ((long long)k * 4 + comp0) * rowsz;
     };
     // apply M: F from the staged inputs (2B wide), E/S of both sets
+    // compressed-block LU: the right-hand sides g_j go to innerH / innerH2, h_j and x_j to inner / inner2
+    const bool lr = c->lr_r > 0;
+    T2 *gB = lr ? W.innerH : W.inner, *g2B = lr ? W.innerH2 : W.inner2;
     for (int l = 0; l < L; l++) {
         const T2 *in[4];
         for (int q = 0; q < 4; q++) in[q] = W.lin + ((long long)l * 4 + q) * rowsz2;
-        lb.add_F(l, 3, in, 2 * B, 2 * B, W.inner2, 2 * B, 0);
+        lb.add_F(l, 3, in, 2 * B, 2 * B, g2B, 2 * B, 0);
     }
     W.f_full = lb.finish();
     for (int l = 0; l < L; l++) {
@@ -869,7 +1066,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
     W.es_down.assign(L, ProbList<T2>());
     for (int k = 1; k <= L - 2; k++) {
         const T2 *in[4] = {vec_rows(W.pb, k - 1, 0), vec_rows(W.pb, k - 1, 1), nullptr, nullptr};
-        lb.add_F(k, 1, in, B, B, W.inner, B, 0);
+        lb.add_F(k, 1, in, B, B, gB, B, 0);
         W.f_down[k] = lb.finish();
         T2 *out[4] = {nullptr, nullptr, vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1)};
         lb.add_ES(k, 1, in, B, 2, out, B, W.inner, B, B, 1);
@@ -880,7 +1077,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
     W.es_up.assign(L, ProbList<T2>());
     for (int k = L - 3; k >= 0; k--) {
         const T2 *in[4] = {nullptr, nullptr, vec_rows(W.pb, k + 1, 2), vec_rows(W.pb, k + 1, 3)};
-        lb.add_F(k + 1, 2, in, B, B, W.inner, B, 0);
+        lb.add_F(k + 1, 2, in, B, B, gB, B, 0);
         W.f_up[k] = lb.finish();
         T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
         lb.add_ES(k + 1, 2, in, B, 1, out, B, W.inner, B, B, 1);
@@ -894,7 +1091,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             in[2] = vec_rows(W.pb, k + 1, 0);
             in[3] = vec_rows(W.pb, k + 1, 1);
         }
-        lb.add_F(k + 1, mask, in, B, B, W.inner, B, 0);
+        lb.add_F(k + 1, mask, in, B, B, gB, B, 0);
     }
     W.f_refl = lb.finish();
     for (int k = 0; k < K; k++) {
@@ -920,7 +1117,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             in[2] = W.pc + ((long long)l * 2 + 0) * rowsz;
             in[3] = W.pc + ((long long)l * 2 + 1) * rowsz;
         }
-        if (mask) lb.add_F(l, mask, in, B, B, W.inner, B, 1);
+        if (mask) lb.add_F(l, mask, in, B, B, gB, B, 1);
     }
     W.f_rec = lb.finish();
     // Newton samples: lout (B-wide view [L][4][NX][B]) += E x_f
@@ -937,8 +1134,12 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
     W.hflops.assign(L, 0.0);
     for (int wide = 0; wide < 2; wide++) {
         const int Bw = wide ? 2 * B : B;
-        T2 *gin = wide ? W.inner2 : W.inner;
-        T2 *hout = wide ? W.innerH2 : W.innerH;
+        // dense: h_j = W_j g_j from inner into innerH; compressed: from innerH into inner,
+        // with ac_j = STW_j g_j beside it
+        T2 *gin = lr ? (wide ? W.innerH2 : W.innerH) : (wide ? W.inner2 : W.inner);
+        T2 *hout = lr ? (wide ? W.inner2 : W.inner) : (wide ? W.innerH2 : W.innerH);
+        T2 *acv = wide ? W.ac2 : W.ac;
+        const int r = c->lr_r;
         int cnt = 0;
         for (int l = 0; l < L; l++) {
             const LayerDesc &ld = c->layers[l];
@@ -960,6 +1161,13 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
                 g.alpha = 1.f;
                 lb.push(g);
                 cnt++;
+                if (lr) {
+                    g.A = o.STW + ld.lr_off + (long long)j * 2 * r * n2;
+                    g.M = 2 * r;
+                    g.Y[0] = acv + (ld.ac_off + (long long)j * 2 * r) * Bw;
+                    lb.push(g);
+                    cnt++;
+                }
             }
             if (!wide) {
                 W.hbytes[l] = lb.bytes - b0;
@@ -972,6 +1180,43 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         else
             W.hB = lb.finish();
     }
+    // compressed-block LU: x_j += UX_j ts_j, ordered by layer
+    if (lr) {
+        W.uoff.assign(L + 1, 0);
+        const int r = c->lr_r;
+        for (int wide = 0; wide < 2; wide++) {
+            const int Bw = wide ? 2 * B : B;
+            T2 *xv = wide ? W.inner2 : W.inner;
+            T2 *tsv = wide ? W.ts2 : W.ts;
+            int cnt = 0;
+            for (int l = 0; l < L; l++) {
+                const LayerDesc &ld = c->layers[l];
+                const int n2 = 2 * ld.nz;
+                if (!wide) W.uoff[l] = cnt;
+                for (int j = 0; j < c->C - 1; j++) {
+                    GemmProb<T2> g{};
+                    g.A = o.UX + ld.lr_off + (long long)j * n2 * 2 * r;
+                    g.lda = 2 * r;
+                    g.M = n2;
+                    g.K = 2 * r;
+                    g.N = Bw;
+                    g.xseg = g.yseg = 1 << 30;
+                    g.ldx = g.ldy = Bw;
+                    g.X[0] = tsv + (ld.ac_off + (long long)j * 2 * r) * Bw;
+                    g.Y[0] = xv + (ld.inner_off + (long long)(j + 1) * n2) * Bw;
+                    g.beta = 1;
+                    g.alpha = 1.f;
+                    lb.push(g);
+                    cnt++;
+                }
+            }
+            if (!wide) W.uoff[L] = cnt;
+            if (wide)
+                W.ux2B = lb.finish();
+            else
+                W.uxB = lb.finish();
+        }
+    }
     // single-layer applications (component entry point), inputs/outputs in lin/lout (B wide)
     W.f_layer.assign(L, ProbList<T2>());
     W.es_layer.assign(L, ProbList<T2>());
@@ -982,7 +1227,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             in[q] = W.lin + ((long long)l * 4 + q) * rowsz;
             out[q] = W.lout + ((long long)l * 4 + q) * rowsz;
         }
-        lb.add_F(l, 3, in, B, B, W.inner, B, 0);
+        lb.add_F(l, 3, in, B, B, gB, B, 0);
         W.f_layer[l] = lb.finish();
         lb.add_ES(l, 3, in, B, 3, out, B, W.inner, B, B, 0);
         W.es_layer[l] = lb.finish();
@@ -994,7 +1239,7 @@ template <> std::unique_ptr<Work<double2>> &work_slot<double2>(hz_ctx *c) { retu
 template <> std::unique_ptr<Work<float2>> &work_slot<float2>(hz_ctx *c) { return c->w32; }
 
 template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
-    void *ptrs[] = {W.vol, W.vol2, W.inner, W.inner2, W.inner_f, W.innerH, W.innerH2, W.lin, W.lout, W.pa, W.pb, W.pc, W.Z, W.V, W.w64,
+    void *ptrs[] = {W.vol, W.vol2, W.inner, W.inner2, W.inner_f, W.innerH, W.innerH2, W.ac, W.ts, W.ac2, W.ts2, W.lin, W.lout, W.pa, W.pb, W.pc, W.Z, W.V, W.w64,
                     W.rhs64, W.x64, W.dots, W.hbuf, W.gsrc, W.u, W.io, W.rnorm};
     for (void *q : ptrs) c->dfree(q);
     auto fl = [&](ProbList<T2> &pl) { c->dfree(pl.d); };
@@ -1006,6 +1251,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.e_newton);
     fl(W.hB);
     fl(W.h2B);
+    fl(W.uxB);
+    fl(W.ux2B);
     for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer})
         for (auto &pl : *vv) fl(pl);
     if (W.hhost) cudaFreeHost(W.hhost);
@@ -1034,6 +1281,12 @@ template <class T2> Work<T2> &work(hz_ctx *c, int B) {
     W.inner_f = (T2 *)al(c->tot_inner * B, sizeof(T2));
     W.innerH = (T2 *)al(c->tot_inner * B, sizeof(T2));
     W.innerH2 = (T2 *)al(c->tot_inner * 2 * B, sizeof(T2));
+    if (c->lr_r > 0) {
+        W.ac = (T2 *)al(c->tot_ac * B, sizeof(T2));
+        W.ts = (T2 *)al(c->tot_ac * B, sizeof(T2));
+        W.ac2 = (T2 *)al(c->tot_ac * 2 * B, sizeof(T2));
+        W.ts2 = (T2 *)al(c->tot_ac * 2 * B, sizeof(T2));
+    }
     HZ_CU(cudaMemset(W.inner, 0, sizeof(T2) * c->tot_inner * B));
     HZ_CU(cudaMemset(W.inner2, 0, sizeof(T2) * c->tot_inner * 2 * B));
     HZ_CU(cudaMemset(W.inner_f, 0, sizeof(T2) * c->tot_inner * B));
@@ -1081,6 +1334,31 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     run(c, sub);
     const int N = wide ? 2 * W.B : W.B;
     double by = 0, fl = 0;
+    if (c->lr_r > 0) {  // compressed-block LU: the r-vector recursion, then x_j += UX_j ts_j
+        const int r = c->lr_r;
+        if (c->opts.time_kernels)
+            for (int l = l0; l < l0 + nl; l++) {
+                const double J = c->C - 1, es = sizeof(T2);
+                by += es * (3 * J * r * r + 4 * J * r * N);
+                fl += 8.0 * 3 * J * r * r * N;
+            }
+        c->kt_begin(1, by, fl);
+        launch_lr_chain<T2>(c, c->d_layer_ids + l0, nl, o.MRN, wide ? W.ac2 : W.ac, wide ? W.ts2 : W.ts, N);
+        c->kt_end();
+        const ProbList<T2> &ua = wide ? W.ux2B : W.uxB;
+        ProbList<T2> us = ua;
+        us.d = ua.d + W.uoff[l0];
+        us.n = W.uoff[l0 + nl] - W.uoff[l0];
+        us.tc_tiles = (long long)us.n * ua.tc_max_tiles;
+        us.bytes = us.flops = 0;
+        for (int l = l0; l < l0 + nl; l++) {
+            const double n2 = 2.0 * c->layers[l].nz, J = c->C - 1, es = sizeof(T2);
+            us.bytes += es * J * (n2 * 2 * r + 2 * r * N + 2 * n2 * N);
+            us.flops += 8.0 * J * n2 * 2 * r * N;
+        }
+        run(c, us);
+        return;
+    }
     if (c->opts.time_kernels) inner_chain_cost<T2>(c, l0, nl, N, by, fl);
     c->kt_begin(1, by, fl);
     launch_inner_sweep<T2>(c->d_layers, c->d_layer_ids + l0, nl, o.P, o.V, wide ? W.innerH2 : W.innerH,
@@ -1910,8 +2188,10 @@ template <class T2> static void newton_enqueue(hz_ctx *c, Work<T2> &W, const dou
         return;
     }
     local_enqueue<T2>(c, W, src);
-    // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy
-    HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
+    // keep the inner right-hand side (inner_f) for the reconstruction; solve a copy (the
+    // compressed-block LU reads its right-hand sides from innerH)
+    HZ_CU(cudaMemcpyAsync(c->lr_r > 0 ? W.innerH : W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B,
+                          cudaMemcpyDeviceToDevice, st));
     chain_layers(c, W, false, 0, L);
     k_samples<T2><<<dim3(64, ncell), 256, 0, st>>>(c->d_cells, W.vol, W.lout, c->NX, B, c->p);
     HZ_CU(cudaGetLastError());
@@ -1948,7 +2228,8 @@ template <class T2> static void recon_enqueue(hz_ctx *c, Work<T2> &W) {
         nested_apply<T2>(c, B, all, W.lin, B, W.cur_src, (T2 *)nullptr, W.u, true);
         return;
     }
-    HZ_CU(cudaMemcpyAsync(W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B, cudaMemcpyDeviceToDevice, st));
+    HZ_CU(cudaMemcpyAsync(c->lr_r > 0 ? W.innerH : W.inner, W.inner_f, sizeof(T2) * c->tot_inner * B,
+                          cudaMemcpyDeviceToDevice, st));
     run(c, W.f_rec);
     chain_layers(c, W, false, 0, L);
     HZ_CU(cudaMemsetAsync(W.vol2, 0, sizeof(T2) * c->tot_vol * B, st));
@@ -2177,6 +2458,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
         }
         stats[i].t_total_ms = now_ms() - t0;
         stats[i].inner_iterations = (int)c->inner_its;
+        stats[i].compress_rank = c->lr_r;
         stats[i].t_local_ms = tm[i].local;
         stats[i].t_gmres_ms = tm[i].gmres;
         stats[i].t_recon_ms = tm[i].recon;
@@ -2207,6 +2489,7 @@ hz_ctx *make_lane(hz_ctx *c) {
     s->tot_vol = c->tot_vol, s->tot_W = c->tot_W, s->tot_F = c->tot_F, s->tot_E = c->tot_E, s->tot_S = c->tot_S;
     s->tot_K = c->tot_K, s->tot_inner = c->tot_inner, s->tot_Wi = c->tot_Wi, s->tot_P = c->tot_P;
     s->tot_V = c->tot_V, s->max_nx = c->max_nx, s->max_nz = c->max_nz, s->max_no = c->max_no;
+    s->lr_r = c->lr_r, s->tot_lr = c->tot_lr, s->tot_m = c->tot_m, s->tot_ac = c->tot_ac;
     s->d_m = c->d_m, s->d_ax = c->d_ax, s->d_axh = c->d_axh, s->d_az = c->d_az, s->d_azh = c->d_azh;
     s->d_gdiag = c->d_gdiag, s->d_gcx = c->d_gcx, s->d_gcz = c->d_gcz, s->d_gD = c->d_gD;
     s->d_ginvD = c->d_ginvD, s->d_ggam = c->d_ggam, s->d_lbeta = c->d_lbeta, s->tot_z = c->tot_z;

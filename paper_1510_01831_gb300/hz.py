@@ -48,7 +48,7 @@ class HzOpts(ctypes.Structure):
                 ("device_ptrs", ctypes.c_int), ("stream", ctypes.c_void_p), ("time_kernels", ctypes.c_int),
                 ("krylov", ctypes.c_int), ("autotune", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("rhs_lanes", ctypes.c_int), ("wait_ms", ctypes.c_double), ("inner", ctypes.c_int),
-                ("inner_tol", ctypes.c_double)]
+                ("compress", ctypes.c_double), ("inner_tol", ctypes.c_double)]
 
 
 class HzStats(ctypes.Structure):
@@ -57,7 +57,7 @@ class HzStats(ctypes.Structure):
                 ("t_gmres_ms", ctypes.c_double), ("t_recon_ms", ctypes.c_double), ("t_resid_ms", ctypes.c_double),
                 ("gpu_launches", ctypes.c_int), ("kt_launches", ctypes.c_int * 3), ("kt_ms", ctypes.c_double * 3),
                 ("kt_bytes", ctypes.c_double * 3), ("kt_flops", ctypes.c_double * 3),
-                ("inner_iterations", ctypes.c_int)]
+                ("inner_iterations", ctypes.c_int), ("compress_rank", ctypes.c_int)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -150,7 +150,7 @@ class Context:
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
                  cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False,
-                 rhs_lanes=1, wait_ms=0.0, inner=HZ_INNER_LU, inner_tol=0.0):
+                 rhs_lanes=1, wait_ms=0.0, inner=HZ_INNER_LU, inner_tol=0.0, compress=0.0):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -174,6 +174,7 @@ class Context:
             o.wait_ms = float(wait_ms)
         o.inner = int(inner)
         o.inner_tol = float(inner_tol)
+        o.compress = float(compress)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")
