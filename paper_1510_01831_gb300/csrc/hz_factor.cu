@@ -449,6 +449,19 @@ __global__ void k_build_ux(double2 *const *qp, double2 *const *qv, double2 *cons
     }
 }
 
+// blocks of the recursion matrices stored transposed (column i of a block contiguous),
+// so that the threads of a warp, which take consecutive rows, read consecutive words:
+// block b is rows[b] x cols[b] at off[b] of src, written cols[b] x rows[b] at off[b] of dst
+__global__ void k_block_t(const double2 *__restrict__ src, double2 *dst, const long long *off, const int *rows,
+                          const int *cols) {
+    const long long o = off[blockIdx.y];
+    const int R = rows[blockIdx.y], Cn = cols[blockIdx.y];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < R * Cn; e += gridDim.x * blockDim.x) {
+        const int i = e / Cn, k = e % Cn;
+        dst[o + (long long)k * R + i] = src[o + e];
+    }
+}
+
 // run a host-built list of FP64 products (64 x 32 tiles, no split)
 static void run_list64(hz_ctx *c, const std::vector<GemmProb<double2>> &v) {
     if (v.empty()) return;
@@ -614,7 +627,8 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
     // STW_j = [BP_{j+1} W_j; BV_{j-1} W_j], UX_j = [QP_j QV_j], and the r x r matrices of the
     // recursion in the order of its steps: forward step j (1..J-1) at (j-1) 2r^2 holds
     // [M_{j+1}; R_{j-1}] (M_j = BP_j QP_{j-1}, R_j = BV_j QP_{j+1}; M_J = 0), backward step j
-    // (J-2..1) at (J-1) 2r^2 + (J-2-j) r^2 holds N_{j-1} (N_j = BV_j QV_{j+1})
+    // (J-2..1) at (J-1) 2r^2 + (J-2-j) r^2 holds N_{j-1} (N_j = BV_j QV_{j+1}); each step's
+    // block is stored transposed
     auto blk = [&](int q, int j, int isV) {
         for (int b = 0; b < nb; b++)
             if (blks[b].q == q && blks[b].j == j && blks[b].isV == isV) return b;
@@ -657,6 +671,42 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
         }
     }
     run_list64(c, v);
+    {  // each step's matrix transposed in place (through a copy of the layers' ranges)
+        std::vector<long long> offs;
+        std::vector<int> rws, cls;
+        long long tot = 0;
+        for (const LayerDesc &ld : lsub) {
+            const long long rr = (long long)r * r, base = ld.m_off;
+            for (int j = 1; j <= J - 1; j++) {  // forward steps: [M; R], 2r x r
+                offs.push_back(base + (long long)(j - 1) * 2 * rr);
+                rws.push_back(2 * r);
+                cls.push_back(r);
+            }
+            for (int b = 0; b < J - 2; b++) {  // backward steps: N, r x r
+                offs.push_back(base + (long long)(J - 1) * 2 * rr + b * rr);
+                rws.push_back(r);
+                cls.push_back(r);
+            }
+            tot = std::max(tot, base + (long long)J * 3 * rr);
+        }
+        const int nbk = (int)offs.size();
+        if (nbk > 0) {
+            double2 *cp = alloc_n<double2>(c, tot);
+            HZ_CU(cudaMemcpyAsync(cp, MRN, sizeof(double2) * tot, cudaMemcpyDeviceToDevice, c->st));
+            long long *doff = (long long *)c->dalloc(sizeof(long long) * nbk);
+            int *drc = (int *)c->dalloc(sizeof(int) * 2 * nbk);
+            HZ_CU(cudaMemcpyAsync(doff, offs.data(), sizeof(long long) * nbk, cudaMemcpyHostToDevice, c->st));
+            HZ_CU(cudaMemcpyAsync(drc, rws.data(), sizeof(int) * nbk, cudaMemcpyHostToDevice, c->st));
+            HZ_CU(cudaMemcpyAsync(drc + nbk, cls.data(), sizeof(int) * nbk, cudaMemcpyHostToDevice, c->st));
+            k_block_t<<<dim3(16, nbk), 256, 0, c->st>>>(cp, MRN, doff, drc, drc + nbk);
+            HZ_CU(cudaGetLastError());
+            c->nl++;
+            HZ_CU(cudaStreamSynchronize(c->st));
+            c->dfree(cp);
+            c->dfree(doff);
+            c->dfree(drc);
+        }
+    }
     const int nu = (int)ux.size();
     double2 **du = (double2 **)c->dalloc(sizeof(double2 *) * nu * 3);
     int *dun = (int *)c->dalloc(sizeof(int) * nu);

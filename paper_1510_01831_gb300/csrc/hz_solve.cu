@@ -586,28 +586,30 @@ __global__ void k_zaxpy(double2 *out, const double2 *__restrict__ a, const doubl
 //                             t_1 = a_1 (M_{j+1} = BP_{j+1} QP_j, R_{j-1} = BV_{j-1} QP_j),
 //   backward step j = J-2..1: s_{j-1} = u_j + N_{j-1} s_j, s_{J-2} = u_{J-1}
 //                             (N_{j-1} = BV_{j-1} QV_j),
-// and x_j = h_j + QP_j t_j + QV_j s_j follows as one batched product.  Each step
-// is one product of a prefetched matrix with the previous step's vector; its
-// other input (ac_j or u_j, known in advance) is loaded a step ahead into
-// registers.  One CTA per (layer, NB right-hand sides); ts_j = [t_j; s_j]
-// (t_0 = 0, s_{J-1} = 0; u_j is kept in the s slot j-1 until s_{j-1} replaces it).
-// The matrices stream in step order through a shared-memory ring by bulk copies
-// issued ST steps ahead (mbarrier-completed, bounded waits).
+// and x_j = h_j + QP_j t_j + QV_j s_j follows as one batched product.  One CTA
+// per (layer, NB right-hand sides) holds all ac_j in shared memory (u_j replaces
+// c_{j-1} once step j has used it), so each step is one product of a matrix
+// from the ring with the previous step's vector, and two barriers.  The
+// matrices stream in step order through the ring by bulk copies issued ST steps
+// ahead (mbarrier-completed, bounded waits); ts_j = [t_j; s_j] (t_0 = 0,
+// s_{J-1} = 0) go to global memory for the x_j product.
 template <class T2, int NB>
 __global__ void __launch_bounds__(256) k_lr_chain(const LayerDesc *__restrict__ layers, const int *__restrict__ ids,
                                                   const T2 *__restrict__ MRN, const T2 *__restrict__ AC, T2 *TS, int r,
                                                   int Bw, int *err) {
-    constexpr int ST = sizeof(T2) == 8 ? 3 : 2;  // ring stages
-    constexpr int PT = 2 * 64 * NB / 256;        // outputs per thread for r <= 64
+    constexpr int ST = 3;                  // ring stages
+    constexpr int PT = 2 * 64 * NB / 256;  // outputs per thread for r <= 64
     extern __shared__ __align__(16) unsigned char lsm[];
     __shared__ __align__(8) unsigned long long full[ST];
     __shared__ int s_dead;
     const long long r2 = (long long)r * r;
-    T2 *ring = reinterpret_cast<T2 *>(lsm);  // ST stages of 2 r^2
-    T2 *vb = ring + ST * 2 * r2;              // the recursion's vector (r x NB)
     const LayerDesc ld = layers[ids[blockIdx.y]];
     const int J = ld.C - 1, n0 = blockIdx.x * NB, tid = threadIdx.x;
-    const long long vs = 2LL * r * Bw;  // one interface's [2r][Bw] vector
+    T2 *ring = reinterpret_cast<T2 *>(lsm);  // ST stages of 2 r^2
+    T2 *vb0 = ring + ST * 2 * r2;             // the recursion's vector, double-buffered (r x NB)
+    T2 *vb1 = vb0 + r * NB;
+    T2 *bs = vb1 + r * NB;                    // ac_j, then u_j in rows r..2r-1 ([J][2r][NB])
+    const long long vs = 2LL * r * Bw;        // one interface's [2r][Bw] vector in global memory
     const T2 *ac = AC + ld.ac_off * Bw;
     T2 *ts = TS + ld.ac_off * Bw;
     const T2 *mrn = MRN + ld.m_off;
@@ -628,6 +630,19 @@ __global__ void __launch_bounds__(256) k_lr_chain(const LayerDesc *__restrict__ 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int q = 0; q < ST; q++) issue(q);
     }
+    // all of the layer's ac_j, this CTA's columns; t_0 = 0 and s_{J-1} = 0
+    for (int e = tid; e < J * 2 * r * NB; e += 256) {
+        const int n = e % NB, row = e / NB;  // row = j * 2r + i
+        bs[e] = n0 + n < Bw ? ac[(long long)row * Bw + n0 + n] : czero<T2>();
+    }
+    for (int e = tid; e < r * NB; e += 256) {
+        const int i = e / NB, n = e % NB;
+        if (n0 + n < Bw) {
+            ts[(long long)i * Bw + n0 + n] = czero<T2>();
+            ts[(J - 1) * vs + (long long)(r + i) * Bw + n0 + n] = czero<T2>();
+        }
+    }
+    __syncthreads();
     bool dead = false;
     auto wait = [&](int q) {  // the whole CTA learns a timeout together
         if (tid == 0 && !s_dead) {
@@ -639,136 +654,112 @@ __global__ void __launch_bounds__(256) k_lr_chain(const LayerDesc *__restrict__ 
         __syncthreads();
         return s_dead == 0;
     };
-    // thread-owned outputs e = tid + 256 p of an m x NB step output (m = 2r forward, r backward)
-    auto load_base = [&](const T2 *base, int m, T2 (&pre)[PT]) {
-#pragma unroll
-        for (int p = 0; p < PT; p++) {
-            const int e = tid + 256 * p;
-            const int i = e / NB, n = e % NB;
-            pre[p] = (e < m * NB && n0 + n < Bw) ? base[(long long)i * Bw + n0 + n] : czero<T2>();
-        }
-    };
-    // out[p] = base[p] + A v over this thread's outputs (A: m x r in shared memory)
-    auto mul = [&](const T2 *A, int m, const T2 (&base)[PT], T2 (&out)[PT]) {
-#pragma unroll
-        for (int p = 0; p < PT; p++) {
-            const int e = tid + 256 * p;
-            T2 p0 = base[p], p1 = czero<T2>(), p2 = czero<T2>(), p3 = czero<T2>();
-            if (e < m * NB) {
-                const int i = e / NB, n = e % NB;
-                const T2 *a = A + (long long)i * r;
-                int k = 0;
-                for (; k + 3 < r; k += 4) {
-                    cmac(p0, a[k], vb[k * NB + n]);
-                    cmac(p1, a[k + 1], vb[(k + 1) * NB + n]);
-                    cmac(p2, a[k + 2], vb[(k + 2) * NB + n]);
-                    cmac(p3, a[k + 3], vb[(k + 3) * NB + n]);
-                }
-                for (; k < r; k++) cmac(p0, a[k], vb[k * NB + n]);
-            }
-            out[p] = (p0 + p1) + (p2 + p3);
-        }
-    };
-    auto store = [&](int m, const T2 (&out)[PT], T2 *dst_lo, T2 *dst_hi) {  // rows < r -> dst_lo, >= r -> dst_hi
+    // this thread's outputs e = tid + 256 p of one step: out = base + A v, A (m x r, stored
+    // transposed) in the ring, v the current vector; rows < r go to vn (the next vector) and to lo (global),
+    // rows >= r back into base (u_j) -- each output is read and written by one thread
+    auto step = [&](const T2 *A, int m, T2 *base, const T2 *v, T2 *vn, T2 *lo) {
 #pragma unroll
         for (int p = 0; p < PT; p++) {
             const int e = tid + 256 * p;
             if (e >= m * NB) continue;
             const int i = e / NB, n = e % NB;
-            if (n0 + n >= Bw) continue;
-            T2 *d = i < r ? dst_lo : dst_hi;
-            if (d) d[(long long)(i < r ? i : i - r) * Bw + n0 + n] = out[p];
+            T2 p0 = base[e], p1 = czero<T2>(), p2 = czero<T2>(), p3 = czero<T2>();
+            const T2 *a = A + i;  // the block is stored transposed: element (i, k) at k m + i
+            int k = 0;
+            for (; k + 3 < r; k += 4) {  // four independent partial sums
+                cmac(p0, a[(long long)k * m], v[k * NB + n]);
+                cmac(p1, a[(long long)(k + 1) * m], v[(k + 1) * NB + n]);
+                cmac(p2, a[(long long)(k + 2) * m], v[(k + 2) * NB + n]);
+                cmac(p3, a[(long long)(k + 3) * m], v[(k + 3) * NB + n]);
+            }
+            for (; k < r; k++) cmac(p0, a[(long long)k * m], v[k * NB + n]);
+            const T2 o = (p0 + p1) + (p2 + p3);
+            if (i < r) {
+                vn[e] = o;
+                if (lo && n0 + n < Bw) lo[(long long)i * Bw + n0 + n] = o;
+            } else {
+                base[e] = o;
+            }
         }
+        __syncthreads();  // vn complete, v and the ring stage no longer read
     };
-    T2 cur[PT], nxt[PT], out[PT];
-    // t_0 = 0 and s_{J-1} = 0
-    for (int e = tid; e < r * NB; e += 256) {
-        const int i = e / NB, n = e % NB;
-        if (n0 + n < Bw) {
-            ts[(long long)i * Bw + n0 + n] = czero<T2>();
-            ts[(J - 1) * vs + (long long)(r + i) * Bw + n0 + n] = czero<T2>();
-        }
-    }
+    T2 *vc = vb0, *vx = vb1;
+    int q = 0;
     if (J >= 2) {
-        // t_1 = a_1 into the vector
+        // t_1 = a_1
         for (int e = tid; e < r * NB; e += 256) {
             const int i = e / NB, n = e % NB;
-            const T2 v = n0 + n < Bw ? ac[(long long)i * Bw + n0 + n] : czero<T2>();
-            vb[e] = v;
-            if (n0 + n < Bw) ts[vs + (long long)i * Bw + n0 + n] = v;
+            vc[e] = bs[e];
+            if (n0 + n < Bw) ts[vs + (long long)i * Bw + n0 + n] = bs[e];
         }
-        load_base(ac + vs, 2 * r, cur);  // ac_1
         __syncthreads();
-        int q = 0;
-        for (int j = 1; j <= J - 1; j++, q++) {
-            if (j + 1 <= J - 1) load_base(ac + (j + 1) * vs, 2 * r, nxt);  // a step ahead
+        for (int j = 1; j <= J - 1; j++, q++) {  // forward
             if (!wait(q)) break;
-            mul(ring + (q % ST) * 2 * r2, 2 * r, cur, out);
-            __syncthreads();  // every thread has read vb and the stage
+            step(ring + (q % ST) * 2 * r2, 2 * r, bs + (long long)j * 2 * r * NB, vc, vx,
+                 j + 1 <= J - 1 ? ts + (j + 1) * vs : nullptr);
             if (tid == 0 && !s_dead) issue(q + ST);
-            // t_{j+1} (rows < r; not for j = J-1) -> ts_{j+1} and the vector; u_j (rows >= r) -> s slot j-1
-            store(2 * r, out, j + 1 <= J - 1 ? ts + (j + 1) * vs : nullptr, ts + (j - 1) * vs + (long long)r * Bw);
-#pragma unroll
-            for (int p = 0; p < PT; p++) {
-                const int e = tid + 256 * p;
-                if (e < r * NB) vb[e] = out[p];
-                cur[p] = nxt[p];
-            }
-            __syncthreads();
+            T2 *t = vc;
+            vc = vx;
+            vx = t;
         }
-        if (s_dead == 0 && J >= 3) {
-            __threadfence_block();
-            __syncthreads();
-            // backward: s_{J-2} = u_{J-1} (already in its slot), s_{j-1} = u_j + N_{j-1} s_j
+        if (s_dead == 0) {
+            // s_{J-2} = u_{J-1}
             for (int e = tid; e < r * NB; e += 256) {
                 const int i = e / NB, n = e % NB;
-                vb[e] = n0 + n < Bw ? ts[(J - 2) * vs + (long long)(r + i) * Bw + n0 + n] : czero<T2>();
+                const T2 u = bs[(long long)(J - 1) * 2 * r * NB + (r + i) * NB + n];
+                vc[e] = u;
+                if (n0 + n < Bw) ts[(J - 2) * vs + (long long)(r + i) * Bw + n0 + n] = u;
             }
-            load_base(ts + (J - 3) * vs + (long long)r * Bw, r, cur);  // u_{J-2}
             __syncthreads();
-            for (int j = J - 2; j >= 1; j--, q++) {
-                if (j - 1 >= 1) load_base(ts + (j - 2) * vs + (long long)r * Bw, r, nxt);  // u_{j-1}
+            for (int j = J - 2; j >= 1; j--, q++) {  // backward: s_{j-1} = u_j + N_{j-1} s_j
                 if (!wait(q)) break;
-                mul(ring + (q % ST) * 2 * r2, r, cur, out);
-                __syncthreads();
+                step(ring + (q % ST) * 2 * r2, r, bs + (long long)j * 2 * r * NB + r * NB, vc, vx,
+                     ts + (j - 1) * vs + (long long)r * Bw);
                 if (tid == 0 && !s_dead) issue(q + ST);
-                store(r, out, ts + (j - 1) * vs + (long long)r * Bw, nullptr);
-#pragma unroll
-                for (int p = 0; p < PT; p++) {
-                    const int e = tid + 256 * p;
-                    if (e < r * NB) vb[e] = out[p];
-                    cur[p] = nxt[p];
-                }
-                __syncthreads();
+                T2 *t = vc;
+                vc = vx;
+                vx = t;
             }
         }
     }
     // after a timeout: let the copies this CTA issued land before it leaves (bounded)
     if (tid == 0 && s_dead) {
-        for (int q = q_waited; q < q_issued; q++) mb_wait(su32(&full[q % ST]), (unsigned)((q / ST) & 1), dead, err);
+        for (int qq = q_waited; qq < q_issued; qq++) mb_wait(su32(&full[qq % ST]), (unsigned)((qq / ST) & 1), dead, err);
     }
     __syncthreads();
 }
 
-template <class T2>
-static void launch_lr_chain(hz_ctx *c, const int *ids, int nl, const T2 *MRN, const T2 *AC, T2 *TS, int Bw) {
-    const int r = c->lr_r;
-    if (r > 64) throw HzError(HZ_EINVAL, "compressed-block LU: rank above 64");
-    constexpr int ST = sizeof(T2) == 8 ? 3 : 2;
-    // 4 right-hand sides per CTA for narrow batches (more CTAs, shorter steps), else 16
-    const int NB = Bw <= 32 ? 4 : 16;
-    const size_t sm = sizeof(T2) * ((size_t)ST * 2 * r * r + (size_t)r * NB);
-    if (sm > 220 * 1024) throw HzError(HZ_EINVAL, "compressed-block LU: rank too large for the recursion kernel");
-    static size_t attr4 = 0, attr16 = 0;
-    size_t &attr = NB == 4 ? attr4 : attr16;
-    auto kern = NB == 4 ? k_lr_chain<T2, 4> : k_lr_chain<T2, 16>;
+template <class T2, int NB> static size_t lr_smem(int r, int J) {
+    return sizeof(T2) * ((size_t)3 * 2 * r * r + 2 * (size_t)r * NB + (size_t)J * 2 * r * NB);
+}
+
+template <class T2, int NB>
+static bool lr_chain_cfg(hz_ctx *c, const int *ids, int nl, const T2 *MRN, const T2 *AC, T2 *TS, int Bw) {
+    const int r = c->lr_r, J = c->C - 1;
+    const size_t sm = lr_smem<T2, NB>(r, J);
+    if (sm > 220 * 1024) return false;
+    static size_t attr = 0;
     if (sm > 48 * 1024 && sm > attr) {
-        HZ_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HZ_CU(cudaFuncSetAttribute(k_lr_chain<T2, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = sm;
     }
-    kern<<<dim3((Bw + NB - 1) / NB, nl), 256, sm, c->st>>>(c->d_layers, ids, MRN, AC, TS, r, Bw, c->d_err);
+    k_lr_chain<T2, NB><<<dim3((Bw + NB - 1) / NB, nl), 256, sm, c->st>>>(c->d_layers, ids, MRN, AC, TS, r, Bw,
+                                                                         c->d_err);
     HZ_CU(cudaGetLastError());
     c->nl++;
+    return true;
+}
+
+template <class T2>
+static void launch_lr_chain(hz_ctx *c, const int *ids, int nl, const T2 *MRN, const T2 *AC, T2 *TS, int Bw) {
+    if (c->lr_r > 64) throw HzError(HZ_EINVAL, "compressed-block LU: rank above 64");
+    // narrow batches: 4 right-hand sides per CTA (more CTAs, shorter steps); else the
+    // widest tile whose vectors fit in shared memory
+    bool ok = false;
+    if (Bw > 32) ok = lr_chain_cfg<T2, 16>(c, ids, nl, MRN, AC, TS, Bw);
+    if (!ok && Bw > 32) ok = lr_chain_cfg<T2, 8>(c, ids, nl, MRN, AC, TS, Bw);
+    if (!ok) ok = lr_chain_cfg<T2, 4>(c, ids, nl, MRN, AC, TS, Bw);
+    if (!ok) throw HzError(HZ_EINVAL, "compressed-block LU: rank too large for the recursion kernel");
 }
 
 // ------------------------------------------------- problem-list build ---
