@@ -367,7 +367,8 @@ def run_ours(args, rank, world):
         "config": {"workload": main_["workload"], "B": main_["B"], "n_x": main_["n_x"], "n_z": main_["n_z"],
                    "L": main_["L"], "C": main_["C"], "precision": args.precision,
                    "frequencies": main_["frequencies"], "krylov": args.krylov, "precond": args.precond,
-                   "inner": args.inner, "compress": args.compress,
+                   "inner": args.inner,
+                   "compress": args.compress if args.compress >= 0 else (1e-8 if args.precision == "mixed" else 0.0),
                    "autotune": args.autotune, "rhs_lanes": args.rhs_lanes,
                    "tensor_cores": "off" if args.no_tensor_cores else
                    ("cell solves + batched products" if args.tc_gemm else "cell solves"),
@@ -510,8 +511,9 @@ def main():
     ap.add_argument("--inner", default="lu", choices=["lu", "nested"],
                     help="local solver of the layers: exact inner block LU or inner nested polarized traces")
     ap.add_argument("--inner-tol", type=float, default=0.0, help="nested inner level: preconditioner inner tolerance")
-    ap.add_argument("--compress", type=float, default=0.0,
-                    help="compressed-block LU tolerance for the inner factors (0: dense factors)")
+    ap.add_argument("--compress", type=float, default=-1.0,
+                    help="compressed-block LU tolerance for the inner factors (0: dense; < 0: library default, "
+                         "1e-8 in mixed precision)")
     ap.add_argument("--autotune", action="store_true", help="time the sweep launch configurations during warm-up")
     ap.add_argument("--tol", type=float, default=0.0, help="GMRES tolerance of the first pass (0: library default)")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)

@@ -133,7 +133,9 @@ typedef struct {
                            product, r the largest numerical rank at relative
                            Frobenius accuracy `compress` found by an adaptive
                            randomized range finder; the inner sweeps then run on
-                           r-vectors.  0 (default): dense factors */
+                           r-vectors.  0: dense factors; < 0 (the default):
+                           1e-8 (the paper's accuracy for the compressed
+                           operators) in HZ_MIXED, dense in HZ_FP64 */
     double inner_tol;   /* HZ_INNER_NESTED: relative GMRES tolerance of the inner
                            solves inside the preconditioner (<= 0: 1e-6); the
                            polarized operator, the Newton potentials and the

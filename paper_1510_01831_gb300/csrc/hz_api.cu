@@ -146,6 +146,7 @@ void hz_default_opts(hz_opts *o) {
     o->tensor_cores = 1;
     o->rhs_lanes = 1;
     o->wait_ms = 1000.0;
+    o->compress = -1.0;  // automatic: 1e-8 in mixed precision, dense in FP64
 }
 
 // HZ_FAULT=alloc[:n] | singular | nan | noconv (documented in hz.h)
@@ -214,6 +215,7 @@ hz_status hz_setup(hz_ctx **out, const double *m, int n_x, int n_z, double omega
         return fail(nullptr, HZ_EINVAL, "inner HZ_INNER_NESTED needs C >= 2, krylov HZ_GMRES and rhs_lanes 1");
     }
     if (!(c->opts.inner_tol > 0)) c->opts.inner_tol = 1e-6;
+    if (c->opts.compress < 0) c->opts.compress = c->opts.precision == HZ_MIXED ? 1e-8 : 0.0;
     if (!(c->opts.compress >= 0) || c->opts.compress >= 1) {
         delete c;
         return fail(nullptr, HZ_EINVAL, "compress must be 0 (dense) or a tolerance in (0, 1)");

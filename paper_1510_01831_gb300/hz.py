@@ -150,7 +150,7 @@ class Context:
     def __init__(self, m, n_x, n_z, omega, h, n_pml, L, C, precision=HZ_FP64, precond=HZ_PGS, tol=0.0,
                  refine_tol=1e-8, max_refine=6, restart=30, max_it=200, pml_C=0.0, layer_rows=None,
                  cell_cols=None, device_ptrs=False, stream=None, time_kernels=False, tensor_cores=True, krylov=0, autotune=False,
-                 rhs_lanes=1, wait_ms=0.0, inner=HZ_INNER_LU, inner_tol=0.0, compress=0.0):
+                 rhs_lanes=1, wait_ms=0.0, inner=HZ_INNER_LU, inner_tol=0.0, compress=None):
         self._ctx = None
         lib = load()
         o = hz_default_opts()
@@ -174,7 +174,8 @@ class Context:
             o.wait_ms = float(wait_ms)
         o.inner = int(inner)
         o.inner_tol = float(inner_tol)
-        o.compress = float(compress)
+        if compress is not None:  # None: the library default (1e-8 in mixed precision, dense in FP64)
+            o.compress = float(compress)
         m = np.ascontiguousarray(m, dtype=np.float64)
         if m.shape != (n_z + 2 * n_pml, n_x + 2 * n_pml):
             raise ValueError(f"m has shape {m.shape}, expected {(n_z + 2 * n_pml, n_x + 2 * n_pml)}")

@@ -33,6 +33,7 @@ def test_default_opts():
     assert o.precision == hz.HZ_FP64 and o.precond == hz.HZ_PGS
     assert o.restart == 30 and o.max_it == 200 and o.refine_tol == 1e-8
     assert o.wait_ms == 1000.0
+    assert o.compress == -1.0  # automatic: compressed inner factors in mixed precision
 
 
 def test_struct_layouts_match_header():
