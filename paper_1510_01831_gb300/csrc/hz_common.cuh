@@ -112,8 +112,9 @@ struct LayerDesc {
     long long zoff;      // offset of the layer's per-row arrays (nz entries)
     // compressed-block LU (rank r of the context): C-1 blocks of 2r x 2nz (STW, and
     // their transposes' shape 2nz x 2r for UX), C-1 triples of r x r (MRN), C-1 vectors
-    // of 2r per right-hand side (the recursion's inputs AC and outputs TS)
-    long long lr_off, m_off, ac_off;
+    // of 2r per right-hand side (the recursion's inputs AC and outputs TS), and the
+    // recursion as one linear map TS = LAM AC (2r(C-1) x 2r(C-1))
+    long long lr_off, m_off, ac_off, lam_off;
 };
 
 // Batched, segmented complex GEMM problem:  Y (+)= alpha (A X + A2 X2)
@@ -180,6 +181,14 @@ int gemm_tiles(int M, int N, int cfg);
 // skinny batched GEMM: every problem's N <= nmax <= 16; max_m = most rows of a problem
 template <class T2>
 void launch_gemm_skinny(const GemmProb<T2> *d_probs, int nprob, int max_m, int nmax, cudaStream_t st, int *nl);
+// narrow batched GEMM: K block, warps per CTA, columns, CTAs resident per SM, and the
+// split-K workspace (partial 32 x NW_NB tiles and their counters)
+constexpr int NW_KB = 16, NW_WPC = 4, NW_NB = 16, NW_CTAS_PER_SM = 4, NW_WS_SLOTS = 2048;
+// narrow batched GEMM (FP32): every problem's N <= nmax <= NW_NB; max_tiles = most 32-row
+// tiles of a problem; split = K slices per tile (<= 8; > 1 needs ws and cnt, whose
+// slots are problem * max_tiles + tile)
+void launch_gemm_narrow(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int nmax, int split, float2 *ws,
+                        int *cnt, cudaStream_t st, int *nl);
 // batched GEMM tile (complex outputs) and K step
 constexpr int GBM = 64, GBN = 32, GBK = 16;
 // split-K is used while a launch has fewer tiles than this; its workspace

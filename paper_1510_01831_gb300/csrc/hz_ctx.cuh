@@ -21,6 +21,9 @@ template <class T2> struct Ops {
     // STW_j = [BP_{j+1} W_j; BV_{j-1} W_j] (2r x 2nz), UX_j = [QP_j QV_j] (2nz x 2r),
     // MRN_j = [BP_j QP_{j-1}, BV_j QP_{j+1}, BV_j QV_{j+1}] (three r x r)
     T2 *STW = nullptr, *UX = nullptr, *MRN = nullptr;
+    // the r-vector recursion of a layer as one matrix: ts = LAM ac (ac, ts in their
+    // [C-1][2r] layout), applied as one product where a single layer is solved
+    T2 *LAM = nullptr;
 };
 
 // Problem lists of batched GEMMs, kept on the device (built once per workspace).
@@ -32,6 +35,7 @@ template <class T2> struct ProbList {
     int tc_max_tiles = 0;         // tensor-core GEMM: most 128 x 64 tiles of a problem,
     int tc_kchunks = 0;           // most K chunks of 16 (both passes), and
     long long tc_tiles = 0;       // tiles of the whole list
+    long long tiles32 = 0;        // 32-row tiles of the whole list
     int max_m = 0, max_n = 0;     // most rows and most right-hand-side columns of a problem
     double bytes = 0, flops = 0;  // algorithmic traffic and real flops of one launch
 };
@@ -83,7 +87,10 @@ template <class T2> struct Work {
     // hB / h2B then also hold ac_j = STW_j g_j (layer by layer with the h_j problems)
     ProbList<T2> uxB, ux2B;
     std::vector<int> uoff;
+    // compressed-block LU of one layer at a time: ts = LAM ac, problem l of layer l
+    ProbList<T2> lamB, lam2B;
     std::vector<double> hbytes, hflops;  // per layer (B wide)
+    std::vector<long long> htiles, utiles;  // 32-row tiles per layer of the h_j and x_j lists
 };
 
 }  // namespace hz
@@ -117,7 +124,7 @@ struct hz_ctx {
     long long tot_vol = 0, tot_W = 0, tot_F = 0, tot_E = 0, tot_S = 0, tot_K = 0;
     long long tot_inner = 0, tot_Wi = 0, tot_P = 0, tot_V = 0;
     int lr_r = 0;  // compressed-block LU rank (0: dense inner factors)
-    long long tot_lr = 0, tot_m = 0, tot_ac = 0;
+    long long tot_lr = 0, tot_m = 0, tot_ac = 0, tot_lam = 0;
     int max_nx = 0, max_nz = 0, max_no = 0;
     // global medium and PML profiles (FP64)
     std::vector<double> h_m;  // host copy of the medium (local model updates compare against it)
@@ -167,6 +174,8 @@ struct hz_ctx {
     int *gemm_cnt = nullptr;  // split-K arrival counters (zero between launches)
     float2 *tcg_ws = nullptr; // split-K partial tiles of the tensor-core GEMM (GEMM_TC_WS_TILES)
     int *tcg_cnt = nullptr;   // its arrival counters
+    float2 *nw_ws = nullptr;  // split-K partial tiles of the narrow GEMM (NW_WS_SLOTS)
+    int *nw_cnt = nullptr;    // its arrival counters
     // TF32 split copies of the operator blocks the tensor-core GEMM reads, keyed by
     // (block address, leading dimension, rows, columns), in device slabs
     std::map<std::tuple<const void *, long long, int, int>, float *> tca;

@@ -463,6 +463,18 @@ __global__ void k_block_t(const double2 *__restrict__ src, double2 *dst, const l
 }
 
 // run a host-built list of FP64 products (64 x 32 tiles, no split)
+// Unit columns that start the recursion on the identity (one thread per unit):
+// for layer q, lam[q] (rows [J][2r], Nc = 2rJ columns) gets t_{j+1} row i <- column
+// 2rj + i (j = 0..J-2), and u[q] ([J][r] rows) gets u_j row i <- column 2rj + r + i
+__global__ void k_lam_init(double2 *const *lam, double2 *const *u, int r, int J) {
+    const int q = blockIdx.y, Nc = 2 * r * J;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < J * r; e += gridDim.x * blockDim.x) {
+        const int j = e / r, i = e % r;
+        if (j <= J - 2) lam[q][((long long)(j + 1) * 2 * r + i) * Nc + (long long)j * 2 * r + i] = make_double2(1.0, 0.0);
+        u[q][((long long)j * r + i) * Nc + (long long)j * 2 * r + r + i] = make_double2(1.0, 0.0);
+    }
+}
+
 static void run_list64(hz_ctx *c, const std::vector<GemmProb<double2>> &v) {
     if (v.empty()) return;
     int mt = 0;
@@ -497,7 +509,7 @@ static GemmProb<double2> prob64(const double2 *A, long long lda, int M, int K, i
 // multiple of 8) and the layers' offsets; later calls (local updates) must fit in it.
 static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<LayerDesc> &lsub, const double2 *Wi,
                            const double2 *Pm, const double2 *Vi, double2 *&STW, double2 *&UX, double2 *&MRN,
-                           bool first) {
+                           double2 *&LAM, bool first) {
     const double eps = c->opts.compress;
     const int C = c->C, J = C - 1;
     if (J < 2) return;
@@ -599,7 +611,7 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
     if (first) {
         c->lr_r = std::min(kmax, std::max(8, (kbig + 7) / 8 * 8));
         const int r = c->lr_r;
-        long long lo = 0, mo = 0, ao = 0;
+        long long lo = 0, mo = 0, ao = 0, la = 0;
         for (LayerDesc &ld : c->layers) {
             ld.lr_off = lo;
             lo += (long long)J * 2 * r * 2 * ld.nz;
@@ -607,10 +619,13 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
             mo += (long long)J * 3 * r * r;
             ld.ac_off = ao;
             ao += (long long)J * 2 * r;
+            ld.lam_off = la;
+            la += (long long)(2 * r * J) * (2 * r * J);
         }
         c->tot_lr = lo;
         c->tot_m = mo;
         c->tot_ac = ao;
+        c->tot_lam = la;
         HZ_CU(cudaMemcpyAsync(c->d_layers, c->layers.data(), sizeof(LayerDesc) * c->layers.size(),
                               cudaMemcpyHostToDevice, c->st));
         for (int q = 0; q < (int)lsub.size(); q++) lsub[q] = c->layers[lays[q]];
@@ -624,6 +639,7 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
     if (!STW) STW = alloc_n<double2>(c, c->tot_lr);
     if (!UX) UX = alloc_n<double2>(c, c->tot_lr);
     if (!MRN) MRN = alloc_n<double2>(c, c->tot_m);
+    if (!LAM) LAM = alloc_n<double2>(c, c->tot_lam);
     // STW_j = [BP_{j+1} W_j; BV_{j-1} W_j], UX_j = [QP_j QV_j], and the r x r matrices of the
     // recursion in the order of its steps: forward step j (1..J-1) at (j-1) 2r^2 holds
     // [M_{j+1}; R_{j-1}] (M_j = BP_j QP_{j-1}, R_j = BV_j QP_{j+1}; M_J = 0), backward step j
@@ -671,6 +687,65 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
         }
     }
     run_list64(c, v);
+    {  // LAM: the recursion below run on the identity (all 2rJ unit columns at once), as
+       // FP64 products over the layers, one list per step, with the step matrices still
+       // stored row-major
+        const int Nc = 2 * r * J, nq = (int)lsub.size();
+        const long long rr = (long long)r * r, unit = (long long)r * Nc;
+        double2 *U = alloc_n<double2>(c, (long long)nq * J * unit);
+        HZ_CU(cudaMemsetAsync(U, 0, sizeof(double2) * nq * J * unit, c->st));
+        std::vector<double2 *> lp(nq), up(nq);
+        for (int q = 0; q < nq; q++) {
+            lp[q] = LAM + lsub[q].lam_off;
+            up[q] = U + (long long)q * J * unit;
+            HZ_CU(cudaMemsetAsync(lp[q], 0, sizeof(double2) * Nc * Nc, c->st));
+        }
+        double2 **dp = (double2 **)c->dalloc(sizeof(double2 *) * 2 * nq);
+        HZ_CU(cudaMemcpyAsync(dp, lp.data(), sizeof(double2 *) * nq, cudaMemcpyHostToDevice, c->st));
+        HZ_CU(cudaMemcpyAsync(dp + nq, up.data(), sizeof(double2 *) * nq, cudaMemcpyHostToDevice, c->st));
+        k_lam_init<<<dim3(8, nq), 256, 0, c->st>>>(dp, dp + nq, r, J);
+        HZ_CU(cudaGetLastError());
+        c->nl++;
+        // forward: [t_{j+1}; u_j] += [M_{j+1}; R_{j-1}] t_j (t_J is not kept)
+        for (int j = 1; j <= J - 1; j++) {
+            std::vector<GemmProb<double2>> w;
+            for (int q = 0; q < nq; q++) {
+                const double2 *blk = MRN + lsub[q].m_off + (long long)(j - 1) * 2 * rr;
+                const double2 *tj = lp[q] + (long long)j * 2 * r * Nc;
+                if (j + 1 <= J - 1) {
+                    GemmProb<double2> g = prob64(blk, r, 2 * r, r, Nc, tj, Nc, lp[q] + (long long)(j + 1) * 2 * r * Nc, Nc);
+                    g.yseg = r;
+                    g.Y[1] = up[q] + (long long)j * unit;
+                    g.beta = 1;
+                    w.push_back(g);
+                } else {
+                    GemmProb<double2> g = prob64(blk + rr, r, r, r, Nc, tj, Nc, up[q] + (long long)j * unit, Nc);
+                    g.beta = 1;
+                    w.push_back(g);
+                }
+            }
+            run_list64(c, w);
+        }
+        // backward: s_{j-1} = u_j + N_{j-1} s_j, from s_{J-2} = u_{J-1} (s_{J-1} = 0)
+        for (int q = 0; q < nq; q++)
+            HZ_CU(cudaMemcpy2DAsync(lp[q] + (long long)r * Nc, sizeof(double2) * 2 * unit, up[q] + unit,
+                                    sizeof(double2) * unit, sizeof(double2) * unit, J - 1, cudaMemcpyDeviceToDevice,
+                                    c->st));
+        for (int j = J - 2; j >= 1; j--) {
+            std::vector<GemmProb<double2>> w;
+            for (int q = 0; q < nq; q++) {
+                const double2 *nb = MRN + lsub[q].m_off + (long long)(J - 1) * 2 * rr + (long long)(J - 2 - j) * rr;
+                GemmProb<double2> g = prob64(nb, r, r, r, Nc, lp[q] + ((long long)j * 2 * r + r) * Nc, Nc,
+                                             lp[q] + ((long long)(j - 1) * 2 * r + r) * Nc, Nc);
+                g.beta = 1;
+                w.push_back(g);
+            }
+            run_list64(c, w);
+        }
+        HZ_CU(cudaStreamSynchronize(c->st));
+        c->dfree(dp);
+        c->dfree(U);
+    }
     {  // each step's matrix transposed in place (through a copy of the layers' ranges)
         std::vector<long long> offs;
         std::vector<int> rws, cls;
@@ -929,18 +1004,20 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
     c->dfree(Zi);
 
     // 3b. compressed-block LU: low-rank P_j, V_j and the operators of the r-vector recursion
-    double2 *STW64 = nullptr, *UX64 = nullptr, *MRN64 = nullptr;
+    double2 *STW64 = nullptr, *UX64 = nullptr, *MRN64 = nullptr, *LAM64 = nullptr;
     if (c->opts.compress > 0 && C > 2) {
         if (!mixed) {  // kept by the context in FP64 (allocated by the first call)
             STW64 = c->o64.STW;
             UX64 = c->o64.UX;
             MRN64 = c->o64.MRN;
+            LAM64 = c->o64.LAM;
         }
-        compress_inner(c, lays, lsub, Wi, Pm, Vi, STW64, UX64, MRN64, first);
+        compress_inner(c, lays, lsub, Wi, Pm, Vi, STW64, UX64, MRN64, LAM64, first);
         if (!mixed) {
             c->o64.STW = STW64;
             c->o64.UX = UX64;
             c->o64.MRN = MRN64;
+            c->o64.LAM = LAM64;
         }
     }
 
@@ -986,15 +1063,19 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
                 o.STW = alloc_n<float2>(c, c->tot_lr);
                 o.UX = alloc_n<float2>(c, c->tot_lr);
                 o.MRN = alloc_n<float2>(c, c->tot_m);
+                o.LAM = alloc_n<float2>(c, c->tot_lam);
                 to_f32(STW64, o.STW, c->tot_lr, st, nl);
                 to_f32(UX64, o.UX, c->tot_lr, st, nl);
                 to_f32(MRN64, o.MRN, c->tot_m, st, nl);
+                to_f32(LAM64, o.LAM, c->tot_lam, st, nl);
             } else {
                 for (const LayerDesc &ld : lsub) {
                     const long long nlr = (long long)J * 2 * r * 2 * ld.nz, nm = (long long)J * 3 * r * r;
+                    const long long nlam = (long long)(2 * r * J) * (2 * r * J);
                     to_f32(STW64 + ld.lr_off, o.STW + ld.lr_off, nlr, st, nl);
                     to_f32(UX64 + ld.lr_off, o.UX + ld.lr_off, nlr, st, nl);
                     to_f32(MRN64 + ld.m_off, o.MRN + ld.m_off, nm, st, nl);
+                    to_f32(LAM64 + ld.lam_off, o.LAM + ld.lam_off, nlam, st, nl);
                 }
             }
         }
@@ -1016,7 +1097,7 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
         }
         HZ_CU(cudaStreamSynchronize(st));
         for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi,
-                        (void *)STW64, (void *)UX64, (void *)MRN64})
+                        (void *)STW64, (void *)UX64, (void *)MRN64, (void *)LAM64})
             c->dfree(q);
     }
     c->dfree(d_info);

@@ -366,6 +366,175 @@ void launch_gemm_skinny(const GemmProb<T2> *d_probs, int nprob, int max_m, int n
 }
 template void launch_gemm_skinny<float2>(const GemmProb<float2> *, int, int, int, cudaStream_t, int *);
 
+// Narrow form of the batched GEMM (FP32) for panels of at most NB = 16 or 32
+// right-hand-side columns, the batch widths of a sweep step's products and of
+// the 2B-wide layer-parallel ones.  Such a product is a stream over the
+// operator: every element of A meets all N columns once, 4 N flops per 8
+// bytes, so the kernel is built to keep many operator bytes in flight.  A CTA
+// of NW_WPC warps owns 32 rows of one problem (lane = row) and one K slice of
+// the K blocks of both operand pairs laid end to end; its warps take the
+// slice's blocks of NW_KB in turn.  Each warp runs its own ring of NW_NS
+// stages filled by asynchronous copies (A block 32 x NW_KB, row-padded, and
+// the X block NW_KB x NB), NW_NS - 1 blocks ahead of its products; A is read
+// back along the lane's row and X as 16-byte broadcasts.  The warps' partial
+// sums are added in warp order; with several K slices per tile (S > 1) the
+// last slice to finish adds the slices' sums in slice order (deterministic)
+// and re-arms the tile's counter.
+template <int NB> __host__ __device__ constexpr int nw_stages() { return 2; }
+template <int NB> __host__ __device__ constexpr int nw_stage_elems() { return 32 * (NW_KB + 1) + NW_KB * NB; }
+template <int NB> constexpr size_t nw_smem() {
+    return sizeof(float2) * (size_t)NW_WPC * nw_stages<NB>() * nw_stage_elems<NB>();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<float2> *__restrict__ probs, int S,
+                                                             float2 *ws, int *cnt, int max_tiles) {
+    constexpr int NS = nw_stages<NB>(), STG = nw_stage_elems<NB>(), ASZ = 32 * (NW_KB + 1);
+    __shared__ GemmProb<float2> P;
+    __shared__ int last;
+    extern __shared__ __align__(16) unsigned char nsm[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2 *wb = reinterpret_cast<float2 *>(nsm) + warp * NS * STG;
+    static_assert(sizeof(GemmProb<float2>) % 8 == 0, "problem descriptor copied as 8-byte words");
+    for (int w = tid; w < (int)(sizeof(GemmProb<float2>) / 8); w += NW_WPC * 32)
+        reinterpret_cast<long long *>(&P)[w] = reinterpret_cast<const long long *>(probs + blockIdx.y)[w];
+    __syncthreads();
+    const int M = P.M, N = P.N;
+    const int tile = blockIdx.x / S, sp = blockIdx.x % S, m0 = tile * 32;
+    if (m0 >= M) return;  // uniform over the CTA and over the tile's slices
+    const int K1 = max(P.K, 0), K2 = max(P.K2, 0);
+    const int nb1 = (K1 + NW_KB - 1) / NW_KB, nbt = nb1 + (K2 + NW_KB - 1) / NW_KB;
+    const int bps = (nbt + S - 1) / S, b0 = min(nbt, sp * bps), b1 = min(nbt, b0 + bps);
+    const int nmine = b1 - b0 > warp ? (b1 - b0 - warp + NW_WPC - 1) / NW_WPC : 0;
+    const int ak = lane & 15, ah = lane >> 4;  // A copies: column ak of rows 2 i + ah
+    auto issue = [&](int t) {
+        float2 *As = wb + (t % NS) * STG, *Xs = As + ASZ;
+        const int b = b0 + warp + t * NW_WPC;
+        const bool p2 = b >= nb1;
+        const int k0 = (p2 ? b - nb1 : b) * NW_KB, K = p2 ? K2 : K1;
+        const float2 *A = p2 ? P.A2 : P.A;
+        const long long lda = p2 ? P.lda2 : P.lda;
+        const int xseg = p2 ? P.xseg2 : P.xseg;
+        const long long ldx = p2 ? P.ldx2 : P.ldx;
+        const float2 *const *Xp = p2 ? P.X2 : P.X;
+        const int gk = k0 + ak;
+        const bool kin = gk < K;
+#pragma unroll
+        for (int i = 0; i < 16; i++) {
+            const int r = 2 * i + ah, gm = m0 + r;
+            const bool ok = kin && gm < M;
+            gemm_cp<8>(As + r * (NW_KB + 1) + ak, ok ? A + (long long)gm * lda + gk : A, ok ? 8u : 0u);
+        }
+        const bool one = xseg >= K;  // a single segment: no division
+#pragma unroll
+        for (int q = 0; q < NB / 2; q++) {
+            const int e = lane + 32 * q, xr = e / NB, xc = e % NB, gx = k0 + xr;
+            const bool ok = gx < K && xc < N;
+            const float2 *src = A;
+            if (ok) {
+                const int sg = one ? 0 : gx / xseg;
+                src = Xp[sg] + (long long)(gx - sg * xseg) * ldx + xc;
+            }
+            gemm_cp<8>(Xs + xr * NB + xc, src, ok ? 8u : 0u);
+        }
+    };
+    float2 acc[NB];
+#pragma unroll
+    for (int n = 0; n < NB; n++) acc[n] = czero<float2>();
+#pragma unroll
+    for (int t = 0; t < NS - 1; t++) {  // prologue: the first NS - 1 blocks in flight
+        if (t < nmine) issue(t);
+        gemm_cp_commit();
+    }
+    for (int t = 0; t < nmine; t++) {
+        gemm_cp_wait<NS - 2>();  // this lane's copies of block t have landed
+        __syncwarp();            // every lane's have; every lane is done with block t - 1
+        if (t + NS - 1 < nmine) issue(t + NS - 1);  // into the stage of block t - 1
+        gemm_cp_commit();
+        const float2 *As = wb + (t % NS) * STG + lane * (NW_KB + 1), *Xs = wb + (t % NS) * STG + ASZ;
+#pragma unroll 4
+        for (int kk = 0; kk < NW_KB; kk++) {
+            const float2 a = As[kk];
+#pragma unroll
+            for (int n = 0; n < NB; n += 2) {
+                const Pair<float2> x = ld_pair(Xs + kk * NB + n);
+                cmac(acc[n], a, x.a);
+                cmac(acc[n + 1], a, x.b);
+            }
+        }
+    }
+    gemm_cp_wait<0>();
+    __syncthreads();  // every warp is done with its ring: it holds the partial sums now
+    float2 *red = reinterpret_cast<float2 *>(nsm);  // [warp][32 rows][NB + 1]
+#pragma unroll
+    for (int n = 0; n < NB; n++) red[(warp * 32 + lane) * (NB + 1) + n] = acc[n];
+    __syncthreads();
+    const long long slot = (long long)blockIdx.y * max_tiles + tile;
+    if (S > 1) {
+        float2 *mine = ws + (slot * S + sp) * (32 * NB);
+        for (int e = tid; e < 32 * NB; e += NW_WPC * 32) {
+            const int r = e / NB, n = e % NB;
+            float2 v = red[r * (NB + 1) + n];
+#pragma unroll
+            for (int w = 1; w < NW_WPC; w++) v = v + red[(w * 32 + r) * (NB + 1) + n];
+            mine[e] = v;
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) last = atomicAdd(&cnt[slot], 1) == S - 1;
+        __syncthreads();
+        if (!last) return;
+        __threadfence();
+    }
+    const float al = P.alpha;
+    for (int e = tid; e < 32 * NB; e += NW_WPC * 32) {
+        const int r = e / NB, n = e % NB, m = m0 + r;
+        if (m >= M || n >= N) continue;
+        float2 v;
+        if (S > 1) {
+            v = czero<float2>();
+            for (int q = 0; q < S; q++) {
+                const float2 w = __ldcg(ws + (slot * S + q) * (32 * NB) + e);
+                v.x += w.x;
+                v.y += w.y;
+            }
+        } else {
+            v = red[r * (NB + 1) + n];
+#pragma unroll
+            for (int w = 1; w < NW_WPC; w++) v = v + red[(w * 32 + r) * (NB + 1) + n];
+        }
+        v.x *= al;
+        v.y *= al;
+        const int sg = m / P.yseg;
+        float2 *row = P.Y[sg] + (long long)(m - sg * P.yseg) * P.ldy;
+        row[n] = P.beta ? row[n] + v : v;
+    }
+    if (S > 1 && tid == 0) cnt[slot] = 0;
+}
+
+template <int NB>
+static void launch_narrow_cfg(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int split, float2 *ws,
+                              int *cnt, cudaStream_t st) {
+    const size_t sm = nw_smem<NB>();
+    static bool attr = false;
+    if (!attr) {
+        HZ_CU(cudaFuncSetAttribute(k_gemm_narrow<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = true;
+    }
+    k_gemm_narrow<NB><<<dim3(max_tiles * split, nprob), NW_WPC * 32, sm, st>>>(d_probs, split, ws, cnt, max_tiles);
+}
+
+void launch_gemm_narrow(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int nmax, int split, float2 *ws,
+                        int *cnt, cudaStream_t st, int *nl) {
+    if (nprob <= 0 || max_tiles <= 0) return;
+    if (nmax > NW_NB) throw HzError(HZ_EINVAL, "narrow GEMM: too many columns");
+    if (split < 1 || split > 8 || (split > 1 && (!ws || !cnt || (long long)nprob * max_tiles * split > NW_WS_SLOTS)))
+        throw HzError(HZ_EINVAL, "narrow GEMM: bad split-K workspace");
+    launch_narrow_cfg<NW_NB>(d_probs, nprob, max_tiles, split, ws, cnt, st);
+    HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+
 int gemm_tiles(int M, int N, int cfg) {
     const int bm = cfg == 1 ? 32 : 64, bn = cfg == 2 ? 16 : 32;
     return ((M + bm - 1) / bm) * ((N + bn - 1) / bn);

@@ -762,13 +762,20 @@ static void launch_lr_chain(hz_ctx *c, const int *ids, int nl, const T2 *MRN, co
     if (!ok) throw HzError(HZ_EINVAL, "compressed-block LU: rank too large for the recursion kernel");
 }
 
+// whether the recursion kernel takes a launch of Bw right-hand sides
+template <class T2> static bool lr_chain_fits(hz_ctx *c, int Bw) {
+    const int r = c->lr_r, J = c->C - 1;
+    if (r > 64) return false;
+    return lr_smem<T2, 4>(r, J) <= 220 * 1024 || (Bw > 32 && lr_smem<T2, 8>(r, J) <= 220 * 1024);
+}
+
 // ------------------------------------------------- problem-list build ---
 template <class T2> struct ListBuilder {
     hz_ctx *c;
     Ops<T2> &o;
     std::vector<GemmProb<T2>> v;
     int max_tiles = 0, kmax = 0, max_tiles32 = 0, tc_max_tiles = 0, tc_kchunks = 0, max_m = 0, max_n = 0;
-    long long tc_tiles = 0;
+    long long tc_tiles = 0, tiles32 = 0;
     ListBuilder(hz_ctx *c_, Ops<T2> &o_) : c(c_), o(o_) {}
 
     double bytes = 0, flops = 0;
@@ -785,6 +792,7 @@ template <class T2> struct ListBuilder {
         v.push_back(g);
         max_tiles = std::max(max_tiles, ((g.M + GBM - 1) / GBM) * ((g.N + GBN - 1) / GBN));
         max_tiles32 = std::max(max_tiles32, gemm_tiles(g.M, g.N, 1));
+        tiles32 += gemm_tiles(g.M, g.N, 1);
         max_m = std::max(max_m, g.M);
         max_n = std::max(max_n, g.N);
         kmax = std::max(kmax, std::max(g.K, 0) + std::max(g.K2, 0));
@@ -888,6 +896,7 @@ template <class T2> struct ListBuilder {
         pl.tc_max_tiles = tc_max_tiles;
         pl.tc_kchunks = tc_kchunks;
         pl.tc_tiles = tc_tiles;
+        pl.tiles32 = tiles32;
         pl.max_m = max_m;
         pl.max_n = max_n;
         pl.bytes = bytes;
@@ -899,7 +908,7 @@ template <class T2> struct ListBuilder {
         }
         v.clear();
         max_tiles = kmax = max_tiles32 = tc_max_tiles = tc_kchunks = max_m = max_n = 0;
-        tc_tiles = 0;
+        tc_tiles = tiles32 = 0;
         return pl;
     }
 };
@@ -932,7 +941,7 @@ static bool run_tc(hz_ctx *c, const ProbList<float2> &pl) {
     if (split > 1 && !c->tcg_ws) {
         c->tcg_ws = (float2 *)c->dalloc(sizeof(float2) * (size_t)GEMM_TC_WS_TILES * GT_M * GT_N);
         c->tcg_cnt = (int *)c->dalloc(sizeof(int) * GEMM_TC_WS_TILES);
-        HZ_CU(cudaMemset(c->tcg_cnt, 0, sizeof(int) * GEMM_TC_WS_TILES));
+        HZ_CU(cudaMemsetAsync(c->tcg_cnt, 0, sizeof(int) * GEMM_TC_WS_TILES, c->st));
     }
     c->kt_begin(2, pl.bytes, pl.flops);
     launch_gemm_tc(pl.d, pl.n, pl.tc_max_tiles, split, c->tcg_ws, c->tcg_cnt, c->d_err, c->st, &c->nl);
@@ -941,13 +950,36 @@ static bool run_tc(hz_ctx *c, const ProbList<float2> &pl) {
 }
 static bool run_tc(hz_ctx *, const ProbList<double2> &) { return false; }
 
-template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
+template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl, int cls = 2) {
     if (!pl.n) return;
     if (run_tc(c, pl)) return;
+    // FP32 lists with panels of <= NW_NB columns: the narrow kernel, a stream over the
+    // operators with a block in flight per warp during the products of another; lists with
+    // few tiles and long K are cut into K slices so that one wave of NW_CTAS_PER_SM CTAs
+    // per SM takes part, each warp with at least two blocks
+    static const bool narrow = !getenv("HZ_GEMM") || strcmp(getenv("HZ_GEMM"), "tiled") != 0;
+    if (sizeof(T2) == 8 && narrow && pl.max_n <= NW_NB) {
+        const long long slots = (long long)pl.n * pl.max_tiles32, wave = 152LL * NW_CTAS_PER_SM;
+        const int nbk = (pl.kmax + NW_KB - 1) / NW_KB;
+        int split = 1;
+        if (pl.tiles32 > 0 && slots <= NW_WS_SLOTS)
+            split = (int)std::max(1LL, std::min<long long>({8, wave / pl.tiles32, NW_WS_SLOTS / slots,
+                                                            std::max(1, nbk / (2 * NW_WPC))}));
+        if (split > 1 && !c->nw_ws) {
+            c->nw_ws = (float2 *)c->dalloc(sizeof(float2) * (size_t)NW_WS_SLOTS * 32 * NW_NB);
+            c->nw_cnt = (int *)c->dalloc(sizeof(int) * NW_WS_SLOTS);
+            HZ_CU(cudaMemsetAsync(c->nw_cnt, 0, sizeof(int) * NW_WS_SLOTS, c->st));
+        }
+        c->kt_begin(cls, pl.bytes, pl.flops);
+        launch_gemm_narrow(reinterpret_cast<const GemmProb<float2> *>(pl.d), pl.n, pl.max_tiles32, pl.max_n, split,
+                           c->nw_ws, c->nw_cnt, c->st, &c->nl);
+        c->kt_end();
+        return;
+    }
     // FP32 short lists (a sweep step's products) with narrow panels (<= 16 columns):
     // the skinny kernel, whose K loop keeps the next block's loads in flight
     if (sizeof(T2) == 8 && pl.max_n <= 16 && (long long)pl.n * pl.max_tiles32 < GEMM_SPLIT_TILES) {
-        c->kt_begin(2, pl.bytes, pl.flops);
+        c->kt_begin(cls, pl.bytes, pl.flops);
         launch_gemm_skinny<T2>(pl.d, pl.n, pl.max_m, pl.max_n, c->st, &c->nl);
         c->kt_end();
         return;
@@ -961,9 +993,9 @@ template <class T2> static void run(hz_ctx *c, const ProbList<T2> &pl) {
     if (split > 1 && !c->gemm_ws) {
         c->gemm_ws = c->dalloc(sizeof(double2) * 2 * GEMM_SPLIT_TILES * GBM * GBN);
         c->gemm_cnt = (int *)c->dalloc(sizeof(int) * GEMM_SPLIT_TILES);
-        HZ_CU(cudaMemset(c->gemm_cnt, 0, sizeof(int) * GEMM_SPLIT_TILES));
+        HZ_CU(cudaMemsetAsync(c->gemm_cnt, 0, sizeof(int) * GEMM_SPLIT_TILES, c->st));
     }
-    c->kt_begin(2, pl.bytes, pl.flops);
+    c->kt_begin(cls, pl.bytes, pl.flops);
     launch_gemm<T2>(pl.d, pl.n, mt, split, (T2 *)c->gemm_ws, c->gemm_cnt, c->st, &c->nl, cfg);
     c->kt_end();
 }
@@ -1123,6 +1155,8 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
     W.hoff.assign(L + 1, 0);
     W.hbytes.assign(L, 0.0);
     W.hflops.assign(L, 0.0);
+    W.htiles.assign(L, 0);
+    W.utiles.assign(L, 0);
     for (int wide = 0; wide < 2; wide++) {
         const int Bw = wide ? 2 * B : B;
         // dense: h_j = W_j g_j from inner into innerH; compressed: from innerH into inner,
@@ -1137,6 +1171,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             const int n2 = 2 * ld.nz;
             if (!wide) W.hoff[l] = cnt;
             double b0 = lb.bytes, f0 = lb.flops;
+            const long long t0 = lb.tiles32;
             for (int j = 0; j < c->C - 1; j++) {
                 GemmProb<T2> g{};
                 g.A = o.W + ld.W_off + (long long)j * n2 * n2;
@@ -1163,6 +1198,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             if (!wide) {
                 W.hbytes[l] = lb.bytes - b0;
                 W.hflops[l] = lb.flops - f0;
+                W.htiles[l] = lb.tiles32 - t0;
             }
         }
         if (!wide) W.hoff[L] = cnt;
@@ -1184,6 +1220,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
                 const LayerDesc &ld = c->layers[l];
                 const int n2 = 2 * ld.nz;
                 if (!wide) W.uoff[l] = cnt;
+                const long long t0 = lb.tiles32;
                 for (int j = 0; j < c->C - 1; j++) {
                     GemmProb<T2> g{};
                     g.A = o.UX + ld.lr_off + (long long)j * n2 * 2 * r;
@@ -1200,12 +1237,38 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
                     lb.push(g);
                     cnt++;
                 }
+                if (!wide) W.utiles[l] = lb.tiles32 - t0;
             }
             if (!wide) W.uoff[L] = cnt;
             if (wide)
                 W.ux2B = lb.finish();
             else
                 W.uxB = lb.finish();
+        }
+        // ts = LAM ac, one problem per layer
+        const int Nc = 2 * r * (c->C - 1);
+        for (int wide = 0; wide < 2; wide++) {
+            const int Bw = wide ? 2 * B : B;
+            for (int l = 0; l < L; l++) {
+                const LayerDesc &ld = c->layers[l];
+                GemmProb<T2> g{};
+                g.A = o.LAM + ld.lam_off;
+                g.lda = Nc;
+                g.M = Nc;
+                g.K = Nc;
+                g.N = Bw;
+                g.xseg = g.yseg = 1 << 30;
+                g.ldx = g.ldy = Bw;
+                g.X[0] = (wide ? W.ac2 : W.ac) + ld.ac_off * Bw;
+                g.Y[0] = (wide ? W.ts2 : W.ts) + ld.ac_off * Bw;
+                g.beta = 0;
+                g.alpha = 1.f;
+                lb.push(g);
+            }
+            if (wide)
+                W.lam2B = lb.finish();
+            else
+                W.lamB = lb.finish();
         }
     }
     // single-layer applications (component entry point), inputs/outputs in lin/lout (B wide)
@@ -1244,6 +1307,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.h2B);
     fl(W.uxB);
     fl(W.ux2B);
+    fl(W.lamB);
+    fl(W.lam2B);
     for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer})
         for (auto &pl : *vv) fl(pl);
     if (W.hhost) cudaFreeHost(W.hhost);
@@ -1277,13 +1342,15 @@ template <class T2> Work<T2> &work(hz_ctx *c, int B) {
         W.ts = (T2 *)al(c->tot_ac * B, sizeof(T2));
         W.ac2 = (T2 *)al(c->tot_ac * 2 * B, sizeof(T2));
         W.ts2 = (T2 *)al(c->tot_ac * 2 * B, sizeof(T2));
+        HZ_CU(cudaMemsetAsync(W.ts, 0, sizeof(T2) * c->tot_ac * B, c->st));
+        HZ_CU(cudaMemsetAsync(W.ts2, 0, sizeof(T2) * c->tot_ac * 2 * B, c->st));
     }
-    HZ_CU(cudaMemset(W.inner, 0, sizeof(T2) * c->tot_inner * B));
-    HZ_CU(cudaMemset(W.inner2, 0, sizeof(T2) * c->tot_inner * 2 * B));
-    HZ_CU(cudaMemset(W.inner_f, 0, sizeof(T2) * c->tot_inner * B));
+    HZ_CU(cudaMemsetAsync(W.inner, 0, sizeof(T2) * c->tot_inner * B, c->st));
+    HZ_CU(cudaMemsetAsync(W.inner2, 0, sizeof(T2) * c->tot_inner * 2 * B, c->st));
+    HZ_CU(cudaMemsetAsync(W.inner_f, 0, sizeof(T2) * c->tot_inner * B, c->st));
     W.lin = (T2 *)al((long long)c->L * 4 * c->NX * 2 * B, sizeof(T2));
     W.lout = (T2 *)al((long long)c->L * 4 * c->NX * 2 * B, sizeof(T2));
-    HZ_CU(cudaMemset(W.lout, 0, sizeof(T2) * c->L * 4 * c->NX * 2 * B));
+    HZ_CU(cudaMemsetAsync(W.lout, 0, sizeof(T2) * c->L * 4 * c->NX * 2 * B, c->st));
     W.pa = (T2 *)al(ntr * B, sizeof(T2));
     W.pb = (T2 *)al(ntr * B, sizeof(T2));
     W.pc = (T2 *)al(ntr * B, sizeof(T2));
@@ -1318,9 +1385,11 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
     sub.n = W.hoff[l0 + nl] - W.hoff[l0];
     sub.tc_tiles = (long long)sub.n * all.tc_max_tiles;
     sub.bytes = sub.flops = 0;
+    sub.tiles32 = 0;
     for (int l = l0; l < l0 + nl; l++) {
         sub.bytes += W.hbytes[l] * (wide ? 2 : 1);
         sub.flops += W.hflops[l] * (wide ? 2 : 1);
+        sub.tiles32 += W.htiles[l];
     }
     run(c, sub);
     const int N = wide ? 2 * W.B : W.B;
@@ -1333,16 +1402,32 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
                 by += es * (3 * J * r * r + 4 * J * r * N);
                 fl += 8.0 * 3 * J * r * r * N;
             }
-        c->kt_begin(1, by, fl);
-        launch_lr_chain<T2>(c, c->d_layer_ids + l0, nl, o.MRN, wide ? W.ac2 : W.ac, wide ? W.ts2 : W.ts, N);
-        c->kt_end();
+        if (nl == 1 || !lr_chain_fits<T2>(c, N)) {
+            // one layer (a sweep step): the recursion as one product, ts = LAM ac, instead
+            // of 2(C-1) dependent steps on a few SMs
+            const ProbList<T2> &la = wide ? W.lam2B : W.lamB;
+            ProbList<T2> ls = la;
+            ls.d = la.d + l0;
+            ls.n = nl;
+            ls.tc_tiles = (long long)nl * la.tc_max_tiles;
+            ls.tiles32 = (long long)nl * la.max_tiles32;
+            ls.bytes = la.bytes * nl / c->L;
+            ls.flops = la.flops * nl / c->L;
+            run(c, ls, 1);
+        } else {
+            c->kt_begin(1, by, fl);
+            launch_lr_chain<T2>(c, c->d_layer_ids + l0, nl, o.MRN, wide ? W.ac2 : W.ac, wide ? W.ts2 : W.ts, N);
+            c->kt_end();
+        }
         const ProbList<T2> &ua = wide ? W.ux2B : W.uxB;
         ProbList<T2> us = ua;
         us.d = ua.d + W.uoff[l0];
         us.n = W.uoff[l0 + nl] - W.uoff[l0];
         us.tc_tiles = (long long)us.n * ua.tc_max_tiles;
         us.bytes = us.flops = 0;
+        us.tiles32 = 0;
         for (int l = l0; l < l0 + nl; l++) {
+            us.tiles32 += W.utiles[l];
             const double n2 = 2.0 * c->layers[l].nz, J = c->C - 1, es = sizeof(T2);
             us.bytes += es * J * (n2 * 2 * r + 2 * r * N + 2 * n2 * N);
             us.flops += 8.0 * J * n2 * 2 * r * N;
@@ -2444,7 +2529,7 @@ int solve_group_impl(const std::vector<hz_ctx *> &cs, const std::vector<const do
         int e = 0;
         HZ_CU(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e) {
-            HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
+            HZ_CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
             throw HzError(HZ_ETIMEOUT, "an inter-CTA exchange in the inner sweep timed out; results are invalid");
         }
         stats[i].t_total_ms = now_ms() - t0;
@@ -2480,7 +2565,7 @@ hz_ctx *make_lane(hz_ctx *c) {
     s->tot_vol = c->tot_vol, s->tot_W = c->tot_W, s->tot_F = c->tot_F, s->tot_E = c->tot_E, s->tot_S = c->tot_S;
     s->tot_K = c->tot_K, s->tot_inner = c->tot_inner, s->tot_Wi = c->tot_Wi, s->tot_P = c->tot_P;
     s->tot_V = c->tot_V, s->max_nx = c->max_nx, s->max_nz = c->max_nz, s->max_no = c->max_no;
-    s->lr_r = c->lr_r, s->tot_lr = c->tot_lr, s->tot_m = c->tot_m, s->tot_ac = c->tot_ac;
+    s->lr_r = c->lr_r, s->tot_lr = c->tot_lr, s->tot_m = c->tot_m, s->tot_ac = c->tot_ac, s->tot_lam = c->tot_lam;
     s->d_m = c->d_m, s->d_ax = c->d_ax, s->d_axh = c->d_axh, s->d_az = c->d_az, s->d_azh = c->d_azh;
     s->d_gdiag = c->d_gdiag, s->d_gcx = c->d_gcx, s->d_gcz = c->d_gcz, s->d_gD = c->d_gD;
     s->d_ginvD = c->d_ginvD, s->d_ggam = c->d_ggam, s->d_lbeta = c->d_lbeta, s->tot_z = c->tot_z;
@@ -2653,7 +2738,7 @@ template <class T2> void comp_reconstruct(hz_ctx *c, const double2 *f_dev, const
     int e = 0;
     HZ_CU(cudaMemcpy(&e, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
     if (e) {
-        HZ_CU(cudaMemset(c->d_err, 0, sizeof(int)));
+        HZ_CU(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->st));
         throw HzError(HZ_ETIMEOUT, "an inter-CTA exchange in the inner sweep timed out; results are invalid");
     }
 }
