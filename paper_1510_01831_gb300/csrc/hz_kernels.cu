@@ -7,6 +7,7 @@
 #include <cooperative_groups.h>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -785,6 +786,169 @@ __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__
     cp_async_wait<0>();
 }
 
+// FP32 cell chain for panels of at most 16 right-hand sides (the batch of the
+// 2000 x 4000 workload): the same recurrence as k_cell_chain, laid out for the
+// FMA pipes.  A thread owns 2 rows x 2 adjacent columns of each 64-row chunk, so
+// a pair of K steps costs two 16-byte loads of W (its rows, k and k+1) and two of
+// t (columns 2c, 2c+1 at k and k+1) per 32 FMAs; the W rows in the two-stage ring
+// are padded by one 16-byte unit so that the four row groups of a warp fall in
+// distinct banks.  The epilogue's operands (next source / own y, and the z
+// coupling) are loaded into registers one step ahead, in the thread's own output
+// layout, right after the epilogue that consumed the previous ones.
+constexpr int C16_CH = 64, C16_MAXCH = 3;  // chunk rows; chunks per step (nx <= 192)
+__host__ __device__ constexpr size_t c16_smem(int ldws, int max_nx) {
+    return sizeof(float2) * ((size_t)2 * C16_CH * ldws + (size_t)2 * max_nx * 16);
+}
+__global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restrict__ cells, const float2 *__restrict__ W,
+                                                         const float2 *__restrict__ cz, float2 *vol, int B, int ldws) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const CellDesc cd = cells[blockIdx.y];
+    const int nx = cd.nx, nz = cd.nz, ldw = cd.ldw;
+    const int n0 = blockIdx.x * 16;
+    if (n0 >= B) return;
+    float2 *ring = reinterpret_cast<float2 *>(smraw);  // 2 stages x 64 rows x ldws
+    float2 *tc = ring + 2 * C16_CH * ldws;             // t of the current step [nx][16]
+    float2 *tn = tc + nx * 16;                          // t of the next step
+    const int tid = threadIdx.x, cg = tid & 7, rg = tid >> 3;
+    const int nch = (nx + C16_CH - 1) / C16_CH, nsteps = 2 * nz - 1, total = nsteps * nch;
+    const float2 *Wc = W + cd.w_off;
+    const float2 *czc = cz + cd.cz_off;
+    float2 *v = vol + cd.vol_off * (long long)B;
+    const long long rs = (long long)nx * B;
+    const int units = ldw / 2;  // 16-byte units per W row
+    const float inv_units = 1.0f / (float)units;
+    auto jb_of = [&](int s) { return s < nz ? s : 2 * nz - 2 - s; };
+    auto issue = [&](int q) {
+        if (q < total) {
+            const int s = q / nch, c = q % nch;
+            const int rows = min(C16_CH, nx - c * C16_CH);
+            const float2 *src = Wc + ((long long)jb_of(s) * nx + (long long)c * C16_CH) * ldw;
+            float2 *dst = ring + (q & 1) * C16_CH * ldws;
+            for (int u = tid; u < rows * units; u += 256) {
+                const int r = __float2int_rz(((float)u + 0.5f) * inv_units), k2 = u - r * units;
+                cp_async16(dst + r * ldws + 2 * k2, src + (long long)r * ldw + 2 * k2);
+            }
+        }
+        cp_async_commit();
+    };
+    // epilogue operands of step s: the global vector (forward: g of step s+1; backward: own y)
+    // and the coupling row (forward: c_s, or c_{nz-2} on the last forward step; backward:
+    // c_{jb-1}); -1: none
+    auto grow = [&](int s) { return s < nz - 1 ? s + 1 : (s < nz ? -1 : jb_of(s)); };
+    auto crow = [&](int s) { return s < nz - 1 ? s : (s < nz ? nz - 2 : jb_of(s) - 1); };
+    float2 gr[C16_MAXCH][2][2], cr[C16_MAXCH][2];
+    auto prefetch = [&](int s, int c) {  // operands of chunk c of step s
+        if (s >= nsteps) return;
+        const int gs = grow(s), cs = crow(s);
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const int m = c * C16_CH + rg * 2 + i;
+            const bool mok = m < nx;
+            cr[c][i] = (mok && cs >= 0) ? czc[(long long)cs * nx + m] : czero<float2>();
+#pragma unroll
+            for (int t = 0; t < 2; t++) {
+                const int nn = 2 * cg + t;
+                gr[c][i][t] = (mok && gs >= 0 && n0 + nn < B) ? v[gs * rs + (long long)m * B + n0 + nn] : czero<float2>();
+            }
+        }
+    };
+    issue(0);
+    for (int e = tid; e < nx * 16; e += 256) {  // t_0 = g_0
+        const int jx = e >> 4, nn = e & 15;
+        tc[e] = (n0 + nn < B) ? v[(long long)jx * B + n0 + nn] : czero<float2>();
+    }
+#pragma unroll
+    for (int c = 0; c < C16_MAXCH; c++)
+        if (c < nch) prefetch(0, c);
+    int q = 0;
+    for (int s = 0; s < nsteps; s++) {
+        const bool fwd = s < nz;
+        const int jb = jb_of(s);
+        float2 *g = v + jb * rs;
+#pragma unroll
+        for (int c = 0; c < C16_MAXCH; c++) {
+            if (c >= nch) break;
+            cp_async_wait<0>();
+            __syncthreads();  // chunk q landed for all; chunk q-1 and the previous step's t are done
+            issue(q + 1);     // into the other stage
+            const float2 *w0 = ring + (q & 1) * C16_CH * ldws + (rg * 2) * ldws, *w1 = w0 + ldws;
+            const float2 *xr = tc + 2 * cg;
+            float2 a00 = czero<float2>(), a01 = a00, a10 = a00, a11 = a00;
+            int k = 0;
+#pragma unroll 4
+            for (; k + 1 < nx; k += 2) {
+                const Pair<float2> p0 = ld_pair(w0 + k), p1 = ld_pair(w1 + k);
+                const Pair<float2> x0 = ld_pair(xr + k * 16), x1 = ld_pair(xr + (k + 1) * 16);
+                cmac(a00, p0.a, x0.a);
+                cmac(a01, p0.a, x0.b);
+                cmac(a10, p1.a, x0.a);
+                cmac(a11, p1.a, x0.b);
+                cmac(a00, p0.b, x1.a);
+                cmac(a01, p0.b, x1.b);
+                cmac(a10, p1.b, x1.a);
+                cmac(a11, p1.b, x1.b);
+            }
+            if (k < nx) {
+                const Pair<float2> x0 = ld_pair(xr + k * 16);
+                const float2 u0 = w0[k], u1 = w1[k];
+                cmac(a00, u0, x0.a);
+                cmac(a01, u0, x0.b);
+                cmac(a10, u1, x0.a);
+                cmac(a11, u1, x0.b);
+            }
+            const float2 acc[2][2] = {{a00, a01}, {a10, a11}};
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int m = c * C16_CH + rg * 2 + i;
+                if (m >= nx) continue;
+#pragma unroll
+                for (int t = 0; t < 2; t++) {
+                    const int nn = 2 * cg + t;
+                    const bool live = n0 + nn < B;
+                    float2 out = acc[i][t], tnext;
+                    if (fwd) {
+                        if (s + 1 < nz)
+                            tnext = gr[c][i][t] - cr[c][i] * out;  // g_{j+1} - c_j y_j
+                        else
+                            tnext = (jb > 0) ? cr[c][i] * out : czero<float2>();  // first backward: c_{nz-2} x_{nz-1}
+                    } else {
+                        out = gr[c][i][t] - out;  // x_j = y_j - W_j t
+                        tnext = (jb > 0) ? cr[c][i] * out : czero<float2>();
+                    }
+                    if (!live) {
+                        out = czero<float2>();
+                        tnext = czero<float2>();
+                    }
+                    tn[m * 16 + nn] = tnext;
+                    if (live) g[(long long)m * B + n0 + nn] = out;
+                }
+            }
+            prefetch(s + 1, c);  // in flight until this chunk's epilogue of the next step
+            q++;
+        }
+        float2 *tt = tc;
+        tc = tn;
+        tn = tt;
+    }
+    cp_async_wait<0>();
+}
+
+static bool cell_chain16(const CellDesc *d_cells, int ncell, const float2 *W, const float2 *cz, float2 *vol, int B,
+                         int max_nx, cudaStream_t st) {
+    if (B > 16 || max_nx > C16_CH * C16_MAXCH) return false;
+    const int ldws = ((max_nx + 1) & ~1) + 2;
+    const size_t sm = c16_smem(ldws, max_nx);
+    if (sm > 227 * 1024) return false;
+    static size_t attr = 0;
+    if (sm > attr) {
+        HZ_CU(cudaFuncSetAttribute(k_cell_chain16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr = sm;
+    }
+    k_cell_chain16<<<dim3(1, ncell), 256, sm, st>>>(d_cells, W, cz, vol, B, ldws);
+    HZ_CU(cudaGetLastError());
+    return true;
+}
+
 template <class T2, int NT, int CH, int ST>
 static bool cell_chain_cfg(const CellDesc *d_cells, int ncell, const T2 *W, const T2 *cz, T2 *vol, int B, int max_nx,
                            cudaStream_t st) {
@@ -804,6 +968,13 @@ void launch_cell_chain(const CellDesc *d_cells, int ncell, const T2 *W, const T2
     if (ncell <= 0 || B <= 0) return;
     // widest RHS tile that fits; narrow tiles when few cells would leave SMs idle
     bool ok = false;
+    if constexpr (std::is_same<T2, float2>::value) {
+        static const bool c16 = !getenv("HZ_CELL") || strcmp(getenv("HZ_CELL"), "tiled") != 0;
+        if (c16 && B <= 16 && cell_chain16(d_cells, ncell, W, cz, vol, B, max_nx, st)) {
+            if (nl) (*nl)++;
+            return;
+        }
+    }
     if (B > 16) ok = cell_chain_cfg<T2, 32, 64, 2>(d_cells, ncell, W, cz, vol, B, max_nx, st);
     if (!ok && B > 16) ok = cell_chain_cfg<T2, 32, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
     if (!ok) ok = cell_chain_cfg<T2, 16, 32, 3>(d_cells, ncell, W, cz, vol, B, max_nx, st);
