@@ -289,24 +289,42 @@ def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_
         tdist.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stats = []  # one list of member stats per step
-    # every member stream has finished when a step returns, so events on the first stream bracket all of them
-    with Clocks(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+
+    def region(kernel_events):
+        # every member stream has finished when a step returns, so events on the first stream
+        # bracket all of them
+        for c in ctxs:
+            c.hz_set_time_kernels(kernel_events)
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+        torch.cuda.synchronize()
+        sts = []  # one list of member stats per step
         ev0.record(streams[0])
         for _ in range(steps):
-            stats.append([st.as_dict() for st in step(f_dev, u_dev)])
+            sts.append([st.as_dict() for st in step(f_dev, u_dev)])
         ev1.record(streams[0])
         torch.cuda.synchronize()
-    if world > 1:
-        import torch.distributed as tdist
-        tdist.barrier()
-    ms = reduce_max(ev0.elapsed_time(ev1) / steps, world)
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.barrier()
+        return reduce_max(ev0.elapsed_time(ev1) / steps, world), sts
+
+    # the timed region runs without per-launch events (consecutive launches may overlap their
+    # prologues); the same steps are then run again with an event pair around every launch,
+    # which gives the per-class kernel times of the roofline
+    with Clocks(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        ms, stats = region(False)
+        ms_ev, stats_ev = region(True)
+    for c in ctxs:
+        c.hz_set_time_kernels(False)
     mdof = sum(pb.n_x * pb.n_z for pb in pbs) / 1e6
     flat = [m for st in stats for m in st]
-    kt_ms = np.sum([s["kt_ms"] for s in flat], axis=0)
-    kt_n = np.sum([s["kt_launches"] for s in flat], axis=0)
-    kt_b = np.sum([s["kt_bytes"] for s in flat], axis=0)
-    kt_f = np.sum([s["kt_flops"] for s in flat], axis=0)
+    flat_ev = [m for st in stats_ev for m in st]
+    kt_ms = np.sum([s["kt_ms"] for s in flat_ev], axis=0)
+    kt_n = np.sum([s["kt_launches"] for s in flat_ev], axis=0)
+    kt_b = np.sum([s["kt_bytes"] for s in flat_ev], axis=0)
+    kt_f = np.sum([s["kt_flops"] for s in flat_ev], axis=0)
     last = stats[-1]
     solve = [{"iterations": m["iterations"], "refinements": m["refinements"], "resid": m["resid"],
               "gmres_resid": m["gmres_resid"], "inner_iterations": m["inner_iterations"],
@@ -320,7 +338,8 @@ def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_
            "C": pbs[0].C, "frequencies": len(pbs),
            "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
            "solve": solve[0] if len(solve) == 1 else solve,
-           "roofline": roofline(kt_ms, kt_n, kt_b, kt_f, ms, steps, mixed, tc > 0, workload),
+           "ms_per_step_with_kernel_events": round(ms_ev, 3),
+           "roofline": roofline(kt_ms, kt_n, kt_b, kt_f, ms_ev, steps, mixed, tc > 0, workload),
            "clocks": clk.summary()}
     if e2e:
         # end-to-end through the same entry point with pinned host buffers: the copies of the
@@ -385,7 +404,10 @@ def run_ours(args, rank, world):
                    "l2": "inputs and operators larger than L2 (no flush needed)", "parallelism": "replicas"},
         "gpu_launches": main_["gpu_launches"],
         "solve": main_["solve"],
-        "roofline": main_["roofline"],
+        "roofline": dict(main_["roofline"], events_region={
+            "ms_per_step": main_["ms_per_step_with_kernel_events"],
+            "what": "the same steps run again right after the timed region, with an event pair around every "
+                    "launch on the solver's stream; kernel times and shares come from this run"}),
         "e2e": main_.get("e2e"),
         "clocks": main_["clocks"],
     }

@@ -338,6 +338,12 @@ hz_status hz_check_timeout(hz_ctx *ctx);
 /* Switch the pointer mode of later calls (same meaning as opts.device_ptrs). */
 hz_status hz_set_device_ptrs(hz_ctx *ctx, int device_ptrs);
 
+/* Switch per-kernel-class CUDA-event timing of later calls (same meaning as
+ * opts.time_kernels: 1 records events around every launch of the online path
+ * and fills hz_stats.kt_*; 0 records none, so that consecutive launches may
+ * overlap their prologues).  HZ_EINVAL if ctx is NULL. */
+hz_status hz_set_time_kernels(hz_ctx *ctx, int time_kernels);
+
 /* Bytes of device memory held by the context (factors + workspaces). */
 long long hz_device_bytes(const hz_ctx *ctx);
 

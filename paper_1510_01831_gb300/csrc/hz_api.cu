@@ -790,6 +790,12 @@ hz_status hz_set_device_ptrs(hz_ctx *c, int device_ptrs) {
     return HZ_OK;
 }
 
+hz_status hz_set_time_kernels(hz_ctx *c, int time_kernels) {
+    if (!c) return fail(nullptr, HZ_EINVAL, "ctx is NULL");
+    c->opts.time_kernels = time_kernels ? 1 : 0;
+    return HZ_OK;
+}
+
 long long hz_device_bytes(const hz_ctx *c) {
     if (!c) return 0;
     long long b = c->dev_bytes;

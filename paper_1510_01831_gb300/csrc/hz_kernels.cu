@@ -396,6 +396,9 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
     extern __shared__ __align__(16) unsigned char nsm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2 *wb = reinterpret_cast<float2 *>(nsm) + warp * NS * STG;
+    // programmatic dependent launch: the next kernel may start its own prologue now; this
+    // one reads only constant data (descriptors, operators) before griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     static_assert(sizeof(GemmProb<float2>) % 8 == 0, "problem descriptor copied as 8-byte words");
     for (int w = tid; w < (int)(sizeof(GemmProb<float2>) / 8); w += NW_WPC * 32)
         reinterpret_cast<long long *>(&P)[w] = reinterpret_cast<const long long *>(probs + blockIdx.y)[w];
@@ -408,7 +411,7 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
     const int bps = (nbt + S - 1) / S, b0 = min(nbt, sp * bps), b1 = min(nbt, b0 + bps);
     const int nmine = b1 - b0 > warp ? (b1 - b0 - warp + NW_WPC - 1) / NW_WPC : 0;
     const int ak = lane & 15, ah = lane >> 4;  // A copies: column ak of rows 2 i + ah
-    auto issue = [&](int t) {
+    auto issue = [&](int t, int parts) {  // parts: 1 = A block, 2 = X block
         float2 *As = wb + (t % NS) * STG, *Xs = As + ASZ;
         const int b = b0 + warp + t * NW_WPC;
         const bool p2 = b >= nb1;
@@ -420,12 +423,15 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
         const float2 *const *Xp = p2 ? P.X2 : P.X;
         const int gk = k0 + ak;
         const bool kin = gk < K;
+        if (parts & 1) {
 #pragma unroll
-        for (int i = 0; i < 16; i++) {
-            const int r = 2 * i + ah, gm = m0 + r;
-            const bool ok = kin && gm < M;
-            gemm_cp<8>(As + r * (NW_KB + 1) + ak, ok ? A + (long long)gm * lda + gk : A, ok ? 8u : 0u);
+            for (int i = 0; i < 16; i++) {
+                const int r = 2 * i + ah, gm = m0 + r;
+                const bool ok = kin && gm < M;
+                gemm_cp<8>(As + r * (NW_KB + 1) + ak, ok ? A + (long long)gm * lda + gk : A, ok ? 8u : 0u);
+            }
         }
+        if (!(parts & 2)) return;
         const bool one = xseg >= K;  // a single segment: no division
 #pragma unroll
         for (int q = 0; q < NB / 2; q++) {
@@ -442,15 +448,21 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
     float2 acc[NB];
 #pragma unroll
     for (int n = 0; n < NB; n++) acc[n] = czero<float2>();
+    // prologue: the operator blocks of the first NS - 1 steps, then (once the kernels this
+    // one depends on are complete and visible) their right-hand-side blocks
 #pragma unroll
-    for (int t = 0; t < NS - 1; t++) {  // prologue: the first NS - 1 blocks in flight
-        if (t < nmine) issue(t);
+    for (int t = 0; t < NS - 1; t++)
+        if (t < nmine) issue(t, 1);
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < NS - 1; t++) {
+        if (t < nmine) issue(t, 2);
         gemm_cp_commit();
     }
     for (int t = 0; t < nmine; t++) {
         gemm_cp_wait<NS - 2>();  // this lane's copies of block t have landed
         __syncwarp();            // every lane's have; every lane is done with block t - 1
-        if (t + NS - 1 < nmine) issue(t + NS - 1);  // into the stage of block t - 1
+        if (t + NS - 1 < nmine) issue(t + NS - 1, 3);  // into the stage of block t - 1
         gemm_cp_commit();
         const float2 *As = wb + (t % NS) * STG + lane * (NW_KB + 1), *Xs = wb + (t % NS) * STG + ASZ;
 #pragma unroll 4
@@ -522,7 +534,18 @@ static void launch_narrow_cfg(const GemmProb<float2> *d_probs, int nprob, int ma
         HZ_CU(cudaFuncSetAttribute(k_gemm_narrow<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = true;
     }
-    k_gemm_narrow<NB><<<dim3(max_tiles * split, nprob), NW_WPC * 32, sm, st>>>(d_probs, split, ws, cnt, max_tiles);
+    static const bool pdl = !getenv("HZ_PDL") || strcmp(getenv("HZ_PDL"), "0") != 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(max_tiles * split, nprob);
+    cfg.blockDim = dim3(NW_WPC * 32);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    HZ_CU(cudaLaunchKernelEx(&cfg, k_gemm_narrow<NB>, d_probs, split, ws, cnt, max_tiles));
 }
 
 void launch_gemm_narrow(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int nmax, int split, float2 *ws,

@@ -30,7 +30,7 @@ STATUS_NAMES = ["HZ_OK", "HZ_EINVAL", "HZ_ENOMEM", "HZ_ECUDA", "HZ_ESTATE", "HZ_
 # every entry point declared in include/hz.h
 EXPORTS = ["hz_default_opts", "hz_setup", "hz_factor", "hz_update_model", "hz_solve", "hz_solve_group", "hz_gradient", "hz_adjoint", "hz_traces", "hz_reconstruct", "hz_cell_solve",
            "hz_layer_green", "hz_apply_M", "hz_precond", "hz_residual", "hz_residual_noalloc",
-           "hz_check_timeout", "hz_set_device_ptrs", "hz_device_bytes", "hz_destroy", "hz_last_error"]
+           "hz_check_timeout", "hz_set_device_ptrs", "hz_set_time_kernels", "hz_device_bytes", "hz_destroy", "hz_last_error"]
 
 
 class HzError(RuntimeError):
@@ -108,6 +108,8 @@ def load() -> ctypes.CDLL:
             L.hz_check_timeout.restype = ctypes.c_int
             L.hz_set_device_ptrs.argtypes = [vp, i]
             L.hz_set_device_ptrs.restype = ctypes.c_int
+            L.hz_set_time_kernels.argtypes = [vp, i]
+            L.hz_set_time_kernels.restype = ctypes.c_int
             L.hz_device_bytes.argtypes = [vp]
             L.hz_device_bytes.restype = ctypes.c_longlong
             L.hz_destroy.argtypes = [vp]
@@ -349,6 +351,9 @@ class Context:
     def hz_set_device_ptrs(self, device: bool):
         _check(load().hz_set_device_ptrs(self._ctx, 1 if device else 0), self._ctx)
         self.device = bool(device)
+
+    def hz_set_time_kernels(self, on: bool):
+        _check(load().hz_set_time_kernels(self._ctx, 1 if on else 0), self._ctx)
 
     def hz_device_bytes(self) -> int:
         return int(load().hz_device_bytes(self._ctx))
