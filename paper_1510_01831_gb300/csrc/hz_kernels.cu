@@ -811,9 +811,9 @@ __global__ void __launch_bounds__(256) k_cell_chain(const CellDesc *__restrict__
 
 // FP32 cell chain for panels of at most 16 right-hand sides (the batch of the
 // 2000 x 4000 workload): the same recurrence as k_cell_chain, laid out for the
-// FMA pipes.  A thread owns 2 rows x 2 adjacent columns of each 64-row chunk, so
-// a pair of K steps costs two 16-byte loads of W (its rows, k and k+1) and two of
-// t (columns 2c, 2c+1 at k and k+1) per 32 FMAs; the W rows in the two-stage ring
+// FMA pipes.  A thread owns TM rows x 2 adjacent columns of each 64-row chunk, so
+// a pair of K steps costs TM 16-byte loads of W (its rows, k and k+1) and two of
+// t (columns 2c, 2c+1 at k and k+1) per 16 TM FMAs; the W rows in the two-stage ring
 // are padded by one 16-byte unit so that the four row groups of a warp fall in
 // distinct banks.  The epilogue's operands (next source / own y, and the z
 // coupling) are loaded into registers one step ahead, in the thread's own output
@@ -822,8 +822,12 @@ constexpr int C16_CH = 64, C16_MAXCH = 3;  // chunk rows; chunks per step (nx <=
 __host__ __device__ constexpr size_t c16_smem(int ldws, int max_nx) {
     return sizeof(float2) * ((size_t)2 * C16_CH * ldws + (size_t)2 * max_nx * 16);
 }
-__global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restrict__ cells, const float2 *__restrict__ W,
-                                                         const float2 *__restrict__ cz, float2 *vol, int B, int ldws) {
+template <int TM>
+__global__ void __launch_bounds__(512 / TM, 1) k_cell_chain16(const CellDesc *__restrict__ cells,
+                                                              const float2 *__restrict__ W,
+                                                              const float2 *__restrict__ cz, float2 *vol, int B,
+                                                              int ldws) {
+    constexpr int NTH = 512 / TM;  // threads: 8 column pairs x (64 / TM) row groups
     extern __shared__ __align__(16) unsigned char smraw[];
     const CellDesc cd = cells[blockIdx.y];
     const int nx = cd.nx, nz = cd.nz, ldw = cd.ldw;
@@ -847,7 +851,7 @@ __global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restr
             const int rows = min(C16_CH, nx - c * C16_CH);
             const float2 *src = Wc + ((long long)jb_of(s) * nx + (long long)c * C16_CH) * ldw;
             float2 *dst = ring + (q & 1) * C16_CH * ldws;
-            for (int u = tid; u < rows * units; u += 256) {
+            for (int u = tid; u < rows * units; u += NTH) {
                 const int r = __float2int_rz(((float)u + 0.5f) * inv_units), k2 = u - r * units;
                 cp_async16(dst + r * ldws + 2 * k2, src + (long long)r * ldw + 2 * k2);
             }
@@ -859,13 +863,13 @@ __global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restr
     // c_{jb-1}); -1: none
     auto grow = [&](int s) { return s < nz - 1 ? s + 1 : (s < nz ? -1 : jb_of(s)); };
     auto crow = [&](int s) { return s < nz - 1 ? s : (s < nz ? nz - 2 : jb_of(s) - 1); };
-    float2 gr[C16_MAXCH][2][2], cr[C16_MAXCH][2];
+    float2 gr[C16_MAXCH][TM][2], cr[C16_MAXCH][TM];
     auto prefetch = [&](int s, int c) {  // operands of chunk c of step s
         if (s >= nsteps) return;
         const int gs = grow(s), cs = crow(s);
 #pragma unroll
-        for (int i = 0; i < 2; i++) {
-            const int m = c * C16_CH + rg * 2 + i;
+        for (int i = 0; i < TM; i++) {
+            const int m = c * C16_CH + rg * TM + i;
             const bool mok = m < nx;
             cr[c][i] = (mok && cs >= 0) ? czc[(long long)cs * nx + m] : czero<float2>();
 #pragma unroll
@@ -876,7 +880,7 @@ __global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restr
         }
     };
     issue(0);
-    for (int e = tid; e < nx * 16; e += 256) {  // t_0 = g_0
+    for (int e = tid; e < nx * 16; e += NTH) {  // t_0 = g_0
         const int jx = e >> 4, nn = e & 15;
         tc[e] = (n0 + nn < B) ? v[(long long)jx * B + n0 + nn] : czero<float2>();
     }
@@ -894,35 +898,36 @@ __global__ void __launch_bounds__(256, 1) k_cell_chain16(const CellDesc *__restr
             cp_async_wait<0>();
             __syncthreads();  // chunk q landed for all; chunk q-1 and the previous step's t are done
             issue(q + 1);     // into the other stage
-            const float2 *w0 = ring + (q & 1) * C16_CH * ldws + (rg * 2) * ldws, *w1 = w0 + ldws;
+            const float2 *w0 = ring + (q & 1) * C16_CH * ldws + (rg * TM) * ldws;
             const float2 *xr = tc + 2 * cg;
-            float2 a00 = czero<float2>(), a01 = a00, a10 = a00, a11 = a00;
+            float2 acc[TM][2];
+#pragma unroll
+            for (int i = 0; i < TM; i++) acc[i][0] = acc[i][1] = czero<float2>();
             int k = 0;
 #pragma unroll 4
             for (; k + 1 < nx; k += 2) {
-                const Pair<float2> p0 = ld_pair(w0 + k), p1 = ld_pair(w1 + k);
                 const Pair<float2> x0 = ld_pair(xr + k * 16), x1 = ld_pair(xr + (k + 1) * 16);
-                cmac(a00, p0.a, x0.a);
-                cmac(a01, p0.a, x0.b);
-                cmac(a10, p1.a, x0.a);
-                cmac(a11, p1.a, x0.b);
-                cmac(a00, p0.b, x1.a);
-                cmac(a01, p0.b, x1.b);
-                cmac(a10, p1.b, x1.a);
-                cmac(a11, p1.b, x1.b);
+#pragma unroll
+                for (int i = 0; i < TM; i++) {
+                    const Pair<float2> p = ld_pair(w0 + i * ldws + k);
+                    cmac(acc[i][0], p.a, x0.a);
+                    cmac(acc[i][1], p.a, x0.b);
+                    cmac(acc[i][0], p.b, x1.a);
+                    cmac(acc[i][1], p.b, x1.b);
+                }
             }
             if (k < nx) {
                 const Pair<float2> x0 = ld_pair(xr + k * 16);
-                const float2 u0 = w0[k], u1 = w1[k];
-                cmac(a00, u0, x0.a);
-                cmac(a01, u0, x0.b);
-                cmac(a10, u1, x0.a);
-                cmac(a11, u1, x0.b);
-            }
-            const float2 acc[2][2] = {{a00, a01}, {a10, a11}};
 #pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int m = c * C16_CH + rg * 2 + i;
+                for (int i = 0; i < TM; i++) {
+                    const float2 w = w0[i * ldws + k];
+                    cmac(acc[i][0], w, x0.a);
+                    cmac(acc[i][1], w, x0.b);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < TM; i++) {
+                const int m = c * C16_CH + rg * TM + i;
                 if (m >= nx) continue;
 #pragma unroll
                 for (int t = 0; t < 2; t++) {
@@ -962,12 +967,14 @@ static bool cell_chain16(const CellDesc *d_cells, int ncell, const float2 *W, co
     const int ldws = ((max_nx + 1) & ~1) + 2;
     const size_t sm = c16_smem(ldws, max_nx);
     if (sm > 227 * 1024) return false;
+    // two rows per thread (256 threads); one row per thread with 512 threads measured 33 %
+    // slower on the 2000 x 4000 workload (more shared-memory loads per FMA)
     static size_t attr = 0;
     if (sm > attr) {
-        HZ_CU(cudaFuncSetAttribute(k_cell_chain16, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HZ_CU(cudaFuncSetAttribute(k_cell_chain16<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr = sm;
     }
-    k_cell_chain16<<<dim3(1, ncell), 256, sm, st>>>(d_cells, W, cz, vol, B, ldws);
+    k_cell_chain16<2><<<dim3(1, ncell), 256, sm, st>>>(d_cells, W, cz, vol, B, ldws);
     HZ_CU(cudaGetLastError());
     return true;
 }

@@ -152,6 +152,52 @@ __global__ void k_residual(const double2 *__restrict__ u, const double2 *__restr
     }
 }
 
+// The same residual and norms for batches that divide 256 (B = 2^lgB): a CTA takes R
+// whole grid rows; the elements of a row, point-major with the right-hand side
+// innermost, are spread over the CTA's threads so that every load and store is
+// coalesced and no division by the row length is needed.  A thread always holds
+// the same right-hand side (b = tid mod B), and its partial sum is added to those
+// of the other threads of that right-hand side in thread order.
+__global__ void __launch_bounds__(256) k_residual_rows(const double2 *__restrict__ u, const double2 *__restrict__ fs,
+                                                       double2 *r, const double2 *__restrict__ dg,
+                                                       const double2 *__restrict__ cx, const double2 *__restrict__ cz,
+                                                       const double2 *__restrict__ Dg, int NX, int NZ, int lgB, int R,
+                                                       double *part, int mode) {
+    const int tid = threadIdx.x, B = 1 << lgB, rowE = NX << lgB;
+    const int z0 = blockIdx.x * R, z1 = min(NZ, z0 + R);
+    const long long rs = (long long)rowE;
+    double acc = 0.0;
+    for (int iz = z0; iz < z1; iz++) {
+        const long long gb = (long long)iz * NX, eb = gb << lgB;
+#pragma unroll 2
+        for (int e = tid; e < rowE; e += 256) {
+            const int ix = e >> lgB;
+            const long long g = gb + ix, i = eb + e;
+            double2 v;
+            if (mode == 0) {
+                double2 Hu = dg[g] * u[i];
+                if (ix > 0) Hu = Hu + cx[g - 1] * u[i - B];
+                if (ix < NX - 1) Hu = Hu + cx[g] * u[i + B];
+                if (iz > 0) Hu = Hu + cz[g - NX] * u[i - rs];
+                if (iz < NZ - 1) Hu = Hu + cz[g] * u[i + rs];
+                v = fs[i] - Hu;
+                r[i] = v;
+            } else {
+                v = fs[i];
+            }
+            acc += cabs2(Dg[g] * v);
+        }
+    }
+    __shared__ double red[256];
+    red[tid] = acc;
+    __syncthreads();
+    if (tid < B) {
+        double sum = 0;
+        for (int t = tid; t < 256; t += B) sum += red[t];
+        part[(long long)blockIdx.x * B + tid] = sum;
+    }
+}
+
 __global__ void k_global_D(const double2 *__restrict__ ax, const double2 *__restrict__ az, int NX, long long N,
                            double2 *D, double2 *invD) {
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
@@ -2319,18 +2365,34 @@ template <class T2> static void recon_enqueue(hz_ctx *c, Work<T2> &W) {
     c->nl++;
 }
 
-// point chunks of the residual (its FP64 arithmetic, not the chunking, bounds it)
+// point chunks of the residual (general batch widths)
 static int residual_chunks(int) { return 256; }
 
-// per-RHS ||alpha r||^2 partial sums -> host buffer (mode 0 writes r = fs - H u);
-// enqueued only: valid after the stream synchronises
-static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
-                             int mode, double *part) {
+// launch the residual kernel; returns the number of per-RHS partial sums written to part
+// (part holds at least 4096 B + B doubles)
+static int residual_launch(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, int mode, double *part) {
+    if (B <= 256 && (256 % B) == 0) {
+        int lgB = 0;
+        while ((1 << lgB) < B) lgB++;
+        const int R = std::max(1, (c->NZ + 1023) / 1024), nchunk = (c->NZ + R - 1) / R;
+        k_residual_rows<<<nchunk, 256, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ,
+                                                   lgB, R, part, mode);
+        HZ_CU(cudaGetLastError());
+        return nchunk;
+    }
     const int nchunk = residual_chunks(B);
     dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
     k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ, B, part,
                                      nchunk, mode);
     HZ_CU(cudaGetLastError());
+    return nchunk;
+}
+
+// per-RHS ||alpha r||^2 partial sums -> host buffer (mode 0 writes r = fs - H u);
+// enqueued only: valid after the stream synchronises
+static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
+                             int mode, double *part) {
+    const int nchunk = residual_launch(c, u, fs, r, B, mode, part);
     double *fin = part + (long long)nchunk * B;
     k_reduce_parts<<<(B + 255) / 256, 256, 0, c->st>>>(part, nchunk, B, fin);
     HZ_CU(cudaGetLastError());
@@ -2340,11 +2402,7 @@ static void residual_enqueue(hz_ctx *c, const double2 *u, const double2 *fs, dou
 
 static void residual_norms(hz_ctx *c, const double2 *u, const double2 *fs, double2 *r, int B, double *out_host,
                            int mode, double *part) {
-    const int nchunk = residual_chunks(B);
-    dim3 g(nchunk, (B + 31) / 32), blk(32, 8);
-    k_residual<<<g, blk, 0, c->st>>>(u, fs, r, c->d_gdiag, c->d_gcx, c->d_gcz, c->d_gD, c->NX, c->NZ, B, part,
-                                     nchunk, mode);
-    HZ_CU(cudaGetLastError());
+    const int nchunk = residual_launch(c, u, fs, r, B, mode, part);
     double *fin = part + (long long)nchunk * B;
     k_reduce_parts<<<(B + 255) / 256, 256, 0, c->st>>>(part, nchunk, B, fin);
     HZ_CU(cudaGetLastError());
