@@ -554,7 +554,10 @@ void launch_gemm_narrow(const GemmProb<float2> *d_probs, int nprob, int max_tile
     if (nmax > NW_NB) throw HzError(HZ_EINVAL, "narrow GEMM: too many columns");
     if (split < 1 || split > 8 || (split > 1 && (!ws || !cnt || (long long)nprob * max_tiles * split > NW_WS_SLOTS)))
         throw HzError(HZ_EINVAL, "narrow GEMM: bad split-K workspace");
-    launch_narrow_cfg<NW_NB>(d_probs, nprob, max_tiles, split, ws, cnt, st);
+    if (nmax <= 8)  // e.g. a batch of 16 solved as two groups of 8 on two streams
+        launch_narrow_cfg<8>(d_probs, nprob, max_tiles, split, ws, cnt, st);
+    else
+        launch_narrow_cfg<NW_NB>(d_probs, nprob, max_tiles, split, ws, cnt, st);
     HZ_CU(cudaGetLastError());
     if (nl) (*nl)++;
 }
