@@ -98,6 +98,14 @@ struct CellDesc {
     long long S_off;     // S: (4 no) x (4 no)
     long long K_off;     // K (offline only): (2 nz) x (4 nz)
     long long tc_off;    // split TF32 copy of the W blocks for the tensor-core cell solve (floats)
+    // compressed-block LU only: the sweep step of the layer as three products whose
+    // operators are composed offline.  The inputs of cell c's composite are the owned
+    // columns of cells c-1, c, c+1 (a contiguous range of Lt columns of each trace row,
+    // cell c's own at offset cl); P2 (4 no x 4 Lt) = E W F + S, P3 (4 no x 4r) = E UX on
+    // [ts of interface c-1; ts of interface c]; P1 (2r x 4 (no + no of cell c+1)) =
+    // STW F of interface c (cells c, c+1; none for the last cell)
+    long long P2_off, P3_off, P1_off;
+    int cl, Lt;
 };
 
 // One layer: its inner SIE over the C-1 cell interfaces.

@@ -24,6 +24,8 @@ template <class T2> struct Ops {
     // the r-vector recursion of a layer as one matrix: ts = LAM ac (ac, ts in their
     // [C-1][2r] layout), applied as one product where a single layer is solved
     T2 *LAM = nullptr;
+    // the sweep-step composites of each cell (offsets in CellDesc)
+    T2 *CP2 = nullptr, *CP3 = nullptr, *CP1 = nullptr;
 };
 
 // Problem lists of batched GEMMs, kept on the device (built once per workspace).
@@ -89,6 +91,9 @@ template <class T2> struct Work {
     std::vector<int> uoff;
     // compressed-block LU of one layer at a time: ts = LAM ac, problem l of layer l
     ProbList<T2> lamB, lam2B;
+    // compressed-block LU sweep steps through the composites: [out += P2 in, ac = P1 in]
+    // then (after ts = LAM ac) out += P3 ts, per step of the downward / upward sweeps
+    std::vector<ProbList<T2>> cA_down, cC_down, cA_up, cC_up;
     std::vector<double> hbytes, hflops;  // per layer (B wide)
     std::vector<long long> htiles, utiles;  // 32-row tiles per layer of the h_j and x_j lists
 };
@@ -124,7 +129,7 @@ struct hz_ctx {
     long long tot_vol = 0, tot_W = 0, tot_F = 0, tot_E = 0, tot_S = 0, tot_K = 0;
     long long tot_inner = 0, tot_Wi = 0, tot_P = 0, tot_V = 0;
     int lr_r = 0;  // compressed-block LU rank (0: dense inner factors)
-    long long tot_lr = 0, tot_m = 0, tot_ac = 0, tot_lam = 0;
+    long long tot_lr = 0, tot_m = 0, tot_ac = 0, tot_lam = 0, tot_cp2 = 0, tot_cp3 = 0, tot_cp1 = 0;
     int max_nx = 0, max_nz = 0, max_no = 0;
     // global medium and PML profiles (FP64)
     std::vector<double> h_m;  // host copy of the medium (local model updates compare against it)

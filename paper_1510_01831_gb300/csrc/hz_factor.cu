@@ -797,6 +797,159 @@ static void compress_inner(hz_ctx *c, const std::vector<int> &lays, std::vector<
 }
 
 
+// P2 += S of each listed cell: S (4 no x 4 no, columns [q][no]) into the cell's own
+// columns of its composite (columns [q][Lt], own columns at cl)
+__global__ void k_add_s(const CellDesc *__restrict__ cells, const double2 *__restrict__ S, double2 *P2) {
+    const CellDesc cd = cells[blockIdx.y];
+    const int no = cd.no, w = 4 * no;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < w * w; e += gridDim.x * blockDim.x) {
+        const int row = e / w, col = e % w, q = col / no, i = col % no;
+        double2 &d = P2[cd.P2_off + (long long)row * 4 * cd.Lt + (long long)q * cd.Lt + cd.cl + i];
+        d = d + S[cd.S_off + e];
+    }
+}
+
+// The sweep step of a layer with the compressed-block LU, out += E x + S in with
+// x_j = W_j g_j + UX_j ts_j, g = F in and ts = LAM (STW g), regrouped as three
+// products: [out += P2 in, ac = P1 in] -> ts = LAM ac -> out += P3 ts, with the
+// per-cell composites P2 = E W F + S, P1 = STW F and P3 = E UX formed here in FP64
+// (layout in CellDesc).  The first call fixes their offsets; later calls (local
+// updates) rewrite the listed layers' blocks in place.
+static void compose_sweep(hz_ctx *c, const std::vector<int> &lays, const double2 *F, const double2 *E,
+                          const double2 *S, const double2 *Wi, const double2 *STW, const double2 *UX, double2 *&P2,
+                          double2 *&P3, double2 *&P1, bool first) {
+    const int C = c->C, J = C - 1, r = c->lr_r;
+    if (r <= 0 || J < 1) return;
+    if (first) {
+        long long o2 = 0, o3 = 0, o1 = 0;
+        for (const LayerDesc &ld : c->layers)
+            for (int cc = 0; cc < C; cc++) {
+                CellDesc &cd = c->cells[ld.cell0 + cc];
+                const int nol = cc > 0 ? c->cells[ld.cell0 + cc - 1].no : 0;
+                const int nor = cc < C - 1 ? c->cells[ld.cell0 + cc + 1].no : 0;
+                if (cc > 0) {  // owned ranges of neighbouring cells are adjacent
+                    const CellDesc &pv = c->cells[ld.cell0 + cc - 1];
+                    if (pv.t + pv.own_lo + pv.no != cd.t + cd.own_lo)
+                        throw HzError(HZ_EINVAL, "sweep composites: owned column ranges are not adjacent");
+                }
+                cd.cl = nol;
+                cd.Lt = nol + cd.no + nor;
+                cd.P2_off = o2;
+                o2 += 4LL * cd.no * 4 * cd.Lt;
+                cd.P3_off = o3;
+                o3 += 4LL * cd.no * 4 * r;
+                cd.P1_off = o1;
+                if (cc < C - 1) o1 += 2LL * r * 4 * (cd.no + nor);
+            }
+        c->tot_cp2 = o2;
+        c->tot_cp3 = o3;
+        c->tot_cp1 = o1;
+        HZ_CU(cudaMemcpyAsync(c->d_cells, c->cells.data(), sizeof(CellDesc) * c->cells.size(),
+                              cudaMemcpyHostToDevice, c->st));
+    }
+    if (!P2) P2 = alloc_n<double2>(c, c->tot_cp2);
+    if (!P3) P3 = alloc_n<double2>(c, c->tot_cp3);
+    if (!P1) P1 = alloc_n<double2>(c, std::max(c->tot_cp1, 1LL));
+    // the listed layers' cells, their WF_j temporaries and zeroed composite blocks
+    std::vector<CellDesc> cl;
+    std::vector<long long> wfo;  // per listed interface: offset of WF_j in the temporary
+    long long wft = 0;
+    for (int l : lays) {
+        const LayerDesc &ld = c->layers[l];
+        for (int cc = 0; cc < C; cc++) {
+            const CellDesc &cd = c->cells[ld.cell0 + cc];
+            cl.push_back(cd);
+            HZ_CU(cudaMemsetAsync(P2 + cd.P2_off, 0, sizeof(double2) * 16LL * cd.no * cd.Lt, c->st));
+            HZ_CU(cudaMemsetAsync(P3 + cd.P3_off, 0, sizeof(double2) * 16LL * cd.no * r, c->st));
+            if (cc < C - 1) {
+                const CellDesc &cn = c->cells[ld.cell0 + cc + 1];
+                wfo.push_back(wft);
+                wft += 2LL * ld.nz * 4 * (cd.no + cn.no);
+            }
+        }
+    }
+    double2 *WF = alloc_n<double2>(c, std::max(wft, 1LL));
+    // WF_j = [W_j(:, 0:nz) F_j^(1) | W_j(:, nz:2nz) F_{j+1}^(0)] (2nz x 4 (no_j + no_{j+1}));
+    // P1_j = the same with STW_j, columns regrouped [q][no_j + no_{j+1}]
+    std::vector<GemmProb<double2>> v1, vl, vr;
+    int iw = 0;
+    for (int l : lays) {
+        const LayerDesc &ld = c->layers[l];
+        const int nz = ld.nz, n2 = 2 * nz;
+        for (int j = 0; j < J; j++, iw++) {
+            const CellDesc &ca = c->cells[ld.cell0 + j], &cb = c->cells[ld.cell0 + j + 1];
+            const int L2 = ca.no + cb.no, lw = 4 * L2;
+            double2 *wf = WF + wfo[iw];
+            const double2 *Wj = Wi + ld.W_off + (long long)j * n2 * n2;
+            const double2 *Fa = F + ca.F_off + (long long)nz * 4 * ca.no;  // F_j^(1): rows nz..2nz
+            const double2 *Fb = F + cb.F_off;                              // F_{j+1}^(0)
+            v1.push_back(prob64(Wj, n2, n2, nz, 4 * ca.no, Fa, 4LL * ca.no, wf, lw));
+            v1.push_back(prob64(Wj + nz, n2, n2, nz, 4 * cb.no, Fb, 4LL * cb.no, wf + 4 * ca.no, lw));
+            const double2 *Sj = STW + ld.lr_off + (long long)j * 2 * r * n2;
+            double2 *p1 = P1 + ca.P1_off;
+            for (int q = 0; q < 4; q++) {
+                v1.push_back(prob64(Sj, n2, 2 * r, nz, ca.no, Fa + (long long)q * ca.no, 4LL * ca.no,
+                                    p1 + (long long)q * L2, lw));
+                v1.push_back(prob64(Sj + nz, n2, 2 * r, nz, cb.no, Fb + (long long)q * cb.no, 4LL * cb.no,
+                                    p1 + (long long)q * L2 + ca.no, lw));
+            }
+        }
+    }
+    run_list64(c, v1);
+    // P2_c = E_c(:, 0:2nz) WF_{c-1} + E_c(:, 2nz:4nz) WF_c (+ S_c below), columns regrouped;
+    // P3_c = [E_c(:, 0:2nz) UX_{c-1} | E_c(:, 2nz:4nz) UX_c]
+    iw = 0;
+    for (int l : lays) {
+        const LayerDesc &ld = c->layers[l];
+        const int nz = ld.nz, n2 = 2 * nz;
+        for (int cc = 0; cc < C; cc++) {
+            const CellDesc &cd = c->cells[ld.cell0 + cc];
+            const double2 *El = E + cd.E_off, *Er = El + n2;
+            const long long ldp = 4LL * cd.Lt;
+            double2 *p2 = P2 + cd.P2_off, *p3 = P3 + cd.P3_off;
+            if (cc > 0) {  // interface cc-1: cells cc-1 (range offset 0) and cc (offset cl)
+                const CellDesc &cp = c->cells[ld.cell0 + cc - 1];
+                const double2 *wf = WF + wfo[iw + cc - 1];
+                const long long lw = 4LL * (cp.no + cd.no);
+                for (int q = 0; q < 4; q++) {
+                    vl.push_back(prob64(El, 2LL * n2, 4 * cd.no, n2, cp.no, wf + (long long)q * cp.no, lw,
+                                        p2 + (long long)q * cd.Lt, ldp));
+                    vl.push_back(prob64(El, 2LL * n2, 4 * cd.no, n2, cd.no, wf + 4 * cp.no + (long long)q * cd.no, lw,
+                                        p2 + (long long)q * cd.Lt + cd.cl, ldp));
+                }
+                vl.push_back(prob64(El, 2LL * n2, 4 * cd.no, n2, 2 * r,
+                                    UX + ld.lr_off + (long long)(cc - 1) * n2 * 2 * r, 2 * r, p3, 4 * r));
+            }
+            if (cc < C - 1) {  // interface cc: cells cc (offset cl) and cc+1 (offset cl + no)
+                const CellDesc &cn = c->cells[ld.cell0 + cc + 1];
+                const double2 *wf = WF + wfo[iw + cc];
+                const long long lw = 4LL * (cd.no + cn.no);
+                for (int q = 0; q < 4; q++) {
+                    vr.push_back(prob64(Er, 2LL * n2, 4 * cd.no, n2, cd.no, wf + (long long)q * cd.no, lw,
+                                        p2 + (long long)q * cd.Lt + cd.cl, ldp));
+                    vr.push_back(prob64(Er, 2LL * n2, 4 * cd.no, n2, cn.no, wf + 4 * cd.no + (long long)q * cn.no, lw,
+                                        p2 + (long long)q * cd.Lt + cd.cl + cd.no, ldp));
+                }
+                vr.push_back(prob64(Er, 2LL * n2, 4 * cd.no, n2, 2 * r, UX + ld.lr_off + (long long)cc * n2 * 2 * r,
+                                    2 * r, p3 + 2 * r, 4 * r));
+            }
+        }
+        iw += J;
+    }
+    for (auto *w : {&vl, &vr})
+        for (auto &g : *w) g.beta = 1;  // the two interfaces of a cell meet in its own columns
+    run_list64(c, vl);
+    run_list64(c, vr);
+    CellDesc *dcl = (CellDesc *)c->dalloc(sizeof(CellDesc) * cl.size());
+    HZ_CU(cudaMemcpyAsync(dcl, cl.data(), sizeof(CellDesc) * cl.size(), cudaMemcpyHostToDevice, c->st));
+    k_add_s<<<dim3(32, (unsigned)cl.size()), 256, 0, c->st>>>(dcl, S, P2);
+    HZ_CU(cudaGetLastError());
+    c->nl++;
+    HZ_CU(cudaStreamSynchronize(c->st));
+    c->dfree(dcl);
+    c->dfree(WF);
+}
+
 // ---------------------------------------------------------- factor ---
 // Factorization of the layers in `lays` (all layers on the first call, from
 // hz_factor; the layers whose cells read a changed medium on a local update,
@@ -1020,6 +1173,21 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
             c->o64.LAM = LAM64;
         }
     }
+    // 3c. the sweep-step composites of the compressed-block LU
+    double2 *CP2_64 = nullptr, *CP3_64 = nullptr, *CP1_64 = nullptr;
+    if (c->lr_r > 0 && STW64) {
+        if (!mixed) {
+            CP2_64 = c->o64.CP2;
+            CP3_64 = c->o64.CP3;
+            CP1_64 = c->o64.CP1;
+        }
+        compose_sweep(c, lays, F, E, S, Wi, STW64, UX64, CP2_64, CP3_64, CP1_64, first);
+        if (!mixed) {
+            c->o64.CP2 = CP2_64;
+            c->o64.CP3 = CP3_64;
+            c->o64.CP1 = CP1_64;
+        }
+    }
 
     // 4. mixed precision: the working-precision copies of these layers' operators
     if (mixed) {
@@ -1068,7 +1236,22 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
                 to_f32(UX64, o.UX, c->tot_lr, st, nl);
                 to_f32(MRN64, o.MRN, c->tot_m, st, nl);
                 to_f32(LAM64, o.LAM, c->tot_lam, st, nl);
+                o.CP2 = alloc_n<float2>(c, c->tot_cp2);
+                o.CP3 = alloc_n<float2>(c, c->tot_cp3);
+                o.CP1 = alloc_n<float2>(c, std::max(c->tot_cp1, 1LL));
+                to_f32(CP2_64, o.CP2, c->tot_cp2, st, nl);
+                to_f32(CP3_64, o.CP3, c->tot_cp3, st, nl);
+                to_f32(CP1_64, o.CP1, c->tot_cp1, st, nl);
             } else {
+                for (int l : lays)
+                    for (int cc = 0; cc < C; cc++) {
+                        const CellDesc &cd = c->cells[c->layers[l].cell0 + cc];
+                        to_f32(CP2_64 + cd.P2_off, o.CP2 + cd.P2_off, 16LL * cd.no * cd.Lt, st, nl);
+                        to_f32(CP3_64 + cd.P3_off, o.CP3 + cd.P3_off, 16LL * cd.no * c->lr_r, st, nl);
+                        if (cc < C - 1)
+                            to_f32(CP1_64 + cd.P1_off, o.CP1 + cd.P1_off,
+                                   8LL * c->lr_r * (cd.no + c->cells[c->layers[l].cell0 + cc + 1].no), st, nl);
+                    }
                 for (const LayerDesc &ld : lsub) {
                     const long long nlr = (long long)J * 2 * r * 2 * ld.nz, nm = (long long)J * 3 * r * r;
                     const long long nlam = (long long)(2 * r * J) * (2 * r * J);
@@ -1097,7 +1280,8 @@ void factor_layers(hz_ctx *c, const std::vector<int> &lays, bool first) {
         }
         HZ_CU(cudaStreamSynchronize(st));
         for (void *q : {(void *)cellW, (void *)czv, (void *)F, (void *)E, (void *)S, (void *)Wi, (void *)Pm, (void *)Vi,
-                        (void *)STW64, (void *)UX64, (void *)MRN64, (void *)LAM64})
+                        (void *)STW64, (void *)UX64, (void *)MRN64, (void *)LAM64, (void *)CP2_64, (void *)CP3_64,
+                        (void *)CP1_64})
             c->dfree(q);
     }
     c->dfree(d_info);

@@ -929,6 +929,77 @@ template <class T2> struct ListBuilder {
             push(g);
         }
     }
+    // sweep step of layer l through the composites (compressed-block LU): every cell's
+    // out rows r0, r0+1 += P2 (trace rows q0, q0+1 over the cell's input range), every
+    // interface's ac = P1 (the same rows over its two cells)
+    void add_compA(int l, int q0, const T2 *const in[4], long long ld, int r0, T2 *const out[4], long long ldo,
+                   T2 *acv, int N) {
+        const LayerDesc &ld_ = c->layers[l];
+        const int r = c->lr_r;
+        for (int cc = 0; cc < c->C; cc++) {
+            const CellDesc &cd = c->cells[ld_.cell0 + cc];
+            const long long gs = cd.t + cd.own_lo - cd.cl;  // first global column of the input range
+            GemmProb<T2> g{};
+            g.A = o.CP2 + cd.P2_off + (long long)r0 * cd.no * 4 * cd.Lt + (long long)q0 * cd.Lt;
+            g.lda = 4LL * cd.Lt;
+            g.M = 2 * cd.no;
+            g.K = 2 * cd.Lt;
+            g.N = N;
+            g.xseg = cd.Lt;
+            g.ldx = ld;
+            for (int q = 0; q < 2; q++) g.X[q] = in[q0 + q] + gs * ld;
+            g.yseg = cd.no;
+            g.ldy = ldo;
+            for (int q = 0; q < 2; q++) g.Y[q] = out[r0 + q] + (long long)(cd.t + cd.own_lo) * ldo;
+            g.beta = 1;
+            g.alpha = 1.f;
+            push(g);
+        }
+        for (int cc = 0; cc + 1 < c->C; cc++) {
+            const CellDesc &cd = c->cells[ld_.cell0 + cc], &cn = c->cells[ld_.cell0 + cc + 1];
+            const int L2 = cd.no + cn.no;
+            GemmProb<T2> g{};
+            g.A = o.CP1 + cd.P1_off + (long long)q0 * L2;
+            g.lda = 4LL * L2;
+            g.M = 2 * r;
+            g.K = 2 * L2;
+            g.N = N;
+            g.xseg = L2;
+            g.ldx = ld;
+            for (int q = 0; q < 2; q++) g.X[q] = in[q0 + q] + (long long)(cd.t + cd.own_lo) * ld;
+            g.yseg = 1 << 30;
+            g.ldy = N;
+            g.Y[0] = acv + (ld_.ac_off + (long long)cc * 2 * r) * N;
+            g.beta = 0;
+            g.alpha = 1.f;
+            push(g);
+        }
+    }
+    // ... then every cell's out rows r0, r0+1 += P3 [ts of interface c-1; ts of interface c]
+    void add_compC(int l, int r0, T2 *const out[4], long long ldo, const T2 *tsv, int N) {
+        const LayerDesc &ld_ = c->layers[l];
+        const int r = c->lr_r, C = c->C;
+        if (C < 2) return;
+        for (int cc = 0; cc < C; cc++) {
+            const CellDesc &cd = c->cells[ld_.cell0 + cc];
+            GemmProb<T2> g{};
+            g.A = o.CP3 + cd.P3_off + (long long)r0 * cd.no * 4 * r;
+            g.lda = 4LL * r;
+            g.M = 2 * cd.no;
+            g.K = (cc == 0 || cc == C - 1) ? 2 * r : 4 * r;
+            if (cc == 0) g.A += 2 * r;  // no interface on the left
+            g.N = N;
+            g.xseg = 1 << 30;
+            g.ldx = N;
+            g.X[0] = tsv + (ld_.ac_off + (long long)std::max(cc - 1, 0) * 2 * r) * N;
+            g.yseg = cd.no;
+            g.ldy = ldo;
+            for (int q = 0; q < 2; q++) g.Y[q] = out[r0 + q] + (long long)(cd.t + cd.own_lo) * ldo;
+            g.beta = 1;
+            g.alpha = 1.f;
+            push(g);
+        }
+    }
     ProbList<T2> finish() {
         if (c->tca_pending) {  // split copies built on this stream are complete before any stream reads them
             HZ_CU(cudaStreamSynchronize(c->st));
@@ -1141,6 +1212,20 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         lb.add_ES(k, 1, in, B, 2, out, B, W.inner, B, B, 1);
         W.es_down[k] = lb.finish();
     }
+    // the same downward steps through the composites (compressed-block LU)
+    const bool comp = lr && o.CP2 && o.LAM;
+    if (comp) {
+        W.cA_down.assign(L, ProbList<T2>());
+        W.cC_down.assign(L, ProbList<T2>());
+        for (int k = 1; k <= L - 2; k++) {
+            const T2 *in[4] = {vec_rows(W.pb, k - 1, 0), vec_rows(W.pb, k - 1, 1), nullptr, nullptr};
+            T2 *out[4] = {nullptr, nullptr, vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1)};
+            lb.add_compA(k, 0, in, B, 2, out, B, W.ac, B);
+            W.cA_down[k] = lb.finish();
+            lb.add_compC(k, 2, out, B, W.ts, B);
+            W.cC_down[k] = lb.finish();
+        }
+    }
     // upward sweep on pb: layer k+1 from the u-part of interface k+1 into the u-part of interface k
     W.f_up.assign(L, ProbList<T2>());
     W.es_up.assign(L, ProbList<T2>());
@@ -1151,6 +1236,18 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
         lb.add_ES(k + 1, 2, in, B, 1, out, B, W.inner, B, B, 1);
         W.es_up[k] = lb.finish();
+    }
+    if (comp) {
+        W.cA_up.assign(L, ProbList<T2>());
+        W.cC_up.assign(L, ProbList<T2>());
+        for (int k = L - 3; k >= 0; k--) {
+            const T2 *in[4] = {nullptr, nullptr, vec_rows(W.pb, k + 1, 2), vec_rows(W.pb, k + 1, 3)};
+            T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
+            lb.add_compA(k + 1, 2, in, B, 0, out, B, W.ac, B);
+            W.cA_up[k] = lb.finish();
+            lb.add_compC(k + 1, 0, out, B, W.ts, B);
+            W.cC_up[k] = lb.finish();
+        }
     }
     // reflections on pb: layer k+1, top = d of interface k, bottom = d of interface k+1
     for (int k = 0; k < K; k++) {
@@ -1355,7 +1452,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.ux2B);
     fl(W.lamB);
     fl(W.lam2B);
-    for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer})
+    for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer, &W.cA_down, &W.cC_down,
+                     &W.cA_up, &W.cC_up})
         for (auto &pl : *vv) fl(pl);
     if (W.hhost) cudaFreeHost(W.hhost);
     if (W.rhost) cudaFreeHost(W.rhost);
@@ -1422,6 +1520,19 @@ template Work<float2> &work<float2>(hz_ctx *, int);
 // ------------------------------------------------------- layer pieces ---
 // inner solve of layers [l0, l0+nl): h_j = W_j g_j (batched GEMM) then the
 // block-LU recurrences; `wide` selects the 2B-wide buffers of the polarized operator
+// ts = LAM ac for layers [l0, l0 + nl) (compressed-block LU), one product per layer
+template <class T2> static void run_lam(hz_ctx *c, Work<T2> &W, bool wide, int l0, int nl) {
+    const ProbList<T2> &la = wide ? W.lam2B : W.lamB;
+    ProbList<T2> ls = la;
+    ls.d = la.d + l0;
+    ls.n = nl;
+    ls.tc_tiles = (long long)nl * la.tc_max_tiles;
+    ls.tiles32 = (long long)nl * la.max_tiles32;
+    ls.bytes = la.bytes * nl / c->L;
+    ls.flops = la.flops * nl / c->L;
+    run(c, ls, 1);
+}
+
 template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, int l0, int nl) {
     if (c->C < 2) return;
     Ops<T2> &o = ops<T2>(c);
@@ -1451,15 +1562,7 @@ template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, 
         if (nl == 1 || !lr_chain_fits<T2>(c, N)) {
             // one layer (a sweep step): the recursion as one product, ts = LAM ac, instead
             // of 2(C-1) dependent steps on a few SMs
-            const ProbList<T2> &la = wide ? W.lam2B : W.lamB;
-            ProbList<T2> ls = la;
-            ls.d = la.d + l0;
-            ls.n = nl;
-            ls.tc_tiles = (long long)nl * la.tc_max_tiles;
-            ls.tiles32 = (long long)nl * la.max_tiles32;
-            ls.bytes = la.bytes * nl / c->L;
-            ls.flops = la.flops * nl / c->L;
-            run(c, ls, 1);
+            run_lam(c, W, wide, l0, nl);
         } else {
             c->kt_begin(1, by, fl);
             launch_lr_chain<T2>(c, c->d_layer_ids + l0, nl, o.MRN, wide ? W.ac2 : W.ac, wide ? W.ts2 : W.ts, N);
@@ -1511,11 +1614,25 @@ template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, dou
 
 // preconditioner on W.pb in place (input copied there by the caller):
 // kind 0 GS, 1 Jacobi, 2 down only, 3 up only, 4 reflections only
+// HZ_SWEEP=factored keeps the sweep steps on the factored operators (for comparisons)
+static bool comp_off() {
+    static const bool off = getenv("HZ_SWEEP") && strcmp(getenv("HZ_SWEEP"), "factored") == 0;
+    return off;
+}
+
 template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind) {
     if (c->nested()) return nested_precond(c, W, kind);
     const int L = c->L;
+    // a sweep step through the composites (compressed-block LU): three products
+    const bool comp = !W.cA_down.empty() && !comp_off();
     if (kind == 0 || kind == 1 || kind == 2) {
         for (int k = 1; k <= L - 2; k++) {
+            if (comp) {
+                run(c, W.cA_down[k]);
+                run_lam(c, W, false, k, 1);
+                run(c, W.cC_down[k]);
+                continue;
+            }
             run(c, W.f_down[k]);
             chain_layers(c, W, false, k, 1);
             run(c, W.es_down[k]);
@@ -1542,6 +1659,12 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
     }
     if (kind == 0 || kind == 1 || kind == 3) {
         for (int k = L - 3; k >= 0; k--) {
+            if (comp) {
+                run(c, W.cA_up[k]);
+                run_lam(c, W, false, k + 1, 1);
+                run(c, W.cC_up[k]);
+                continue;
+            }
             run(c, W.f_up[k]);
             chain_layers(c, W, false, k + 1, 1);
             run(c, W.es_up[k]);
