@@ -63,16 +63,15 @@ METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roof
 # cells a launch processes).  Keyed by (kernel class, workload whose launch
 # shapes were captured); a class without a capture of its current kernel
 # reports traffic null.
-# ncu DRAM bytes (read + write) over algorithmic bytes of a kernel class, from one capture.
-# The traffic per launch reported beside the roofline is this ratio times the live algorithmic
-# bytes per launch.  The 2000 x 400 layered shape has the launch shapes of the 2000 x 4000 one
-# (same cell width, rank and list lengths per layer), so its ratio stands for both.
-_GEMM_RATIO = (0.861, "ncu DRAM bytes of every batched-product launch of two solves of the"
-                      " 2000 x 400 layered shape (the launch shapes of the 2000 x 4000 workload)"
-                      " over their algorithmic bytes")
+# ncu DRAM bytes (read + write) over algorithmic bytes of a kernel class, from one capture of
+# its current kernel.  The traffic per launch reported beside the roofline is this ratio times
+# the live algorithmic bytes per launch.  The 2000 x 400 layered shape has the cells of the
+# 2000 x 4000 one (160 x 160 cell boxes, 16 right-hand sides), so its ratio stands for both.
+_CELL_RATIO = (0.987, "ncu DRAM bytes of one cell-solve launch (80 cells of 160 x 160, 16 right-hand sides)"
+                      " of the 2000 x 400 layered shape over its algorithmic bytes")
 DRAM_PER_ALGO = {
-    ("batched_fes_gemm", "layered2000x4000", "tc"): _GEMM_RATIO,
-    ("batched_fes_gemm", "layered2000x400", "tc"): _GEMM_RATIO,
+    ("cell_chain", "layered2000x4000", "tc"): _CELL_RATIO,
+    ("cell_chain", "layered2000x400", "tc"): _CELL_RATIO,
 }
 UNIT = "RHS*Mdof/s"
 

@@ -906,18 +906,47 @@ __global__ void __launch_bounds__(512 / TM, 1) k_cell_chain16(const CellDesc *__
             float2 acc[TM][2];
 #pragma unroll
             for (int i = 0; i < TM; i++) acc[i][0] = acc[i][1] = czero<float2>();
-            int k = 0;
-#pragma unroll 4
-            for (; k + 1 < nx; k += 2) {
-                const Pair<float2> x0 = ld_pair(xr + k * 16), x1 = ld_pair(xr + (k + 1) * 16);
+            // K pairs software-pipelined: the next pair's shared-memory loads are issued before
+            // the current pair's FMAs; even and odd K accumulate apart (shorter FMA chains)
+            float2 acc2[TM][2];
 #pragma unroll
-                for (int i = 0; i < TM; i++) {
-                    const Pair<float2> p = ld_pair(w0 + i * ldws + k);
-                    cmac(acc[i][0], p.a, x0.a);
-                    cmac(acc[i][1], p.a, x0.b);
-                    cmac(acc[i][0], p.b, x1.a);
-                    cmac(acc[i][1], p.b, x1.b);
+            for (int i = 0; i < TM; i++) acc2[i][0] = acc2[i][1] = czero<float2>();
+            int k = 0;
+            const int kp = nx & ~1;  // K covered by pairs
+            if (kp > 0) {
+                Pair<float2> x0 = ld_pair(xr), x1 = ld_pair(xr + 16), p[TM];
+#pragma unroll
+                for (int i = 0; i < TM; i++) p[i] = ld_pair(w0 + i * ldws);
+#pragma unroll 2
+                for (; k + 2 < kp; k += 2) {
+                    const Pair<float2> y0 = ld_pair(xr + (k + 2) * 16), y1 = ld_pair(xr + (k + 3) * 16);
+                    Pair<float2> pn[TM];
+#pragma unroll
+                    for (int i = 0; i < TM; i++) pn[i] = ld_pair(w0 + i * ldws + k + 2);
+#pragma unroll
+                    for (int i = 0; i < TM; i++) {
+                        cmac(acc[i][0], p[i].a, x0.a);
+                        cmac(acc[i][1], p[i].a, x0.b);
+                        cmac(acc2[i][0], p[i].b, x1.a);
+                        cmac(acc2[i][1], p[i].b, x1.b);
+                        p[i] = pn[i];
+                    }
+                    x0 = y0;
+                    x1 = y1;
                 }
+#pragma unroll
+                for (int i = 0; i < TM; i++) {  // the last pair
+                    cmac(acc[i][0], p[i].a, x0.a);
+                    cmac(acc[i][1], p[i].a, x0.b);
+                    cmac(acc2[i][0], p[i].b, x1.a);
+                    cmac(acc2[i][1], p[i].b, x1.b);
+                }
+                k = kp;
+            }
+#pragma unroll
+            for (int i = 0; i < TM; i++) {
+                acc[i][0] = acc[i][0] + acc2[i][0];
+                acc[i][1] = acc[i][1] + acc2[i][1];
             }
             if (k < nx) {
                 const Pair<float2> x0 = ld_pair(xr + k * 16);

@@ -57,4 +57,6 @@ def test_16_and_17_columns_agree():
     x17 = ctx.hz_cell_solve(1, 0, g)          # general kernel
     x16 = ctx.hz_cell_solve(1, 0, g[:16])     # 16-column kernel
     ctx.close()
-    assert _rel(x16, x17[:16]) < 1e-6
+    # each kernel is within 2e-6 of the oracle (its own FP32 rounding order), so the two
+    # differ by at most the sum of their bars
+    assert _rel(x16, x17[:16]) < 4e-6
