@@ -24,6 +24,15 @@ template <> Ops<float2> &ops<float2>(hz_ctx *c) { return c->o32; }
 // max that keeps a NaN (std::max drops it when it comes second)
 static inline double nanmax(double a, double b) { return (std::isnan(a) || std::isnan(b)) ? NAN : std::max(a, b); }
 
+// right-hand side of element e of a [points][B] array (no 64-bit division for power-of-two B)
+__device__ __forceinline__ int rhs_of(long long e, int B) {
+    return (B & (B - 1)) == 0 ? (int)(e & (B - 1)) : (int)(e % B);
+}
+
+// point of element e of a [points][B] array
+__device__ __forceinline__ long long point_of(long long e, int B) {
+    return (B & (B - 1)) == 0 ? (e >> (__ffs(B) - 1)) : e / B;
+}
 static inline int grid1(long long n, int t = 256) { return (int)std::min<long long>((n + t - 1) / t, 65535LL * 8); }
 
 // ----------------------------------------------------------- kernels ---
@@ -236,8 +245,8 @@ __global__ void k_scatter(const CellDesc *__restrict__ cells, const double2 *__r
     const CellDesc &cd = cells[blockIdx.y];
     const long long n = (long long)cd.nx * cd.nz * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        long long pt = e / B;
-        int b = (int)(e % B);
+        long long pt = point_of(e, B);
+        int b = rhs_of(e, B);
         int jz = (int)(pt / cd.nx), jx = (int)(pt % cd.nx);
         T2 v = czero<T2>();
         if (jz >= cd.row_lo && jz < cd.row_hi && jx >= cd.own_lo && jx < cd.own_lo + cd.no)
@@ -256,7 +265,7 @@ __global__ void k_gather_inner(const LayerDesc *__restrict__ layers, const CellD
     const int nz = ld.nz, J = ld.C - 1;
     const long long n = (long long)J * 2 * nz * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
+        int b = rhs_of(e, B);
         long long q = e / B;
         int m = (int)(q % (2 * nz)), j = (int)(q / (2 * nz));
         T2 v;
@@ -279,7 +288,7 @@ __global__ void k_samples(const CellDesc *__restrict__ cells, const T2 *__restri
     const CellDesc &cd = cells[blockIdx.y];
     const long long n = 4LL * cd.no * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
+        int b = rhs_of(e, B);
         long long q = e / B;
         int o = (int)(q % cd.no), rho = (int)(q / cd.no);
         int jz = rho == 0 ? p - 1 : (rho == 1 ? p : (rho == 2 ? p + cd.n - 1 : p + cd.n));
@@ -424,7 +433,7 @@ __global__ void k_get_traces(const LayerDesc *__restrict__ layers, const double2
 __global__ void k_put_traces(const double2 *__restrict__ tr, double2 *x, int K, int NX, int B) {
     const long long n = (long long)K * 4 * NX * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e % B);
+        const int b = rhs_of(e, B);
         long long q = e / B;
         const int xi = (int)(q % NX);
         q /= NX;
@@ -451,7 +460,7 @@ __global__ void k_recon_src(const CellDesc *__restrict__ cells, const LayerDesc 
     const int c0 = p - 1, c1 = p, cw = p + cd.w - 1, cw1 = p + cd.w;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)npts * B;
          e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e % B);
+        const int b = rhs_of(e, B);
         const int q = (int)(e / B);
         int jz, jx;
         if (q < 4 * cd.no) {
@@ -506,7 +515,7 @@ __global__ void k_accum_u(const CellDesc *__restrict__ cells, const T2 *__restri
     const int rows = cd.row_hi - cd.row_lo;
     const long long n = (long long)rows * cd.no * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
+        int b = rhs_of(e, B);
         long long q = e / B;
         int jx = cd.own_lo + (int)(q % cd.no), jz = cd.row_lo + (int)(q / cd.no);
         long long o = (cd.vol_off + (long long)jz * cd.nx + jx) * B + b;
@@ -528,14 +537,19 @@ __global__ void k_cast(const TA *__restrict__ a, TB *b, long long n) {
 __global__ void k_dots(const double2 *__restrict__ V, long long vstride, const double2 *__restrict__ w, long long n,
                        int B, int nchunk, double2 *part) {
     const int i = blockIdx.z;
-    const int b = blockIdx.y * 32 + threadIdx.x;
+    // batches that divide 32 put 32 / B points side by side in a warp, so that every lane
+    // works; wider batches take 32 right-hand sides per warp
+    const bool packed = B < 32 && (32 % B) == 0;
+    const int P = packed ? 32 / B : 1;
+    const int b = packed ? (int)threadIdx.x % B : blockIdx.y * 32 + threadIdx.x;
+    const int p0 = packed ? threadIdx.y * P + threadIdx.x / B : threadIdx.y, ps = blockDim.y * P;
     const long long chunk = (n + nchunk - 1) / nchunk;
     const long long x0 = blockIdx.x * chunk, x1 = min(n, x0 + chunk);
     double2 acc = make_double2(0.0, 0.0);
     if (b < B) {
         const double2 *Vi = V + i * vstride;
 #pragma unroll 4
-        for (long long x = x0 + threadIdx.y; x < x1; x += blockDim.y) {
+        for (long long x = x0 + p0; x < x1; x += ps) {
             const double2 a = Vi[x * B + b], c = w[x * B + b];
             acc.x += a.x * c.x + a.y * c.y;
             acc.y += a.x * c.y - a.y * c.x;
@@ -544,9 +558,10 @@ __global__ void k_dots(const double2 *__restrict__ V, long long vstride, const d
     __shared__ double2 red[8][33];
     red[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
-    if (threadIdx.y == 0 && b < B) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int y = 0; y < blockDim.y; y++) s = s + red[y][threadIdx.x];
+    if (threadIdx.y == 0 && (int)threadIdx.x < (packed ? B : 32) && b < B) {
+        double2 s = make_double2(0.0, 0.0);  // rows, then the lanes of this right-hand side, in order
+        for (int y = 0; y < blockDim.y; y++)
+            for (int l = threadIdx.x; l < 32; l += packed ? B : 32) s = s + red[y][l];
         part[((long long)i * nchunk + blockIdx.x) * B + b] = s;
     }
 }
@@ -576,7 +591,7 @@ __global__ void k_dots_final(const double2 *__restrict__ part, int nchunk, int B
 __global__ void k_axpy_multi(const double2 *__restrict__ V, long long vstride, const double2 *__restrict__ hc, int nvec,
                              double2 *w, long long n, int B) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
+        int b = rhs_of(e, B);
         double2 s = w[e];
         for (int i = 0; i < nvec; i++) s = s - V[i * vstride + e] * hc[i * B + b];
         w[e] = s;
@@ -587,7 +602,7 @@ __global__ void k_axpy_multi(const double2 *__restrict__ V, long long vstride, c
 __global__ void k_scale(const double2 *__restrict__ w, const double *__restrict__ scale, double2 *out, long long n,
                         int B) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x)
-        out[e] = scale[e % B] * w[e];
+        out[e] = scale[rhs_of(e, B)] * w[e];
 }
 
 // x += sum_j Z_j y[j][b]
@@ -595,7 +610,7 @@ template <class T2>
 __global__ void k_update_x(const T2 *__restrict__ Z, long long zstride, const double2 *__restrict__ y, int nvec,
                            double2 *x, long long n, int B) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
-        int b = (int)(e % B);
+        int b = rhs_of(e, B);
         double2 s = x[e];
         for (int j = 0; j < nvec; j++) s = s + to2(Z[j * zstride + e], double2{}) * y[j * B + b];
         x[e] = s;
@@ -613,7 +628,7 @@ __global__ void k_sub(const double2 *__restrict__ a, const double2 *__restrict__
 __global__ void k_bicg_p(double2 *p, const double2 *__restrict__ r, const double2 *__restrict__ v,
                          const double2 *__restrict__ beta, const double2 *__restrict__ omega, long long n, int B) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x) {
-        const int b = (int)(e % B);
+        const int b = rhs_of(e, B);
         p[e] = r[e] + beta[b] * (p[e] - omega[b] * v[e]);
     }
 }
@@ -621,7 +636,7 @@ __global__ void k_bicg_p(double2 *p, const double2 *__restrict__ r, const double
 __global__ void k_zaxpy(double2 *out, const double2 *__restrict__ a, const double2 *__restrict__ x,
                         const double2 *__restrict__ coef, long long n, int B) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * B; e += (long long)gridDim.x * blockDim.x)
-        out[e] = a[e] + coef[e % B] * x[e];
+        out[e] = a[e] + coef[rhs_of(e, B)] * x[e];
 }
 
 // ---------------------------------------- compressed-block LU recursion ---
