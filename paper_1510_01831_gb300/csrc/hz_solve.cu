@@ -944,11 +944,11 @@ template <class T2> struct ListBuilder {
             push(g);
         }
     }
-    // sweep step of layer l through the composites (compressed-block LU): every cell's
-    // out rows r0, r0+1 += P2 (trace rows q0, q0+1 over the cell's input range), every
+    // a layer's Green's integral through the composites (compressed-block LU): every cell's
+    // out rows r0, r0+1 += P2 (trace rows q0 .. q0+nq-1 over the cell's input range), every
     // interface's ac = P1 (the same rows over its two cells)
-    void add_compA(int l, int q0, const T2 *const in[4], long long ld, int r0, T2 *const out[4], long long ldo,
-                   T2 *acv, int N) {
+    void add_compA(int l, int q0, int nq, const T2 *const in[4], long long ld, int r0, T2 *const out[4],
+                   long long ldo, T2 *acv, int N) {
         const LayerDesc &ld_ = c->layers[l];
         const int r = c->lr_r;
         for (int cc = 0; cc < c->C; cc++) {
@@ -958,11 +958,11 @@ template <class T2> struct ListBuilder {
             g.A = o.CP2 + cd.P2_off + (long long)r0 * cd.no * 4 * cd.Lt + (long long)q0 * cd.Lt;
             g.lda = 4LL * cd.Lt;
             g.M = 2 * cd.no;
-            g.K = 2 * cd.Lt;
+            g.K = nq * cd.Lt;
             g.N = N;
             g.xseg = cd.Lt;
             g.ldx = ld;
-            for (int q = 0; q < 2; q++) g.X[q] = in[q0 + q] + gs * ld;
+            for (int q = 0; q < nq; q++) g.X[q] = in[q0 + q] + gs * ld;
             g.yseg = cd.no;
             g.ldy = ldo;
             for (int q = 0; q < 2; q++) g.Y[q] = out[r0 + q] + (long long)(cd.t + cd.own_lo) * ldo;
@@ -977,11 +977,11 @@ template <class T2> struct ListBuilder {
             g.A = o.CP1 + cd.P1_off + (long long)q0 * L2;
             g.lda = 4LL * L2;
             g.M = 2 * r;
-            g.K = 2 * L2;
+            g.K = nq * L2;
             g.N = N;
             g.xseg = L2;
             g.ldx = ld;
-            for (int q = 0; q < 2; q++) g.X[q] = in[q0 + q] + (long long)(cd.t + cd.own_lo) * ld;
+            for (int q = 0; q < nq; q++) g.X[q] = in[q0 + q] + (long long)(cd.t + cd.own_lo) * ld;
             g.yseg = 1 << 30;
             g.ldy = N;
             g.Y[0] = acv + (ld_.ac_off + (long long)cc * 2 * r) * N;
@@ -1235,7 +1235,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         for (int k = 1; k <= L - 2; k++) {
             const T2 *in[4] = {vec_rows(W.pb, k - 1, 0), vec_rows(W.pb, k - 1, 1), nullptr, nullptr};
             T2 *out[4] = {nullptr, nullptr, vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1)};
-            lb.add_compA(k, 0, in, B, 2, out, B, W.ac, B);
+            lb.add_compA(k, 0, 2, in, B, 2, out, B, W.ac, B);
             W.cA_down[k] = lb.finish();
             lb.add_compC(k, 2, out, B, W.ts, B);
             W.cC_down[k] = lb.finish();
@@ -1258,7 +1258,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         for (int k = L - 3; k >= 0; k--) {
             const T2 *in[4] = {nullptr, nullptr, vec_rows(W.pb, k + 1, 2), vec_rows(W.pb, k + 1, 3)};
             T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
-            lb.add_compA(k + 1, 2, in, B, 0, out, B, W.ac, B);
+            lb.add_compA(k + 1, 2, 2, in, B, 0, out, B, W.ac, B);
             W.cA_up[k] = lb.finish();
             lb.add_compC(k + 1, 0, out, B, W.ts, B);
             W.cC_up[k] = lb.finish();
@@ -1286,6 +1286,24 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         lb.add_ES(k + 1, mask, in, B, 1, out, B, W.inner, B, B, 1);
     }
     W.es_refl = lb.finish();
+    if (comp) {  // the same reflections through the composites: [P2, P1] lists, then P3
+        for (int k = 0; k < K; k++) {
+            const int nq = (k + 1 <= L - 2) ? 4 : 2;
+            const T2 *in[4] = {vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1), nullptr, nullptr};
+            if (nq == 4) {
+                in[2] = vec_rows(W.pb, k + 1, 0);
+                in[3] = vec_rows(W.pb, k + 1, 1);
+            }
+            T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
+            lb.add_compA(k + 1, 0, nq, in, B, 0, out, B, W.ac, B);
+        }
+        W.cA_refl = lb.finish();
+        for (int k = 0; k < K; k++) {
+            T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
+            lb.add_compC(k + 1, 0, out, B, W.ts, B);
+        }
+        W.cC_refl = lb.finish();
+    }
     // reconstruction F-step from the traces tr = pc viewed as [K][2][NX][B] (accumulating)
     for (int l = 0; l < L; l++) {
         int mask = (l > 0 ? 1 : 0) | (l < L - 1 ? 2 : 0);
@@ -1466,6 +1484,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.uxB);
     fl(W.ux2B);
     fl(W.lamB);
+    fl(W.cA_refl);
+    fl(W.cC_refl);
     fl(W.lam2B);
     for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer, &W.cA_down, &W.cC_down,
                      &W.cA_up, &W.cC_up})
@@ -1546,6 +1566,25 @@ template <class T2> static void run_lam(hz_ctx *c, Work<T2> &W, bool wide, int l
     ls.bytes = la.bytes * nl / c->L;
     ls.flops = la.flops * nl / c->L;
     run(c, ls, 1);
+}
+
+// the compressed-block LU recursion ts = LAM ac of layers [l0, l0 + nl): one product for a
+// single layer, else the r-vector chain kernel over the layers
+template <class T2> static void lr_recursion(hz_ctx *c, Work<T2> &W, bool wide, int l0, int nl) {
+    const int N = wide ? 2 * W.B : W.B;
+    if (nl == 1 || !lr_chain_fits<T2>(c, N)) {
+        run_lam(c, W, wide, l0, nl);
+        return;
+    }
+    double by = 0, fl = 0;
+    if (c->opts.time_kernels) {
+        const double J = c->C - 1, es = sizeof(T2), r = c->lr_r;
+        by = nl * es * (3 * J * r * r + 4 * J * r * N);
+        fl = nl * 8.0 * 3 * J * r * r * N;
+    }
+    c->kt_begin(1, by, fl);
+    launch_lr_chain<T2>(c, c->d_layer_ids + l0, nl, ops<T2>(c).MRN, wide ? W.ac2 : W.ac, wide ? W.ts2 : W.ts, N);
+    c->kt_end();
 }
 
 template <class T2> static void chain_layers(hz_ctx *c, Work<T2> &W, bool wide, int l0, int nl) {
@@ -1663,9 +1702,15 @@ template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind
         k_gs_fix<T2><<<grid1((long long)(L - 1) * c->NX * W.B), 256, 0, c->st>>>(W.pb, L - 1, c->NX, W.B);
         HZ_CU(cudaGetLastError());
         c->nl++;
-        run(c, W.f_refl);
-        chain_layers(c, W, false, 1, L - 1);
-        run(c, W.es_refl);
+        if (comp) {
+            run(c, W.cA_refl);
+            lr_recursion(c, W, false, 1, L - 1);
+            run(c, W.cC_refl);
+        } else {
+            run(c, W.f_refl);
+            chain_layers(c, W, false, 1, L - 1);
+            run(c, W.es_refl);
+        }
         if (kind == 4) {
             k_refl_finish<T2><<<grid1((long long)(L - 1) * c->NX * W.B), 256, 0, c->st>>>(W.pb, L - 1, c->NX, W.B);
             HZ_CU(cudaGetLastError());

@@ -1,7 +1,9 @@
 """Sweep steps of the compressed-block LU through the per-cell composites
 (P2 = E W F + S, P1 = STW F, P3 = E UX; the step is out += P2 in, ac = P1 in,
-ts = LAM ac, out += P3 ts) against the oracle's sweeps (Alg. downwardsSweep,
-Alg. upwardsSweep; Section 4.2.2 with the compression of Section 4.3).
+ts = LAM ac, out += P3 ts) against the oracle's sweeps and reflections
+(Alg. downwardsSweep, Alg. upwardsSweep, Alg. upwardsReflections; Section
+4.2.2 with the compression of Section 4.3).  The reflections apply every layer
+at once with four input rows and the r-vector chain between the products.
 
 The composites are the same linear map regrouped and formed in FP64, so at a
 tight compression tolerance (eps = 1e-12) the FP64 sweeps match the oracle to
@@ -56,12 +58,15 @@ def test_sweeps_match_the_oracle(case, precision, eps, bar):
     ctx = _ctx(pb, C_pml, eps, precision)
     down = ctx.hz_precond(2, x)
     up = ctx.hz_precond(3, x)
+    refl = ctx.hz_precond(4, x)
     gs = ctx.hz_precond(0, x)
     ctx.close()
     ref_down = np.concatenate([O.sweep_down(D, x[..., 0:2, :]), x[..., 2:4, :]], axis=-2)
     ref_up = np.concatenate([x[..., 0:2, :], O.sweep_up(D, x[..., 2:4, :])], axis=-2)
+    ref_refl = np.concatenate([np.zeros_like(x[..., 0:2, :]), O.reflections(D, x[..., 0:2, :])], axis=-2)
     assert _rel(down, ref_down) < bar
     assert _rel(up, ref_up) < bar
+    assert _rel(refl, ref_refl) < bar
     assert _rel(gs, O.precond_gs(D, x)) < bar
 
 
