@@ -95,6 +95,7 @@ template <class T2> struct Work {
     // then (after ts = LAM ac) out += P3 ts, per step of the downward / upward sweeps
     std::vector<ProbList<T2>> cA_down, cC_down, cA_up, cC_up;
     ProbList<T2> cA_refl, cC_refl;  // the reflections (all layers) through the composites
+    ProbList<T2> cA_M, cC_M;        // the polarized operator (both input sets) through the composites
     std::vector<double> hbytes, hflops;  // per layer (B wide)
     std::vector<long long> htiles, utiles;  // 32-row tiles per layer of the h_j and x_j lists
 };

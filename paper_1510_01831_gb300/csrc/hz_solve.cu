@@ -945,12 +945,10 @@ template <class T2> struct ListBuilder {
         }
     }
     // a layer's Green's integral through the composites (compressed-block LU): every cell's
-    // out rows r0, r0+1 += P2 (trace rows q0 .. q0+nq-1 over the cell's input range), every
-    // interface's ac = P1 (the same rows over its two cells)
-    void add_compA(int l, int q0, int nq, const T2 *const in[4], long long ld, int r0, T2 *const out[4],
-                   long long ldo, T2 *acv, int N) {
+    // out rows r0, r0+1 (+)= P2 (trace rows q0 .. q0+nq-1 over the cell's input range) ...
+    void add_compP2(int l, int q0, int nq, const T2 *const in[4], long long ld, int r0, T2 *const out[4],
+                    long long ldo, int N, int beta) {
         const LayerDesc &ld_ = c->layers[l];
-        const int r = c->lr_r;
         for (int cc = 0; cc < c->C; cc++) {
             const CellDesc &cd = c->cells[ld_.cell0 + cc];
             const long long gs = cd.t + cd.own_lo - cd.cl;  // first global column of the input range
@@ -966,10 +964,15 @@ template <class T2> struct ListBuilder {
             g.yseg = cd.no;
             g.ldy = ldo;
             for (int q = 0; q < 2; q++) g.Y[q] = out[r0 + q] + (long long)(cd.t + cd.own_lo) * ldo;
-            g.beta = 1;
+            g.beta = beta;
             g.alpha = 1.f;
             push(g);
         }
+    }
+    // ... and every interface's ac = P1 (the same rows over its two cells), ac with ld ldac
+    void add_compP1(int l, int q0, int nq, const T2 *const in[4], long long ld, T2 *acv, long long ldac, int N) {
+        const LayerDesc &ld_ = c->layers[l];
+        const int r = c->lr_r;
         for (int cc = 0; cc + 1 < c->C; cc++) {
             const CellDesc &cd = c->cells[ld_.cell0 + cc], &cn = c->cells[ld_.cell0 + cc + 1];
             const int L2 = cd.no + cn.no;
@@ -983,15 +986,21 @@ template <class T2> struct ListBuilder {
             g.ldx = ld;
             for (int q = 0; q < nq; q++) g.X[q] = in[q0 + q] + (long long)(cd.t + cd.own_lo) * ld;
             g.yseg = 1 << 30;
-            g.ldy = N;
-            g.Y[0] = acv + (ld_.ac_off + (long long)cc * 2 * r) * N;
+            g.ldy = ldac;
+            g.Y[0] = acv + (ld_.ac_off + (long long)cc * 2 * r) * ldac;
             g.beta = 0;
             g.alpha = 1.f;
             push(g);
         }
     }
+    void add_compA(int l, int q0, int nq, const T2 *const in[4], long long ld, int r0, T2 *const out[4],
+                   long long ldo, T2 *acv, int N) {
+        add_compP2(l, q0, nq, in, ld, r0, out, ldo, N, 1);
+        add_compP1(l, q0, nq, in, ld, acv, N, N);
+    }
     // ... then every cell's out rows r0, r0+1 += P3 [ts of interface c-1; ts of interface c]
-    void add_compC(int l, int r0, T2 *const out[4], long long ldo, const T2 *tsv, int N) {
+    // (ts with ld ldts)
+    void add_compC(int l, int r0, T2 *const out[4], long long ldo, const T2 *tsv, long long ldts, int N) {
         const LayerDesc &ld_ = c->layers[l];
         const int r = c->lr_r, C = c->C;
         if (C < 2) return;
@@ -1005,8 +1014,8 @@ template <class T2> struct ListBuilder {
             if (cc == 0) g.A += 2 * r;  // no interface on the left
             g.N = N;
             g.xseg = 1 << 30;
-            g.ldx = N;
-            g.X[0] = tsv + (ld_.ac_off + (long long)std::max(cc - 1, 0) * 2 * r) * N;
+            g.ldx = ldts;
+            g.X[0] = tsv + (ld_.ac_off + (long long)std::max(cc - 1, 0) * 2 * r) * ldts;
             g.yseg = cd.no;
             g.ldy = ldo;
             for (int q = 0; q < 2; q++) g.Y[q] = out[r0 + q] + (long long)(cd.t + cd.own_lo) * ldo;
@@ -1229,7 +1238,32 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
     }
     // the same downward steps through the composites (compressed-block LU)
     const bool comp = lr && o.CP2 && o.LAM;
-    if (comp) {
+    if (comp) {  // the polarized operator: set A (columns 0..B) -> rows n, n+1, set B -> rows 0, 1
+        for (int l = 0; l < L; l++) {
+            const T2 *in[4], *inB[4];
+            T2 *out[4], *outB[4];
+            for (int q = 0; q < 4; q++) {
+                in[q] = W.lin + ((long long)l * 4 + q) * rowsz2;
+                out[q] = W.lout + ((long long)l * 4 + q) * rowsz2;
+                inB[q] = in[q] + B;
+                outB[q] = out[q] + B;
+            }
+            if (l < L - 1) lb.add_compP2(l, 0, 4, in, 2 * B, 2, out, 2 * B, B, 0);
+            if (l > 0) lb.add_compP2(l, 0, 4, inB, 2 * B, 0, outB, 2 * B, B, 0);
+            lb.add_compP1(l, 0, 4, in, 2 * B, W.ac2, 2 * B, B);
+            lb.add_compP1(l, 0, 4, inB, 2 * B, W.ac2 + B, 2 * B, B);
+        }
+        W.cA_M = lb.finish();
+        for (int l = 0; l < L; l++) {
+            T2 *out[4], *outB[4];
+            for (int q = 0; q < 4; q++) {
+                out[q] = W.lout + ((long long)l * 4 + q) * rowsz2;
+                outB[q] = out[q] + B;
+            }
+            if (l < L - 1) lb.add_compC(l, 2, out, 2 * B, W.ts2, 2 * B, B);
+            if (l > 0) lb.add_compC(l, 0, outB, 2 * B, W.ts2 + B, 2 * B, B);
+        }
+        W.cC_M = lb.finish();
         W.cA_down.assign(L, ProbList<T2>());
         W.cC_down.assign(L, ProbList<T2>());
         for (int k = 1; k <= L - 2; k++) {
@@ -1237,7 +1271,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             T2 *out[4] = {nullptr, nullptr, vec_rows(W.pb, k, 0), vec_rows(W.pb, k, 1)};
             lb.add_compA(k, 0, 2, in, B, 2, out, B, W.ac, B);
             W.cA_down[k] = lb.finish();
-            lb.add_compC(k, 2, out, B, W.ts, B);
+            lb.add_compC(k, 2, out, B, W.ts, B, B);
             W.cC_down[k] = lb.finish();
         }
     }
@@ -1260,7 +1294,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
             T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
             lb.add_compA(k + 1, 2, 2, in, B, 0, out, B, W.ac, B);
             W.cA_up[k] = lb.finish();
-            lb.add_compC(k + 1, 0, out, B, W.ts, B);
+            lb.add_compC(k + 1, 0, out, B, W.ts, B, B);
             W.cC_up[k] = lb.finish();
         }
     }
@@ -1300,7 +1334,7 @@ template <class T2> static void build_lists(hz_ctx *c, Work<T2> &W) {
         W.cA_refl = lb.finish();
         for (int k = 0; k < K; k++) {
             T2 *out[4] = {vec_rows(W.pb, k, 2), vec_rows(W.pb, k, 3), nullptr, nullptr};
-            lb.add_compC(k + 1, 0, out, B, W.ts, B);
+            lb.add_compC(k + 1, 0, out, B, W.ts, B, B);
         }
         W.cC_refl = lb.finish();
     }
@@ -1485,6 +1519,8 @@ template <class T2> static void free_work(hz_ctx *c, Work<T2> &W) {
     fl(W.ux2B);
     fl(W.lamB);
     fl(W.cA_refl);
+    fl(W.cA_M);
+    fl(W.cC_M);
     fl(W.cC_refl);
     fl(W.lam2B);
     for (auto *vv : {&W.f_down, &W.es_down, &W.f_up, &W.es_up, &W.f_layer, &W.es_layer, &W.cA_down, &W.cC_down,
@@ -1650,6 +1686,12 @@ template <class T2> static void nested_apply_M(hz_ctx *c, Work<T2> &W, const T2 
 template <class T2> static void nested_precond(hz_ctx *c, Work<T2> &W, int kind);
 
 // polarized operator: y (FP64) = M x (x in the working precision)
+// HZ_SWEEP=factored keeps the sweep steps and the polarized operator on the factored operators (for comparisons)
+static bool comp_off() {
+    static const bool off = getenv("HZ_SWEEP") && strcmp(getenv("HZ_SWEEP"), "factored") == 0;
+    return off;
+}
+
 template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, double2 *y) {
     if (c->nested()) return nested_apply_M(c, W, x, y);
     const int B = W.B;
@@ -1657,9 +1699,15 @@ template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, dou
     k_stage_M<T2><<<grid1(n), 256, 0, c->st>>>(x, W.lin, c->L, c->NX, B);
     HZ_CU(cudaGetLastError());
     c->nl++;
-    run(c, W.f_full);
-    chain_layers(c, W, true, 0, c->L);
-    run(c, W.es_bot_A);
+    if (!W.cA_M.d || comp_off()) {
+        run(c, W.f_full);
+        chain_layers(c, W, true, 0, c->L);
+        run(c, W.es_bot_A);
+    } else {  // through the composites (compressed-block LU)
+        run(c, W.cA_M);
+        lr_recursion(c, W, true, 0, c->L);
+        run(c, W.cC_M);
+    }
     const long long m = c->n_tr() * B;
     k_combine_M<T2><<<grid1(m), 256, 0, c->st>>>(x, W.lout, y, c->L, c->NX, B);
     HZ_CU(cudaGetLastError());
@@ -1668,11 +1716,6 @@ template <class T2> static void apply_M(hz_ctx *c, Work<T2> &W, const T2 *x, dou
 
 // preconditioner on W.pb in place (input copied there by the caller):
 // kind 0 GS, 1 Jacobi, 2 down only, 3 up only, 4 reflections only
-// HZ_SWEEP=factored keeps the sweep steps on the factored operators (for comparisons)
-static bool comp_off() {
-    static const bool off = getenv("HZ_SWEEP") && strcmp(getenv("HZ_SWEEP"), "factored") == 0;
-    return off;
-}
 
 template <class T2> static void precond_inplace(hz_ctx *c, Work<T2> &W, int kind) {
     if (c->nested()) return nested_precond(c, W, kind);

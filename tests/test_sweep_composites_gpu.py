@@ -2,8 +2,9 @@
 (P2 = E W F + S, P1 = STW F, P3 = E UX; the step is out += P2 in, ac = P1 in,
 ts = LAM ac, out += P3 ts) against the oracle's sweeps and reflections
 (Alg. downwardsSweep, Alg. upwardsSweep, Alg. upwardsReflections; Section
-4.2.2 with the compression of Section 4.3).  The reflections apply every layer
-at once with four input rows and the r-vector chain between the products.
+4.2.2 with the compression of Section 4.3), and the polarized operator (Alg.
+applyM).  The reflections and the operator apply every layer at once with four
+input rows and the r-vector chain between the products.
 
 The composites are the same linear map regrouped and formed in FP64, so at a
 tight compression tolerance (eps = 1e-12) the FP64 sweeps match the oracle to
@@ -68,6 +69,17 @@ def test_sweeps_match_the_oracle(case, precision, eps, bar):
     assert _rel(up, ref_up) < bar
     assert _rel(refl, ref_refl) < bar
     assert _rel(gs, O.precond_gs(D, x)) < bar
+
+
+@pytest.mark.parametrize("precision,eps,bar", [(hz.HZ_FP64, 1e-12, 1e-9), (hz.HZ_MIXED, 1e-8, 1e-5)])
+def test_polarized_operator_matches_the_oracle(case, precision, eps, bar):
+    # both input sets of every layer (4 input rows each) in one 2B-wide application
+    pb, C_pml, D = case
+    x = _x(D, 3, 74)
+    ctx = _ctx(pb, C_pml, eps, precision)
+    y = ctx.hz_apply_M(x)
+    ctx.close()
+    assert _rel(y, O.apply_M(D, x)) < bar
 
 
 def test_local_update_rewrites_the_composites(case):
