@@ -197,6 +197,17 @@ constexpr int NW_KB = 16, NW_WPC = 4, NW_NB = 16, NW_CTAS_PER_SM = 4, NW_WS_SLOT
 // slots are problem * max_tiles + tile)
 void launch_gemm_narrow(const GemmProb<float2> *d_probs, int nprob, int max_tiles, int nmax, int split, float2 *ws,
                         int *cnt, cudaStream_t st, int *nl);
+// persistent narrow sweep: phases run in order, each a list of n problems (<= NW_NB
+// columns, N and ldx even, 16-byte aligned right-hand-side rows) with max_tiles 32-row
+// tiles and split K slices; grid <= narrow_sweep_grid() CTAs (all co-resident), bar a
+// device counter, err the context's status block
+struct NwPhase {
+    const GemmProb<float2> *d;
+    int n, max_tiles, split;
+};
+int narrow_sweep_grid();
+void launch_narrow_sweep(const NwPhase *d_ph, int nph, float2 *ws, int *cnt, unsigned *bar, int *err, int grid,
+                         cudaStream_t st, int *nl);
 // batched GEMM tile (complex outputs) and K step
 constexpr int GBM = 64, GBN = 32, GBK = 16;
 // split-K is used while a launch has fewer tiles than this; its workspace

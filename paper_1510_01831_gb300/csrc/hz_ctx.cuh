@@ -96,6 +96,12 @@ template <class T2> struct Work {
     std::vector<ProbList<T2>> cA_down, cC_down, cA_up, cC_up;
     ProbList<T2> cA_refl, cC_refl;  // the reflections (all layers) through the composites
     ProbList<T2> cA_M, cC_M;        // the polarized operator (both input sets) through the composites
+    // persistent sweeps (FP32, <= 16 even columns): the phases of the downward and upward
+    // sweeps, their algorithmic bytes / flops, and the grid barrier counter
+    NwPhase *sw_down = nullptr, *sw_up = nullptr;
+    int nsw_down = 0, nsw_up = 0;
+    double sw_bytes[2] = {0, 0}, sw_flops[2] = {0, 0};
+    unsigned *sw_bar = nullptr;
     std::vector<double> hbytes, hflops;  // per layer (B wide)
     std::vector<long long> htiles, utiles;  // 32-row tiles per layer of the h_j and x_j lists
 };
@@ -194,6 +200,7 @@ struct hz_ctx {
     // error word and timers
     std::vector<hz_ctx *> lanes;
     hz_ctx *parent = nullptr;  // set on a lane
+    int group_n = 1;           // contexts of the solve in progress (persistent sweeps need the GPU alone)
     // inner nested polarized traces (opts.inner = HZ_INNER_NESTED): per layer, a
     // context of the layer's box with x and z swapped (its layers are the cells),
     // a lane of it for 2B-wide applications, and FP64 source / solution volumes

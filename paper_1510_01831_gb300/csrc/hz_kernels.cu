@@ -27,6 +27,11 @@ template <int SZ> __device__ __forceinline__ void gemm_cp(void *dst, const void 
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(SZ), "r"(bytes) : "memory");
 }
+// 16-byte asynchronous copy that bypasses L1 (data written by other CTAs of the same launch)
+__device__ __forceinline__ void gemm_cp16cg(void *dst, const void *src, unsigned bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void gemm_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N> __device__ __forceinline__ void gemm_cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
@@ -387,24 +392,25 @@ template <int NB> constexpr size_t nw_smem() {
     return sizeof(float2) * (size_t)NW_WPC * nw_stages<NB>() * nw_stage_elems<NB>();
 }
 
-template <int NB>
-__global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<float2> *__restrict__ probs, int S,
-                                                             float2 *ws, int *cnt, int max_tiles) {
+// One work unit of the narrow GEMM: tile `tile` (32 rows) of problem *prob, K slice sp
+// of S.  PERSIST: called repeatedly by the CTAs of the persistent sweep kernel, whose
+// phases read what other CTAs of the same launch wrote, so the right-hand-side blocks
+// and the accumulated outputs are read past L1 (16-byte cp.async.cg, ld.global.cg);
+// otherwise one unit per CTA, with programmatic dependent launch.
+template <int NB, bool PERSIST>
+__device__ __forceinline__ void narrow_unit(const GemmProb<float2> *__restrict__ prob, int tile, int sp, int S,
+                                            float2 *ws, int *cnt, long long slot, GemmProb<float2> &P, int &last,
+                                            unsigned char *nsm) {
     constexpr int NS = nw_stages<NB>(), STG = nw_stage_elems<NB>(), ASZ = 32 * (NW_KB + 1);
-    __shared__ GemmProb<float2> P;
-    __shared__ int last;
-    extern __shared__ __align__(16) unsigned char nsm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     float2 *wb = reinterpret_cast<float2 *>(nsm) + warp * NS * STG;
-    // programmatic dependent launch: the next kernel may start its own prologue now; this
-    // one reads only constant data (descriptors, operators) before griddepcontrol.wait
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     static_assert(sizeof(GemmProb<float2>) % 8 == 0, "problem descriptor copied as 8-byte words");
+    __syncthreads();  // the previous unit of this CTA is done with P and the rings
     for (int w = tid; w < (int)(sizeof(GemmProb<float2>) / 8); w += NW_WPC * 32)
-        reinterpret_cast<long long *>(&P)[w] = reinterpret_cast<const long long *>(probs + blockIdx.y)[w];
+        reinterpret_cast<long long *>(&P)[w] = reinterpret_cast<const long long *>(prob)[w];
     __syncthreads();
     const int M = P.M, N = P.N;
-    const int tile = blockIdx.x / S, sp = blockIdx.x % S, m0 = tile * 32;
+    const int m0 = tile * 32;
     if (m0 >= M) return;  // uniform over the CTA and over the tile's slices
     const int K1 = max(P.K, 0), K2 = max(P.K2, 0);
     const int nb1 = (K1 + NW_KB - 1) / NW_KB, nbt = nb1 + (K2 + NW_KB - 1) / NW_KB;
@@ -433,6 +439,20 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
         }
         if (!(parts & 2)) return;
         const bool one = xseg >= K;  // a single segment: no division
+        if constexpr (PERSIST) {  // 16-byte copies of column pairs (N and ldx even, 16-byte aligned rows)
+#pragma unroll
+            for (int q = 0; q < NB / 4; q++) {
+                const int e = lane + 32 * q, xr = e / (NB / 2), xc = 2 * (e % (NB / 2)), gx = k0 + xr;
+                const bool ok = gx < K && xc < N;
+                const float2 *src = A;
+                if (ok) {
+                    const int sg = one ? 0 : gx / xseg;
+                    src = Xp[sg] + (long long)(gx - sg * xseg) * ldx + xc;
+                }
+                gemm_cp16cg(Xs + xr * NB + xc, src, ok ? 16u : 0u);
+            }
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < NB / 2; q++) {
             const int e = lane + 32 * q, xr = e / NB, xc = e % NB, gx = k0 + xr;
@@ -453,7 +473,7 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
 #pragma unroll
     for (int t = 0; t < NS - 1; t++)
         if (t < nmine) issue(t, 1);
-    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if constexpr (!PERSIST) asm volatile("griddepcontrol.wait;" ::: "memory");
 #pragma unroll
     for (int t = 0; t < NS - 1; t++) {
         if (t < nmine) issue(t, 2);
@@ -482,7 +502,6 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
 #pragma unroll
     for (int n = 0; n < NB; n++) red[(warp * 32 + lane) * (NB + 1) + n] = acc[n];
     __syncthreads();
-    const long long slot = (long long)blockIdx.y * max_tiles + tile;
     if (S > 1) {
         float2 *mine = ws + (slot * S + sp) * (32 * NB);
         for (int e = tid; e < 32 * NB; e += NW_WPC * 32) {
@@ -520,9 +539,23 @@ __global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<floa
         v.y *= al;
         const int sg = m / P.yseg;
         float2 *row = P.Y[sg] + (long long)(m - sg * P.yseg) * P.ldy;
-        row[n] = P.beta ? row[n] + v : v;
+        row[n] = P.beta ? __ldcg(row + n) + v : v;
     }
     if (S > 1 && tid == 0) cnt[slot] = 0;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NW_WPC * 32) k_gemm_narrow(const GemmProb<float2> *__restrict__ probs, int S,
+                                                             float2 *ws, int *cnt, int max_tiles) {
+    __shared__ GemmProb<float2> P;
+    __shared__ int last;
+    extern __shared__ __align__(16) unsigned char nsm[];
+    // programmatic dependent launch: the next kernel may start its own prologue now; this
+    // one reads only constant data (descriptors, operators) before griddepcontrol.wait
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int tile = blockIdx.x / S, sp = blockIdx.x % S;
+    narrow_unit<NB, false>(probs + blockIdx.y, tile, sp, S, ws, cnt, (long long)blockIdx.y * max_tiles + tile, P,
+                           last, nsm);
 }
 
 template <int NB>
@@ -2075,6 +2108,97 @@ void launch_cell_factor(const CellDesc *d_cells, int ncell, const double2 *diag,
     HZ_CU(cudaFuncSetAttribute(k_cell_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     k_cell_factor<<<ncell, 256, sm, st>>>(d_cells, diag, cx, cz, W, d_info);
     HZ_CU(cudaGetLastError());
+    if (nl) (*nl)++;
+}
+
+
+// ================================================= persistent narrow sweep ===
+// A whole Gauss-Seidel sweep (every step's [P2, P1], Λ and P3 lists of §8e, in
+// order) as one cooperative launch: the CTAs stay resident and take the work
+// units of a phase (problem, 32-row tile, K slice) in turn, and the phases are
+// separated by a grid barrier.  The barrier is a counter that every CTA raises
+// once per phase and polls with acquire loads; the wait is bounded by the
+// context's wait limit, after which the CTA sets the error word and leaves (the
+// others see the error word and leave too), so a failed barrier ends the launch
+// with HZ_ETIMEOUT instead of hanging.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(NW_WPC * 32) k_narrow_sweep(const NwPhase *__restrict__ ph, int nph, float2 *ws,
+                                                              int *cnt, unsigned *bar, int *err) {
+    __shared__ GemmProb<float2> P;
+    __shared__ int last, dead;
+    extern __shared__ __align__(16) unsigned char nsm[];
+    for (int f = 0; f < nph; f++) {
+        const NwPhase Q = ph[f];
+        const int per = Q.max_tiles * Q.split, units = Q.n * per;
+        for (int u = blockIdx.x; u < units; u += gridDim.x) {
+            const int pr = u / per, rem = u - pr * per, tile = rem / Q.split, sp = rem - tile * Q.split;
+            narrow_unit<NB, true>(Q.d + pr, tile, sp, Q.split, ws, cnt, (long long)pr * Q.max_tiles + tile, P, last,
+                                  nsm);
+        }
+        if (f + 1 == nph) break;
+        __syncthreads();  // this CTA's stores of the phase are issued
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(bar, 1u);
+            const unsigned target = (unsigned)(f + 1) * gridDim.x;
+            const unsigned long long lim = wait_limit_ns(err);
+            unsigned long long t0 = 0;
+            int d = 0;
+            for (unsigned it = 0;; it++) {
+                if (ld_acquire_u32(bar) >= target) break;
+                if ((it & 63u) == 63u) {
+                    if (*reinterpret_cast<volatile int *>(err)) {  // another CTA gave up
+                        d = 1;
+                        break;
+                    }
+                    const unsigned long long t = global_ns();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if (t - t0 > lim) {
+                        atomicExch(err, 1);
+                        d = 1;
+                        break;
+                    }
+                }
+                __nanosleep(64);
+            }
+            __threadfence();
+            dead = d;
+        }
+        __syncthreads();
+        if (dead) return;
+    }
+}
+
+int narrow_sweep_grid() {
+    static int g = -1;
+    if (g < 0) {
+        int dev = 0, sms = 0, per = 0, coop = 0;
+        HZ_CU(cudaGetDevice(&dev));
+        HZ_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        HZ_CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        const size_t sm = nw_smem<NW_NB>();
+        HZ_CU(cudaFuncSetAttribute(k_narrow_sweep<NW_NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HZ_CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_narrow_sweep<NW_NB>, NW_WPC * 32, sm));
+        g = coop ? std::min(per, NW_CTAS_PER_SM) * sms : 0;
+    }
+    return g;
+}
+
+void launch_narrow_sweep(const NwPhase *d_ph, int nph, float2 *ws, int *cnt, unsigned *bar, int *err, int grid,
+                         cudaStream_t st, int *nl) {
+    if (nph <= 0) return;
+    if (grid <= 0 || grid > narrow_sweep_grid()) throw HzError(HZ_EINVAL, "persistent sweep: grid not co-resident");
+    HZ_CU(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
+    void *args[] = {(void *)&d_ph, (void *)&nph, (void *)&ws, (void *)&cnt, (void *)&bar, (void *)&err};
+    HZ_CU(cudaLaunchCooperativeKernel((const void *)k_narrow_sweep<NW_NB>, dim3(grid), dim3(NW_WPC * 32), args,
+                                      nw_smem<NW_NB>(), st));
     if (nl) (*nl)++;
 }
 

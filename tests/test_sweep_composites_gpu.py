@@ -82,6 +82,43 @@ def test_polarized_operator_matches_the_oracle(case, precision, eps, bar):
     assert _rel(y, O.apply_M(D, x)) < bar
 
 
+@pytest.mark.parametrize("B", [2, 16])
+def test_persistent_sweeps(case, B, monkeypatch):
+    # with HZ_PERSIST=1, even batches of <= 16 columns run each sweep as one persistent
+    # launch (phases separated by grid barriers)
+    pb, C_pml, D = case
+    x = _x(D, B, 75)
+    monkeypatch.setenv("HZ_PERSIST", "1")
+    ctx = _ctx(pb, C_pml, 1e-8, hz.HZ_MIXED)
+    down = ctx.hz_precond(2, x)
+    up = ctx.hz_precond(3, x)
+    gs = ctx.hz_precond(0, x)
+    gs2 = ctx.hz_precond(0, x)
+    ctx.close()
+    ref_down = np.concatenate([O.sweep_down(D, x[..., 0:2, :]), x[..., 2:4, :]], axis=-2)
+    ref_up = np.concatenate([x[..., 0:2, :], O.sweep_up(D, x[..., 2:4, :])], axis=-2)
+    assert _rel(down, ref_down) < 1e-5
+    assert _rel(up, ref_up) < 1e-5
+    assert _rel(gs, O.precond_gs(D, x)) < 1e-5
+    assert _rel(gs2, gs) < 1e-12  # repeatable: split-K slices are added in a fixed order
+
+
+def test_persistent_solve_matches_and_launches_less(case, monkeypatch):
+    pb, C_pml, D = case
+    f = I.random_sources(pb.shape_ext, pb.n_pml, 4, 76)
+    monkeypatch.setenv("HZ_PERSIST", "1")
+    ctx = _ctx(pb, C_pml, 1e-8, hz.HZ_MIXED)
+    u1, st1 = ctx.hz_solve(f)
+    ctx.close()
+    monkeypatch.setenv("HZ_PERSIST", "0")
+    ctx = _ctx(pb, C_pml, 1e-8, hz.HZ_MIXED)
+    u0, st0 = ctx.hz_solve(f)
+    ctx.close()
+    assert st1.gpu_launches < st0.gpu_launches  # the sweeps ran as single launches
+    assert st1.resid < 1e-8 and st0.resid < 1e-8
+    assert _rel(u1, u0) < 1e-6
+
+
 def test_local_update_rewrites_the_composites(case):
     pb, C_pml, D = case
     m1 = pb.m.copy()
