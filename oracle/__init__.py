@@ -14,7 +14,9 @@ Layers of the oracle:
   integrals of Section 2.3 written through the identity of Appendix C, the
   polarized system of Section 3 and its preconditioners, the inner nested
   polarized traces of Section 4.2 (a layer solved over its cells by the same
-  functions on its swapped-axes box), and the misfit gradient.  Every operator is applied through explicit local solves; no
+  functions on its swapped-axes box), the block-LU sweeps of the inner SIE and
+  their compressed (low-rank) form (Sections 4.2.2, 4.3), and the misfit
+  gradient.  Every operator is applied through explicit local solves; no
   operator is precomputed or compressed.
 
 Readings of the paper taken where it is ambiguous (each is listed with its
@@ -651,3 +653,60 @@ def misfit_gradient(box: Box, f: np.ndarray, d: np.ndarray, rec_idx: np.ndarray,
     lam = fac.solve(g.reshape(f.shape), trans=True).reshape(B, -1)
     grad = box.omega ** 2 * np.sum(np.real(lam * uf), axis=0)
     return J, grad.reshape(box.shape), u
+
+
+# ---------------------------------------------------------------------------
+# Block-LU sweeps of a layer's inner SIE (Section 4.2.2) and their compressed
+# form (the compression of the inner operators to a tolerance eps, Section 4.3).
+# The inner unknowns of interface j are written x_j; with W_j the inverted
+# diagonal Schur block, h_j = W_j g_j, P_j the sub-diagonal and V_j the
+# super-diagonal factor, the two sweeps are
+#     y_0 = h_0,  y_j = h_j + P_j y_{j-1};   x_{J-1} = y_{J-1},  x_j = y_j + V_j x_{j+1}.
+
+def inner_block_lu(P, V, h):
+    """The two sweeps above.  P[j] (j >= 1), V[j] (j <= J-2): (n x n); h: (J, n, B)."""
+    J = len(h)
+    y = [None] * J
+    y[0] = h[0].copy()
+    for j in range(1, J):
+        y[j] = h[j] + P[j] @ y[j - 1]
+    x = [None] * J
+    x[J - 1] = y[J - 1]
+    for j in range(J - 2, -1, -1):
+        x[j] = y[j] + V[j] @ x[j + 1]
+    return np.array(x)
+
+
+def lowrank(A, eps):
+    """A ~ Q Bf with orthonormal Q and the smallest rank whose relative Frobenius
+    error is <= eps (truncated SVD: the optimal low-rank form for that norm)."""
+    U, s, Vh = np.linalg.svd(A, full_matrices=False)
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1]))[::-1]  # tail[k] = ||s[k:]||
+    total = tail[0] if len(s) else 0.0
+    r = len(s)
+    for k in range(len(s)):
+        if tail[k] <= eps * total:
+            r = k
+            break
+    r = max(r, 1)
+    return U[:, :r], s[:r, None] * Vh[:r]
+
+
+def inner_block_lu_lowrank(QP, BP, QV, BV, h):
+    """The same sweeps with P_j = QP_j BP_j and V_j = QV_j BV_j, carried on the
+    r-vectors t_j = BP_j y_{j-1} and s_j = BV_j x_{j+1}:
+        t_1 = BP_1 h_0,  t_{j+1} = BP_{j+1} (h_j + QP_j t_j);
+        s_{J-2} = BV_{J-2} (h_{J-1} + QP_{J-1} t_{J-1}),  s_{j-1} = BV_{j-1} (h_j + QP_j t_j + QV_j s_j);
+        x_j = h_j + QP_j t_j + QV_j s_j   (t_0 = 0, s_{J-1} = 0)."""
+    J = len(h)
+    y = [None] * J
+    y[0] = h[0]
+    for j in range(1, J):
+        t = BP[j] @ y[j - 1]
+        y[j] = h[j] + QP[j] @ t
+    x = [None] * J
+    x[J - 1] = y[J - 1]
+    for j in range(J - 2, -1, -1):
+        s = BV[j] @ x[j + 1]
+        x[j] = y[j] + QV[j] @ s
+    return np.array(x)
