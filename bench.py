@@ -70,8 +70,8 @@ METRIC = "RHS*Mdof/s, nested polarized-traces solve at 1e-8 residual; % HBM roof
 _CELL_RATIO = (0.987, "ncu DRAM bytes of one cell-solve launch (80 cells of 160 x 160, 16 right-hand sides)"
                       " of the 2000 x 400 layered shape over its algorithmic bytes")
 DRAM_PER_ALGO = {
-    ("cell_chain", "layered2000x4000", "tc"): _CELL_RATIO,
-    ("cell_chain", "layered2000x400", "tc"): _CELL_RATIO,
+    ("cell_chain", "layered2000x4000", "simt"): _CELL_RATIO,
+    ("cell_chain", "layered2000x400", "simt"): _CELL_RATIO,
 }
 UNIT = "RHS*Mdof/s"
 
@@ -192,7 +192,15 @@ def make_problem(wl):
 CLASS_NAMES = ["cell_chain", "inner_chain", "batched_fes_gemm"]
 
 
+def widest_cell(pb):
+    """Columns of the widest cell box (interior columns + the PML on both sides)."""
+    cols = pb.cell_cols if pb.cell_cols is not None else [-(-pb.n_x // pb.C)]
+    return max(cols) + 2 * pb.n_pml
+
+
 def roofline(kt_ms, kt_n, kt_b, kt_f, ms, steps, mixed, tensor_cores, workload):
+    """tensor_cores: the cell solves run on the tensor cores (mixed precision, cells of at
+    most 128 columns); otherwise on the FP32 / FP64 pipes."""
     """Roofline of the kernel class with the largest device time, against the roof
     it is closer to, plus every class's algorithmic rates against both roofs."""
     top = int(np.argmax(kt_ms))
@@ -213,7 +221,7 @@ def roofline(kt_ms, kt_n, kt_b, kt_f, ms, steps, mixed, tensor_cores, workload):
         roof = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
                 "frac": round(tfl / alu_peak, 4)}
     traffic, traffic_src = None, None
-    key = (CLASS_NAMES[top], workload, "tc" if (mixed and tensor_cores) else "simt")
+    key = (CLASS_NAMES[top], workload, "tc" if (mixed and tensor_cores) else "simt" if mixed else "fp64")
     if key in DRAM_PER_ALGO and kt_n[top] > 0:
         ratio, traffic_src = DRAM_PER_ALGO[key]
         traffic = round(float(ratio * kt_b[top] / kt_n[top]))
@@ -338,7 +346,8 @@ def measure(args, workload, precision, steps, warmup, world, e2e=False, measure_
            "gpu_launches": int(sum(m["gpu_launches"] for m in flat)),
            "solve": solve[0] if len(solve) == 1 else solve,
            "ms_per_step_with_kernel_events": round(ms_ev, 3),
-           "roofline": roofline(kt_ms, kt_n, kt_b, kt_f, ms_ev, steps, mixed, tc > 0, workload),
+           "roofline": roofline(kt_ms, kt_n, kt_b, kt_f, ms_ev, steps, mixed,
+                                tc > 0 and max(widest_cell(pb) for pb in pbs) <= 128, workload),
            "clocks": clk.summary()}
     if e2e:
         # end-to-end through the same entry point with pinned host buffers: the copies of the
